@@ -1,0 +1,373 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: textbook
+lattice isotropy, the moment conditions that the equilibria and the Guo term
+must satisfy for the Chapman-Enskog limit (Sec. 2.2), closed forms of the
+lattice stencils, the planar tanh interface (Sec. 2.2), the Laplace law with
+sigma = sqrt(8 kappa A / 9), exact conservation, plane Couette flow between
+the moving walls, the viscosity nu = cs^2 (tau - 1/2) (Sec. 2.2) and the
+symmetries of the four-roller device (Sec. 3.2).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+CS2 = 1.0 / 3.0
+
+
+def _lat(orc, lattice):
+    c, w = orc.lattice_info(lattice)
+    return c.astype(float), w
+
+
+# ----------------------------------------------------------------- lattices
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_lattice_isotropy(orc, lattice):
+    """Textbook DdQq conditions: weights sum to 1, odd moments vanish,
+    sum w c c = cs^2 I and sum w cccc = cs^4 (dd + dd + dd) with cs^2 = 1/3."""
+    c, w = _lat(orc, lattice)
+    q = 9 if lattice == 0 else 19
+    assert len(w) == q
+    d = 2 if lattice == 0 else 3
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.abs(np.einsum("i,ia->a", w, c)).max() < 1e-16
+    M2 = np.einsum("i,ia,ib->ab", w, c, c)
+    assert np.allclose(M2[:d, :d], CS2 * np.eye(d), atol=1e-15)
+    M3 = np.einsum("i,ia,ib,ic->abc", w, c, c, c)
+    assert np.abs(M3).max() < 1e-16
+    M4 = np.einsum("i,ia,ib,ic,id->abcd", w, c, c, c, c)
+    dl = np.eye(3)
+    for a, b, cc, dd in itertools.product(range(d), repeat=4):
+        want = CS2 ** 2 * (dl[a, b] * dl[cc, dd] + dl[a, cc] * dl[b, dd] + dl[a, dd] * dl[b, cc])
+        assert abs(M4[a, b, cc, dd] - want) < 1e-15
+    # every velocity has its opposite in the set
+    for ci in c:
+        assert any(np.array_equal(-ci, cj) for cj in c)
+
+
+# --------------------------------------------------------- moment conditions
+
+def _rand_u(rng, lattice):
+    u = rng.uniform(-0.08, 0.08, 3)
+    if lattice == 0:
+        u[2] = 0.0
+    return u
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_feq_moments(orc, lattice):
+    """Eq. feq carries rho, rho u and rho (cs^2 I + u u)."""
+    c, _ = _lat(orc, lattice)
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        rho = rng.uniform(0.8, 1.2)
+        u = _rand_u(rng, lattice)
+        f = orc.feq(lattice, rho, u)
+        assert abs(f.sum() - rho) < 1e-14
+        assert np.abs(c.T @ f - rho * u).max() < 1e-15
+        P = np.einsum("i,ia,ib->ab", f, c, c)
+        want = rho * (CS2 * np.eye(3) + np.outer(u, u))
+        if lattice == 0:
+            want[2, 2] = 0.0
+        assert np.abs(P - want).max() < 1e-14
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_geq_moments(orc, lattice):
+    """Eq. geq: sum g_eq = phi (by the rest population), first moment phi u,
+    second moment Gamma mu I + phi u u (the Cahn-Hilliard flux of Sec. 2.2)."""
+    c, _ = _lat(orc, lattice)
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        phi = rng.uniform(-1.0, 1.0)
+        mu = rng.uniform(-0.05, 0.05)
+        G = rng.uniform(0.1, 2.0)
+        u = _rand_u(rng, lattice)
+        g = orc.geq(lattice, phi, mu, G, u)
+        assert abs(g.sum() - phi) < 1e-15
+        assert np.abs(c.T @ g - phi * u).max() < 1e-15
+        P = np.einsum("i,ia,ib->ab", g, c, c)
+        want = G * mu * np.eye(3) + phi * np.outer(u, u)
+        if lattice == 0:
+            want[2, 2] = 0.0
+        assert np.abs(P - want).max() < 1e-15
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_guo_moments(orc, lattice):
+    """Eq. Fi (Guo): zeroth moment 0, first (1 - 1/2tau) F, second
+    (1 - 1/2tau)(u F + F u)."""
+    c, _ = _lat(orc, lattice)
+    rng = np.random.default_rng(13)
+    for _ in range(20):
+        tau = rng.uniform(0.55, 2.5)
+        u = _rand_u(rng, lattice)
+        F = rng.uniform(-1e-3, 1e-3, 3)
+        if lattice == 0:
+            F[2] = 0.0
+        S = orc.guo(lattice, tau, u, F)
+        k = 1.0 - 0.5 / tau
+        assert abs(S.sum()) < 1e-18
+        assert np.abs(c.T @ S - k * F).max() < 1e-18
+        P = np.einsum("i,ia,ib->ab", S, c, c)
+        assert np.abs(P - k * (np.outer(u, F) + np.outer(F, u))).max() < 1e-18
+
+
+# ------------------------------------------------------------- stencils
+
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 6, 20)), (1, (5, 4, 20))])
+def test_mu_closed_form_1d_wave(orc, lattice, shape):
+    """For phi varying along x only, the isotropic Laplacian reduces to the
+    three-point second difference; mu = A(phi^3-phi) - kappa lap(phi)."""
+    nz, ny, nx = shape
+    A, kappa = 0.05, 0.03
+    o = orc.Oracle(lattice, orc.PERIODIC, nx, ny, nz, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
+    x = np.arange(nx)
+    k = 2 * np.pi * 3 / nx
+    phi1 = 0.1 + 0.6 * np.cos(k * x) + 0.2 * np.sin(2 * k * x)
+    phi = np.broadcast_to(phi1, shape).copy()
+    one = np.ones(shape)
+    zero = np.zeros(shape)
+    o.init_fields(one, zero, zero, zero, phi)
+    fl = o.fields()
+    lap = np.roll(phi1, -1) - 2 * phi1 + np.roll(phi1, 1)
+    mu = A * (phi1 ** 3 - phi1) - kappa * lap
+    assert np.abs(fl["phi"] - phi).max() < 1e-14
+    assert np.abs(fl["mu"] - mu[None, None, :]).max() < 1e-14
+
+
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 5, 18)), (1, (4, 3, 18))])
+def test_force_closed_form_1d(orc, lattice, shape):
+    """With f at rest equilibrium (rho = 1, u = 0) the velocity returned is
+    F/2 (Eq. veloMoment).  For phi varying along x only the isotropic
+    gradient reduces to the central difference, so
+    F = mu dphi - d(phi mu) with d(a) = (a(x+1) - a(x-1))/2."""
+    nz, ny, nx = shape
+    A, kappa = 0.04, 0.04
+    o = orc.Oracle(lattice, orc.PERIODIC, nx, ny, nz, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
+    x = np.arange(nx)
+    phi1 = np.tanh((x - nx / 4) / 1.7) * -np.tanh((x - 3 * nx / 4) / 2.3)
+    phi = np.broadcast_to(phi1, shape).copy()
+    one, zero = np.ones(shape), np.zeros(shape)
+    o.init_fields(one, zero, zero, zero, phi)
+    fl = o.fields()
+    mu = fl["mu"][0, 0]
+    d = lambda a: (np.roll(a, -1) - np.roll(a, 1)) / 2
+    F = mu * d(phi1) - d(phi1 * mu)
+    assert np.abs(fl["rho"] - 1).max() < 1e-14
+    assert np.abs(fl["ux"] - (F / 2)[None, None, :]).max() < 1e-15
+    assert np.abs(fl["uy"]).max() < 1e-16
+    assert np.abs(fl["uz"]).max() < 1e-16
+    assert np.abs(F).max() > 1e-3  # the test is not vacuous
+
+
+# ------------------------------------------------------- planar interface
+
+def _slab(orc, xi, init_width, steps):
+    kappa = 0.04
+    A = kappa / xi ** 2
+    L = int(48 * xi)
+    o = orc.Oracle(0, orc.PERIODIC, L, 1, 1, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
+    x = np.arange(L)
+    x1, x2 = L / 4 - 0.5, 3 * L / 4 - 0.5
+    prof = lambda wd: np.tanh((x - x1) / (np.sqrt(2) * wd)) * -np.tanh((x - x2) / (np.sqrt(2) * wd))
+    init = prof(init_width)[None, None, :]
+    z = np.zeros_like(init)
+    o.init_fields(np.ones_like(init), z, z, z, init)
+    o.step(steps)
+    ph = o.fields()["phi"][0, 0]
+    d = (np.roll(ph, -1) - np.roll(ph, 1)) / 2
+    # excess free energy per interface of the reduced functional
+    sigma = np.sum(0.25 * A * (ph ** 2 - 1) ** 2 + 0.5 * kappa * d ** 2) / 2
+    return ph, prof(xi), sigma, np.sqrt(8 * kappa * A / 9)
+
+
+def test_flat_interface_tanh(orc):
+    """Sec. 2.2: a planar interface relaxes to phi = tanh(x / (sqrt 2 xi)),
+    xi = sqrt(kappa/A); the lattice error shrinks like xi^-2, and the excess
+    free energy tends to sigma = sqrt(8 kappa A / 9)."""
+    errs, sig_err = [], []
+    for xi in (1.0, 2.0, 4.0):
+        ph, ref, sig, sig_th = _slab(orc, xi, xi, int(1000 * xi * xi))
+        errs.append(np.abs(ph - ref).max())
+        sig_err.append(abs(sig / sig_th - 1))
+    assert errs[0] < 0.04
+    assert errs[1] < errs[0] / 3.5 and errs[2] < errs[1] / 3.5
+    assert errs[2] < 2.5e-3
+    assert sig_err[2] < 0.01 and sig_err[1] < 0.025
+    # relaxation from a profile 1.5x too wide reaches the same discrete state
+    ph_w, ref, _, _ = _slab(orc, 1.0, 1.5, 6000)
+    ph_e, _, _, _ = _slab(orc, 1.0, 1.0, 6000)
+    assert np.abs(ph_w - ph_e).max() < 2e-3
+
+
+def test_laplace_law(orc):
+    """Static 2D droplets: dp = sigma / R with sigma = sqrt(8 kappa A / 9);
+    the slope of dp against 1/R_eff is sigma within 5%."""
+    A = kappa = 0.04
+    sig = np.sqrt(8 * kappa * A / 9)
+    inv_r, dps = [], []
+    for R in (8, 12, 16, 20):
+        N = max(48, 4 * R)
+        o = orc.Oracle(0, orc.PERIODIC, N, N, 1, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
+        o.init_droplet((N - 1) / 2, (N - 1) / 2, 0, R)
+        o.step(12000)
+        ob = o.observables()
+        ph = o.fields()["phi"]
+        out, inn = ph[0, 0, 0], ph[0, N // 2, N // 2]
+        area = np.sum((ph - out) / (inn - out))
+        inv_r.append(1 / np.sqrt(area / np.pi))
+        dps.append(ob["dp"])
+        assert ob["status"] == 0 and ob["max_u"] < 1e-4
+    slope = np.polyfit(inv_r, dps, 1)[0]
+    assert abs(slope / sig - 1) < 0.05
+
+
+# ----------------------------------------------------------- conservation
+
+@pytest.mark.parametrize("lattice,shape,R", [(0, (1, 24, 48), 6.0), (1, (8, 12, 16), 3.5)])
+def test_conservation_shear(orc, lattice, shape, R):
+    """Sum rho and sum phi are collision invariants (Eq. feq, Eq. Fi, Eq. geq)
+    and the flat-wall moving bounce-back terms cancel per node: relative
+    drift < 1e-12 over 10^4 steps in the shear device."""
+    nz, ny, nx = shape
+    o = orc.Oracle(lattice, orc.SHEAR, nx, ny, nz, 1.0, 1.0, 0.04, 0.04, 1.0, 0.02, 1.0)
+    o.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, R)
+    a = o.observables()
+    o.step(10000)
+    b = o.observables()
+    n = nx * ny * nz
+    assert b["status"] == 0
+    assert abs(b["mass"] - a["mass"]) / a["mass"] < 1e-12
+    assert abs(b["phi_sum"] - a["phi_sum"]) / n < 1e-12
+
+
+# -------------------------------------------------------- single phase flow
+
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 16, 4)), (1, (3, 12, 4))])
+def test_couette_between_moving_walls(orc, lattice, shape):
+    """Walls at y = -1/2 and y = ny - 1/2 moving at -u_w and +u_w: from rest,
+    the flow converges to the exact linear profile u_w (2(y+1/2)/ny - 1),
+    which half-way bounce-back with the moving-wall term reproduces exactly."""
+    nz, ny, nx = shape
+    uw = 0.02
+    o = orc.Oracle(lattice, orc.SHEAR, nx, ny, nz, 0.8, 1.0, 0.0, 0.0, 1.0, uw, 1.0)
+    one = np.ones(shape)
+    zero = np.zeros(shape)
+    o.init_fields(one, zero, zero, zero, -one)
+    o.step(12000)
+    fl = o.fields()
+    y = np.arange(ny)
+    want = uw * (2 * (y + 0.5) / ny - 1)
+    assert np.abs(fl["ux"] - want[None, :, None]).max() < 1e-10
+    assert np.abs(fl["uy"]).max() < 1e-12
+    assert np.abs(fl["rho"] - 1).max() < 1e-10
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.3])
+def test_shear_wave_viscosity(orc, tau):
+    """nu = cs^2 (tau - 1/2) (Sec. 2.2): a transverse wave u_y = U sin(k x)
+    decays like exp(-nu k^2 t)."""
+    L = 64
+    o = orc.Oracle(0, orc.PERIODIC, L, 2, 1, tau, 1.0, 0.0, 0.0, 1.0, 0.0, 1.0)
+    x = np.arange(L)
+    k = 2 * np.pi / L
+    shape = (1, 2, L)
+    uy = np.broadcast_to(1e-4 * np.sin(k * x), shape).copy()
+    z = np.zeros(shape)
+    o.init_fields(np.ones(shape), z, uy, z, -np.ones(shape))
+    o.step(100)
+    a1 = np.abs(np.fft.rfft(o.fields()["uy"][0, 0])[1])
+    o.step(1000)
+    a2 = np.abs(np.fft.rfft(o.fields()["uy"][0, 0])[1])
+    nu = np.log(a1 / a2) / (k * k * 1000)
+    assert abs(nu / (CS2 * (tau - 0.5)) - 1) < 5e-3
+
+
+# ---------------------------------------------------------------- rollers
+
+def test_four_roller_extension(orc):
+    """Four-roller device: the rotation senses make a planar extensional flow
+    at the centre, stretching along x and compressing along y, mirror
+    symmetric about both centre lines; fluid next to a roller moves with its
+    surface."""
+    N = 64
+    uw = 0.01
+    o = orc.Oracle(0, orc.FOUR_ROLLER, N, N, 1, 1.0, 1.0, 0.0, 0.0, 1.0, uw, 1.0)
+    solid = o.solid_mask()[0]
+    # staircase discs of radius N/8
+    assert abs(solid.sum() / (4 * np.pi * (N / 8) ** 2) - 1) < 0.05
+    shape = (1, N, N)
+    z = np.zeros(shape)
+    o.init_fields(np.ones(shape), z, z, z, -np.ones(shape))
+    o.step(4000)
+    fl = o.fields()
+    ux, uy = fl["ux"][0], fl["uy"][0]
+    # mirror symmetry: x -> N-1-x flips u_x, y -> N-1-y flips u_y
+    assert np.abs(ux + ux[:, ::-1]).max() < 1e-12
+    assert np.abs(ux - ux[::-1, :]).max() < 1e-12
+    assert np.abs(uy + uy[::-1, :]).max() < 1e-12
+    c = N // 2
+    dudx = (ux[c, c + 2] - ux[c, c - 3]) / 5
+    dvdy = (uy[c + 2, c] - uy[c - 3, c]) / 5
+    assert dudx > 0 and dvdy < 0
+    assert abs(dudx + dvdy) < 0.1 * dudx  # nearly divergence free
+    # tangential speed at fluid nodes touching the top-right roller
+    rc = np.array([(N - 1) / 2 + N / 4, (N - 1) / 2 + N / 4])
+    speeds = []
+    for yy in range(N):
+        for xx in range(N):
+            if solid[yy, xx]:
+                continue
+            r = np.array([xx, yy]) - rc
+            dist = np.hypot(*r)
+            if N / 8 < dist <= N / 8 + 1:
+                t = np.array([-r[1], r[0]]) / dist  # counter-clockwise tangent
+                speeds.append(ux[yy, xx] * t[0] + uy[yy, xx] * t[1])
+    speeds = np.array(speeds)
+    assert speeds.mean() > 0.6 * uw and speeds.mean() < 1.05 * uw
+
+
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 12, 4)), (1, (3, 10, 4))])
+def test_couette_order_parameter_wall_term(orc, lattice, shape):
+    """With A = kappa = 0, a uniform phi0 and tau_g = tau_f, Eq. geq is
+    phi0 f_eq(rho=1, u) + phi0 (delta_i0 - w_i).  In steady Couette flow
+    (rho = 1) g = phi0 f + phi0 (delta_i0 - w_i) is then the steady state
+    exactly when the moving-wall term of g carries phi at the wall the way
+    the term of f carries rho0; without it (or with rho0 in its place) the
+    wall rows differ."""
+    nz, ny, nx = shape
+    phi0 = 0.3
+    o = orc.Oracle(lattice, orc.SHEAR, nx, ny, nz, 0.9, 0.9, 0.0, 0.0, 1.0, 0.03, 1.0)
+    one, zero = np.ones(shape), np.zeros(shape)
+    o.init_fields(one, zero, zero, zero, phi0 * one)
+    o.step(15000)
+    f, g = o.populations()
+    _, w = _lat(orc, lattice)
+    e = phi0 * (np.eye(len(w))[0] - w)
+    assert np.abs(o.fields()["rho"] - 1).max() < 1e-11
+    assert np.abs(g - phi0 * f - e[:, None, None, None]).max() < 1e-11
+    assert np.abs(o.fields()["phi"] - phi0).max() < 1e-11
+
+
+def test_neutral_wall_half_droplet(orc):
+    """Stencil values behind a flat wall mirror the first fluid row, i.e.
+    d phi / dn = 0 at the half-way wall (90 degree contact angle).  A resting
+    droplet centred on the bottom wall then matches the upper half of a full
+    droplet in a periodic box of twice the height, whose mirror line is the
+    wall position y = -1/2."""
+    N, R, steps = 48, 10.0, 3000
+    A = kappa = 0.04
+    half = orc.Oracle(0, orc.SHEAR, N, N // 2, 1, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
+    half.init_droplet((N - 1) / 2, -0.5, 0, R)
+    full = orc.Oracle(0, orc.PERIODIC, N, N, 1, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
+    full.init_droplet((N - 1) / 2, N / 2 - 0.5, 0, R)
+    half.step(steps)
+    full.step(steps)
+    ph = half.fields()["phi"][0]
+    pf = full.fields()["phi"][0, N // 2:, :]
+    assert np.abs(ph - pf).max() < 2e-3
+    # not vacuous: the droplet still touches the wall
+    assert ph[0, N // 2] > 0.9
