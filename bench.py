@@ -1,0 +1,387 @@
+"""Benchmark of the two-lattice free energy LBM step on GB300.
+
+Workload (default): D3Q19 parallel-band shear, 512x256x256 nodes (33.5M),
+droplet R = 48 centred, A = kappa = 0.04, tau_f = tau_g = 2, Gamma = 0.5,
+u_wall = 0.03, FP32 populations; the FP16/BF16 deviation stores are timed on
+the same lattice.  One "step" = one time step of the whole lattice (phi pass,
+mu pass, fused pull + collide of f and g).  Metric: MLUPS (million lattice
+node updates per second, higher is better).  The state (10.6 GB for FP32) is
+far larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU): every rank advances its own independent
+lattice (weak scaling, no collective on the data path); value = total MLUPS.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 FRE-LBM MLUPS & %HBM peak; FP16-store vs FP32; batched p50/p99 latency"
+WORKLOAD = dict(lattice="d3q19", device="shear", nx=512, ny=256, nz=256, tau_f=2.0, tau_g=2.0,
+                A=0.04, kappa=0.04, gamma_mob=0.5, u_wall=0.03, rho0=1.0)
+DROPLET = (255.5, 127.5, 127.5, 48.0)
+# algorithmic bytes per node update: read + write of f and g once (q = 19)
+ALG_BYTES = {"fp32": 2 * 2 * 19 * 4, "fp16dev": 2 * (19 * 2 + 18 * 2 + 4),
+             "bf16dev": 2 * (19 * 2 + 18 * 2 + 4), "fp64": 2 * 2 * 19 * 8}
+KERNEL_SRC = os.path.join(ROOT, "paper_2212_01617_gb300", "csrc", "fre_kernels.cuh")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def ncu_traffic(precision: str):
+    """DRAM bytes per launch of the update kernel from the committed ncu summary,
+    or None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "k_update_d3q19_dram.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        if d.get("kernel_sha") != kernel_hash():
+            return None
+        e = d["per_precision"][precision]
+        return float(e["dram_bytes_per_node"]) * WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"]
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(r[0] for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(fre, precision, steps, warmup, ws, local):
+    """Kernel-only timing of `steps` time steps with inputs resident in HBM."""
+    import torch
+    n = WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"]
+    sim = fre.Simulation(precision=precision, **WORKLOAD)
+    sim.init_droplet(*DROPLET)
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ms_phi, ms_mu, ms_upd, ms_tot, launches = sim.step_timed(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ws, ms)
+    obs = sim.observables()
+    sim.close()
+    return dict(ms=ms_max, ms_local=ms, ms_phi=ms_phi, ms_mu=ms_mu, ms_update=ms_upd, ms_seq=ms_tot,
+                launches=launches, clocks=clk, obs=obs, n=n)
+
+
+def time_e2e(fre, precision, steps, obs_every=100):
+    """End to end through the public C API with host buffers: upload of the
+    initial fields from pinned host memory, `steps` time steps, observables
+    read back to the host every `obs_every` steps and at the end."""
+    import numpy as np
+    import torch
+    nx, ny, nz = WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"]
+    n = nx * ny * nz
+    cx, cy, cz, R = DROPLET
+    xi = (WORKLOAD["kappa"] / WORKLOAD["A"]) ** 0.5
+    host = {k: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for k in
+            ("rho", "ux", "uy", "uz", "phi")}
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2).reshape(-1)
+    host["phi"][:] = np.tanh((R - r) / (np.sqrt(2.0) * xi))
+    host["rho"][:] = WORKLOAD["rho0"]
+    host["ux"][:] = (WORKLOAD["u_wall"] * (2.0 * (y + 0.5) / ny - 1.0)).reshape(-1)
+    host["uy"][:] = 0.0
+    host["uz"][:] = 0.0
+    del x, y, z, r
+    sim = fre.Simulation(precision=precision, **WORKLOAD)
+    # one untimed pass allocates the I/O staging buffer of the context
+    sim.init_fields(host["rho"], host["ux"], host["uy"], host["uz"], host["phi"])
+    sim.step(2)
+    sim.observables()
+    torch.cuda.synchronize()
+    reads = 0
+    t0 = time.perf_counter()
+    sim.init_fields(host["rho"], host["ux"], host["uy"], host["uz"], host["phi"])
+    done = 0
+    while done < steps:
+        k = min(obs_every, steps - done)
+        sim.step(k)
+        done += k
+        sim.observables()
+        reads += 1
+    t1 = time.perf_counter()
+    sim.close()
+    obs_bytes = 8 * 22 + 8 + 8
+    return dict(value=n * steps / (t1 - t0) / 1e6, unit="MLUPS",
+                h2d_bytes_per_step=5 * 8 * n / steps, d2h_bytes_per_step=reads * obs_bytes / steps,
+                obs_every=obs_every, seconds=t1 - t0)
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    nx, ny, nz = 64, 32, 32
+    scale = nx / WORKLOAD["nx"]
+    w = WORKLOAD
+    o = oracle.Oracle(oracle.D3Q19, oracle.SHEAR, nx, ny, nz, w["tau_f"], w["tau_g"], w["A"], w["kappa"],
+                      w["gamma_mob"], w["u_wall"], w["rho0"])
+    o.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, DROPLET[3] * scale)
+    o.step(2)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(10)
+        steps += 10
+    dt = time.perf_counter() - t0
+    return {"value": nx * ny * nz * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"D3Q19 shear {nx}x{ny}x{nz} (1/8-scale twin, droplet R={DROPLET[3] * scale:g}), "
+                      f"FP64, {steps} steps in {dt:.1f} s"}
+
+
+def base_config(precision):
+    return {"workload": "D3Q19 two-lattice FRE-LBM, parallel-band shear 512x256x256 (33.5M nodes), "
+                        "droplet R=48, A=kappa=0.04, tau=2, Gamma=0.5, u_w=0.03",
+            "lattice": "D3Q19", "nodes": WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"],
+            "shape": [WORKLOAD["nx"], WORKLOAD["ny"], WORKLOAD["nz"]], "precision": precision,
+            "l2": "inputs larger than L2 (10.6 GB FP32 state vs 129 MB L2); no flush",
+            "parallelism": "independent lattice per GPU (replicas)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    nx, ny, nz = 64, 32, 32
+    scale = nx / WORKLOAD["nx"]
+    w = WORKLOAD
+    o = oracle.Oracle(oracle.D3Q19, oracle.SHEAR, nx, ny, nz, w["tau_f"], w["tau_g"], w["A"], w["kappa"],
+                      w["gamma_mob"], w["u_wall"], w["rho0"])
+    o.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, DROPLET[3] * scale)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    n = nx * ny * nz
+    value = n * args.steps / dt / 1e6
+    sample = (f"each step: one FP64 oracle time step of the 1/8-scale twin {nx}x{ny}x{nz} "
+              f"(droplet R={DROPLET[3] * scale:g}) on the host cores")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": base_config("fp64"),
+            "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precisions", default="fp32,fp16dev,bf16dev")
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        return run_reference(args, ws, rank)
+
+    import torch
+    ws, rank, local = dist_setup()
+    import paper_2212_01617_gb300 as fre
+    fre.load_library()
+
+    precisions = [p for p in args.precisions.split(",") if p]
+    runs = {}
+    for prec in precisions:
+        runs[prec] = time_steps(fre, prec, args.steps, args.warmup, ws, local)
+        r = runs[prec]
+        log(f"[rank {rank}] {prec}: {r['ms'] / args.steps:.3f} ms/step, "
+            f"{r['n'] * args.steps / (r['ms'] * 1e-3) / 1e6:.0f} MLUPS per GPU, update "
+            f"{r['ms_update'] / args.steps:.3f} ms, phi {r['ms_phi'] / args.steps:.3f} ms, "
+            f"mu {r['ms_mu'] / args.steps:.3f} ms, D={r['obs']['D']:.4f}")
+    main_prec = precisions[0]
+    r = runs[main_prec]
+    n = r["n"]
+    value = ws * n * args.steps / (r["ms"] * 1e-3) / 1e6
+    peak, peak_src = measured_peak_gbs()
+    t_upd = r["ms_update"] / args.steps * 1e-3
+    achieved = ALG_BYTES[main_prec] * n / t_upd / 1e9
+    traffic = ncu_traffic(main_prec)
+    step_achieved = ALG_BYTES[main_prec] * n / (r["ms"] / args.steps * 1e-3) / 1e9
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = time_e2e(fre, main_prec, args.e2e_steps)
+        e2e["value"] *= ws  # every rank ran the same job on its own GPU
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        variants = {}
+        for prec, rr in runs.items():
+            t = rr["ms_update"] / args.steps * 1e-3
+            variants[prec] = {
+                "mlups": ws * rr["n"] * args.steps / (rr["ms"] * 1e-3) / 1e6,
+                "ms_per_step": rr["ms"] / args.steps,
+                "update_ms": rr["ms_update"] / args.steps, "phi_ms": rr["ms_phi"] / args.steps,
+                "mu_ms": rr["ms_mu"] / args.steps,
+                "update_alg_gbs": ALG_BYTES[prec] * rr["n"] / t / 1e9,
+                "update_frac_of_measured_hbm": ALG_BYTES[prec] * rr["n"] / t / 1e9 / peak,
+                "step_alg_frac_of_measured_hbm": ALG_BYTES[prec] * rr["n"] / (rr["ms"] / args.steps * 1e-3)
+                / 1e9 / peak,
+                "D_after_run": rr["obs"]["D"], "mass": rr["obs"]["mass"],
+            }
+        if "fp32" in runs and "fp16dev" in runs:
+            variants["fp16dev_speedup_vs_fp32"] = variants["fp16dev"]["mlups"] / variants["fp32"]["mlups"]
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if main_prec == "fp32" else ("f16-store/f32" if main_prec == "fp16dev" else main_prec),
+            "data": "synthetic", "config": base_config(main_prec),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": f"k_update<19,{main_prec},pull> (fused pull + collide of f and g)",
+                         "algorithmic_bytes_per_launch": ALG_BYTES[main_prec] * n,
+                         "peak_source": peak_src,
+                         "step_achieved": step_achieved, "step_frac": step_achieved / peak},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * fre.h -- C ABI of the GB300 (sm_103a) two-lattice free energy lattice
+ * Boltzmann update (Simonis et al., arXiv:2212.01617).
+ *
+ * One context holds one simulation: the momentum populations f (Eq. LBE) and
+ * the order-parameter populations g (Eq. LBEg) on a D2Q9 or D3Q19 lattice,
+ * resident in device memory, plus the auxiliary phi and mu fields.  Each
+ * time step (fre_step) runs, on the device and in the paper's order
+ * (Algorithm 1, Sec. 2.3):
+ *   rho = sum f_i, phi = sum g_i            (Eq. densMoment, Eq. ordeMoment)
+ *   mu  = A(phi^3 - phi) - kappa lap(phi)   (Eq. mu_phi, kappa_1 = kappa_2,
+ *                                            rho = 1; isotropic stencil)
+ *   F   = -phi grad(mu)                     (Eq. F without the rho term;
+ *                                            evaluated as mu grad(phi) -
+ *                                            grad(phi mu))
+ *   u   = (sum c_i f_i + F/2) / rho         (Eq. veloMoment)
+ *   BGK + Guo for f, BGK for g              (Eq. bgk, Eq. feq, Eq. Fi,
+ *                                            Eq. geq, Eq. LBEg)
+ *   streaming with half-way bounce-back and the moving-wall term at solid
+ *   sources (Sec. 2.3, "standard LBM boundary methods").
+ *
+ * Conventions shared by every entry point:
+ *   - node index n = (z*ny + y)*nx + x, x fastest; D2Q9 has nz = 1;
+ *   - host population arrays are FP64 [q][n] in this direction order
+ *       D2Q9 : 0 (0,0); 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1); 5 (1,1);
+ *              6 (-1,1); 7 (-1,-1); 8 (1,-1)
+ *       D3Q19: 0 rest; 1 (1,0,0); 2 (-1,0,0); 3 (0,1,0); 4 (0,-1,0);
+ *              5 (0,0,1); 6 (0,0,-1); 7 (1,1,0); 8 (-1,-1,0); 9 (1,0,1);
+ *              10 (-1,0,-1); 11 (0,1,1); 12 (0,-1,-1); 13 (1,-1,0);
+ *              14 (-1,1,0); 15 (1,0,-1); 16 (-1,0,1); 17 (0,1,-1);
+ *              18 (0,-1,1)
+ *     and hold the PRE-collision populations f(x,t), g(x,t);
+ *   - host pointers are owned by the caller and only read/written during the
+ *     call; all device memory is owned by the context;
+ *   - every call returns a fre_status and never aborts; fre_last_error()
+ *     gives a human-readable message for the last failure of this thread;
+ *   - calls on one context must not overlap (one host thread at a time);
+ *     the work is issued on the context's CUDA stream.
+ */
+#ifndef FRE_H
+#define FRE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FRE_OK = 0,
+    FRE_ERR_ARG = 1,       /* invalid argument (checked before any work) */
+    FRE_ERR_OOM = 2,       /* device allocation failed */
+    FRE_ERR_CUDA = 3,      /* a CUDA call failed; the context is unusable */
+    FRE_ERR_UNSTABLE = 4,  /* non-finite values or |u| > 0.3 were found */
+    FRE_ERR_BUDGET = 5,    /* admission refused: device-memory budget */
+    FRE_ERR_STATE = 6      /* call not valid in the current state */
+} fre_status;
+
+typedef enum { FRE_D2Q9 = 0, FRE_D3Q19 = 1 } fre_lattice;
+
+/* Storage of the populations on the device.  FP64 and FP32 store f_i and
+ * g_i as is and compute in the same precision.  FP16DEV and BF16DEV store
+ * f_i - w_i rho0 and g_i (i != 0) in 16 bits (round to nearest even), keep
+ * g_0 in FP32 and compute in FP32. */
+typedef enum { FRE_FP64 = 0, FRE_FP32 = 1, FRE_FP16DEV = 2, FRE_BF16DEV = 3 } fre_precision;
+
+/* FRE_SHEAR: Taylor's parallel-band device (Sec. 3.1): walls at y = -1/2
+ *   (moving at -u_wall in x) and y = ny - 1/2 (moving at +u_wall), periodic
+ *   in x and z.
+ * FRE_FOUR_ROLLER: Taylor's four-roller device (Sec. 3.2): four staircase
+ *   cylinders (axis z) of radius nx/8 centred at ((nx-1)/2 +- nx/4,
+ *   (ny-1)/2 +- ny/4) with surface speed u_wall, top-right and bottom-left
+ *   counter-clockwise, the others clockwise, so the centre sees extension
+ *   along x; periodic outer box.
+ * FRE_PERIODIC: fully periodic box (no walls). */
+typedef enum { FRE_SHEAR = 0, FRE_FOUR_ROLLER = 1, FRE_PERIODIC = 2 } fre_device;
+
+typedef struct {
+    int lattice;       /* fre_lattice */
+    int precision;     /* fre_precision */
+    int device;        /* fre_device */
+    int nx, ny, nz;    /* lattice nodes; nz = 1 for D2Q9; each >= 1 */
+    double tau_f;      /* relaxation time of f, > 0.5 (Eq. bgk) */
+    double tau_g;      /* relaxation time of g, > 0.5 (Eq. LBEg) */
+    double A;          /* bulk free-energy coefficient, >= 0 */
+    double kappa;      /* gradient free-energy coefficient, >= 0 */
+    double gamma_mob;  /* mobility parameter Gamma (Eq. geq), M = Gamma (tau_g - 1/2) */
+    double u_wall;     /* wall (shear) or roller surface (four-roller) speed */
+    double rho0;       /* reference density; also the wall density of the
+                          moving bounce-back term */
+} fre_params;
+
+/* Observables of the state at the current step, from the pre-collision
+ * populations; sums in FP64 over fluid nodes. */
+typedef struct {
+    double mass;         /* sum rho */
+    double phi_sum;      /* sum phi */
+    double volume;       /* sum (1 + phi)/2, the amount of component C1 */
+    double drop_weight;  /* W = sum over phi > 0 of (1 + phi)/2 */
+    double drop_count;   /* number of nodes with phi > 0 */
+    double centroid[3];  /* sum w x / W over phi > 0, w = (1 + phi)/2 */
+    double I[6];         /* central second moments xx yy zz xy xz yz, / W */
+    double D;            /* deformation (L - B)/(L + B) of the x-y moment ellipse */
+    double theta_deg;    /* inclination of its long axis to x, degrees */
+    double p_centre;     /* cs^2 rho + phi mu - (A/4)(phi^2 - 1)^2 at the
+                            node nearest the centroid */
+    double p_far;        /* same at the node half a period away in x (and z) */
+    double dp;           /* p_centre - p_far (Laplace pressure) */
+    double max_u;        /* max |u| */
+    long long step;      /* time steps taken since the last initialisation */
+    int status;          /* 0 ok, 1 non-finite value seen, 2 |u| > 0.3 */
+} fre_obs;
+
+typedef struct fre_ctx fre_ctx;
+
+/* Device bytes a context with these parameters allocates (populations in
+ * two buffers, phi/mu fields, geometry, reduction scratch); 0 if invalid. */
+size_t fre_device_bytes(const fre_params *p);
+
+/* Create a context.  cuda_stream is a cudaStream_t (NULL: the context
+ * creates its own non-blocking stream).  Validates tau_f, tau_g > 1/2
+ * (Eq. bgk, Eq. LBEg), sizes >= 1, nz = 1 for D2Q9, known enums; allocates
+ * all device memory with cudaMalloc.  On failure *out is NULL. */
+fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out);
+
+/* Initialise a droplet phi = tanh((R - |x - c|)/(sqrt(2) xi)), xi =
+ * sqrt(kappa/A) (the planar profile of Sec. 2.2 applied radially), rho =
+ * rho0, u = the Couette profile u_x = u_wall (2(y + 1/2)/ny - 1) for the
+ * shear device and 0 otherwise, mu from phi, and f = f_eq, g = g_eq
+ * (Sec. 2.3).  In 2D cz is ignored.  Needs A > 0, kappa > 0, R > 0. */
+fre_status fre_init_droplet(fre_ctx *c, double cx, double cy, double cz, double R);
+
+/* Initialise from host FP64 fields (n values each; uz may be NULL in 2D):
+ * mu from phi, f = f_eq(rho, u), g = g_eq(phi, mu, u).  Values at solid
+ * nodes are ignored. */
+fre_status fre_init_fields(fre_ctx *c, const double *rho, const double *ux,
+                           const double *uy, const double *uz, const double *phi);
+
+/* Replace the state by host FP64 pre-collision populations [q][n]; the step
+ * counter restarts at 0.  16-bit formats round them to their storage. */
+fre_status fre_load_populations(fre_ctx *c, const double *f, const double *g);
+
+/* Copy the pre-collision populations of the current step to host FP64
+ * arrays [q][n] (either pointer may be NULL); solid nodes read 0. */
+fre_status fre_store_populations(fre_ctx *c, double *f, double *g);
+
+/* Advance nsteps >= 0 time steps; asynchronous on the context stream. */
+fre_status fre_step(fre_ctx *c, int nsteps);
+
+/* fre_step with per-kernel device timing: CUDA events are recorded on the
+ * context stream before and after each kernel of every step.  ms[0], ms[1],
+ * ms[2] receive the summed milliseconds of the phi, mu (including the roller
+ * stencil passes) and fused update kernels, ms[3] the whole sequence;
+ * launches[0] (if not NULL) the number of kernels launched.  Synchronises. */
+fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launches);
+
+/* Macroscopic fields of the current step into host FP64 arrays of n values
+ * (any pointer may be NULL); solid nodes read 0.  Synchronises. */
+fre_status fre_copy_fields(fre_ctx *c, double *rho, double *ux, double *uy,
+                           double *uz, double *phi, double *mu);
+
+/* Observables of the current step (FP64 device reductions); synchronises.
+ * Returns FRE_ERR_UNSTABLE (with *out filled) when out->status != 0. */
+fre_status fre_observables(fre_ctx *c, fre_obs *out);
+
+/* Steps taken since the last initialisation. */
+long long fre_step_count(const fre_ctx *c);
+
+/* Destroy a context and free its device memory; NULL-safe. */
+void fre_destroy(fre_ctx *c);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *fre_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRE_H */

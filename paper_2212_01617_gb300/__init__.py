@@ -1,0 +1,20 @@
+"""GB300 (sm_103a) two-lattice free energy lattice Boltzmann update.
+
+A C-ABI CUDA library (``libfre.so``, declared in ``include/fre.h``) that
+advances binary-mixture flows with the free energy LBM of Simonis et al.,
+arXiv:2212.01617 (Sec. 2.2-2.3, Algorithm 1) on D2Q9 and D3Q19 lattices, in
+the parallel-band shear and four-roller devices (Sec. 3), plus this thin
+Python binding.  ``build.build()`` compiles the library in-tree.
+"""
+from .binding import (  # noqa: F401
+    EXPORTS, FreError, Simulation, fre_copy_fields, fre_create, fre_destroy, fre_device_bytes,
+    fre_init_droplet, fre_init_fields, fre_last_error, fre_load_populations, fre_observables,
+    fre_params, fre_step, fre_step_count, fre_step_timed, fre_store_populations, load_library, make_params,
+)
+
+__all__ = [
+    "EXPORTS", "FreError", "Simulation", "fre_copy_fields", "fre_create", "fre_destroy",
+    "fre_device_bytes", "fre_init_droplet", "fre_init_fields", "fre_last_error",
+    "fre_load_populations", "fre_observables", "fre_params", "fre_step", "fre_step_count", "fre_step_timed",
+    "fre_store_populations", "load_library", "make_params",
+]

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in include/fre.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; all the
+computation runs in the CUDA library libfre.so.  There is no CPU fallback: if
+the library is missing or no GPU is visible, the calls raise.
+
+PyTorch supplies the CUDA stream (``torch.cuda.current_stream()``) when it is
+importable; the library owns the device memory of each context.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libfre.so")
+
+FRE_OK, FRE_ERR_ARG, FRE_ERR_OOM, FRE_ERR_CUDA, FRE_ERR_UNSTABLE, FRE_ERR_BUDGET, FRE_ERR_STATE = range(7)
+FRE_D2Q9, FRE_D3Q19 = 0, 1
+FRE_FP64, FRE_FP32, FRE_FP16DEV, FRE_BF16DEV = 0, 1, 2, 3
+FRE_SHEAR, FRE_FOUR_ROLLER, FRE_PERIODIC = 0, 1, 2
+
+PRECISIONS = {"fp64": FRE_FP64, "fp32": FRE_FP32, "fp16dev": FRE_FP16DEV, "bf16dev": FRE_BF16DEV}
+LATTICES = {"d2q9": FRE_D2Q9, "d3q19": FRE_D3Q19}
+DEVICES = {"shear": FRE_SHEAR, "four_roller": FRE_FOUR_ROLLER, "periodic": FRE_PERIODIC}
+
+# every entry point declared in include/fre.h
+EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_fields",
+           "fre_load_populations", "fre_store_populations", "fre_step", "fre_step_timed",
+           "fre_copy_fields", "fre_observables", "fre_step_count", "fre_destroy", "fre_last_error"]
+
+
+class FreError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[fre status {status}] {msg}")
+        self.status = status
+
+
+class fre_params(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("precision", C.c_int), ("device", C.c_int),
+                ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("tau_f", C.c_double), ("tau_g", C.c_double), ("A", C.c_double),
+                ("kappa", C.c_double), ("gamma_mob", C.c_double), ("u_wall", C.c_double),
+                ("rho0", C.c_double)]
+
+
+class fre_obs(C.Structure):
+    _fields_ = [("mass", C.c_double), ("phi_sum", C.c_double), ("volume", C.c_double),
+                ("drop_weight", C.c_double), ("drop_count", C.c_double),
+                ("centroid", C.c_double * 3), ("I", C.c_double * 6),
+                ("D", C.c_double), ("theta_deg", C.c_double),
+                ("p_centre", C.c_double), ("p_far", C.c_double), ("dp", C.c_double),
+                ("max_u", C.c_double), ("step", C.c_longlong), ("status", C.c_int)]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfre.so and declare the signatures; raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FreError(FRE_ERR_STATE, f"CUDA library {path} is not built; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        dp = C.POINTER(C.c_double)
+        vp = C.c_void_p
+        L.fre_device_bytes.restype = C.c_size_t
+        L.fre_device_bytes.argtypes = [C.POINTER(fre_params)]
+        L.fre_create.argtypes = [C.POINTER(fre_params), vp, C.POINTER(vp)]
+        L.fre_init_droplet.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double]
+        L.fre_init_fields.argtypes = [vp, dp, dp, dp, dp, dp]
+        L.fre_load_populations.argtypes = [vp, dp, dp]
+        L.fre_store_populations.argtypes = [vp, dp, dp]
+        L.fre_step.argtypes = [vp, C.c_int]
+        L.fre_step_timed.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_longlong)]
+        L.fre_copy_fields.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+        L.fre_observables.argtypes = [vp, C.POINTER(fre_obs)]
+        L.fre_step_count.restype = C.c_longlong
+        L.fre_step_count.argtypes = [vp]
+        L.fre_destroy.argtypes = [vp]
+        L.fre_destroy.restype = None
+        L.fre_last_error.restype = C.c_char_p
+        for name in ("fre_create", "fre_init_droplet", "fre_init_fields", "fre_load_populations",
+                     "fre_store_populations", "fre_step", "fre_step_timed", "fre_copy_fields",
+                     "fre_observables"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def _check(status: int, what: str):
+    if status != FRE_OK:
+        msg = load_library().fre_last_error().decode(errors="replace")
+        raise FreError(status, f"{what}: {msg}")
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def current_stream_handle():
+    """cudaStream_t of torch's current stream (None without torch/CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def make_params(lattice="d2q9", precision="fp64", device="shear", nx=16, ny=8, nz=1,
+                tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0,
+                rho0=1.0) -> fre_params:
+    lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    dev = DEVICES[device] if isinstance(device, str) else int(device)
+    return fre_params(lat, prec, dev, int(nx), int(ny), int(nz), float(tau_f), float(tau_g),
+                      float(A), float(kappa), float(gamma_mob), float(u_wall), float(rho0))
+
+
+# --------------------------------------------------- one call per C entry point
+
+def fre_device_bytes(p: fre_params) -> int:
+    return int(load_library().fre_device_bytes(C.byref(p)))
+
+
+def fre_create(p: fre_params, stream=None) -> int:
+    h = C.c_void_p()
+    s = stream if stream is not None else current_stream_handle()
+    _check(load_library().fre_create(C.byref(p), C.c_void_p(s) if s else None, C.byref(h)), "fre_create")
+    return h.value
+
+
+def fre_init_droplet(h, cx, cy, cz, R):
+    _check(load_library().fre_init_droplet(h, cx, cy, cz, R), "fre_init_droplet")
+
+
+def fre_init_fields(h, rho, ux, uy, uz, phi):
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+            for a in (rho, ux, uy, uz, phi)]
+    _check(load_library().fre_init_fields(h, *[_dptr(a) for a in arrs]), "fre_init_fields")
+
+
+def fre_load_populations(h, f, g):
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+    _check(load_library().fre_load_populations(h, _dptr(f), _dptr(g)), "fre_load_populations")
+
+
+def fre_store_populations(h, f=None, g=None):
+    _check(load_library().fre_store_populations(h, _dptr(f), _dptr(g)), "fre_store_populations")
+
+
+def fre_step(h, nsteps: int):
+    _check(load_library().fre_step(h, int(nsteps)), "fre_step")
+
+
+def fre_step_timed(h, nsteps: int):
+    """Returns (ms_phi, ms_mu, ms_update, ms_total, kernel_launches)."""
+    ms = np.zeros(4)
+    nl = C.c_longlong(0)
+    _check(load_library().fre_step_timed(h, int(nsteps), _dptr(ms), C.byref(nl)), "fre_step_timed")
+    return float(ms[0]), float(ms[1]), float(ms[2]), float(ms[3]), int(nl.value)
+
+
+def fre_copy_fields(h, rho=None, ux=None, uy=None, uz=None, phi=None, mu=None):
+    _check(load_library().fre_copy_fields(h, *[_dptr(a) for a in (rho, ux, uy, uz, phi, mu)]),
+           "fre_copy_fields")
+
+
+def fre_observables(h, allow_unstable: bool = True) -> dict:
+    o = fre_obs()
+    s = load_library().fre_observables(h, C.byref(o))
+    if not (s == FRE_OK or (allow_unstable and s == FRE_ERR_UNSTABLE)):
+        _check(s, "fre_observables")
+    return o.as_dict()
+
+
+def fre_step_count(h) -> int:
+    return int(load_library().fre_step_count(h))
+
+
+def fre_destroy(h):
+    if h:
+        load_library().fre_destroy(h)
+
+
+def fre_last_error() -> str:
+    return load_library().fre_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------ convenience
+
+class Simulation:
+    """One context: owns its device memory until close()."""
+
+    def __init__(self, stream=None, **kw):
+        self.params = make_params(**kw)
+        self.q = 9 if self.params.lattice == FRE_D2Q9 else 19
+        self.shape = (self.params.nz, self.params.ny, self.params.nx)
+        self.n = self.params.nx * self.params.ny * self.params.nz
+        self.h = fre_create(self.params, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            fre_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init_droplet(self, cx, cy, cz, R):
+        fre_init_droplet(self.h, cx, cy, cz, R)
+
+    def init_fields(self, rho, ux, uy, uz, phi):
+        fre_init_fields(self.h, rho, ux, uy, uz, phi)
+
+    def load_populations(self, f, g):
+        fre_load_populations(self.h, f, g)
+
+    def populations(self):
+        f = np.zeros(self.q * self.n)
+        g = np.zeros(self.q * self.n)
+        fre_store_populations(self.h, f, g)
+        return f.reshape((self.q,) + self.shape), g.reshape((self.q,) + self.shape)
+
+    def step(self, nsteps: int = 1):
+        fre_step(self.h, nsteps)
+
+    def step_timed(self, nsteps: int = 1):
+        return fre_step_timed(self.h, nsteps)
+
+    def fields(self) -> dict:
+        out = {k: np.zeros(self.n) for k in ("rho", "ux", "uy", "uz", "phi", "mu")}
+        fre_copy_fields(self.h, *[out[k] for k in ("rho", "ux", "uy", "uz", "phi", "mu")])
+        return {k: v.reshape(self.shape) for k, v in out.items()}
+
+    def observables(self) -> dict:
+        return fre_observables(self.h)
+
+    @property
+    def steps_taken(self) -> int:
+        return fre_step_count(self.h)

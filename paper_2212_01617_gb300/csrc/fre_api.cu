@@ -1,0 +1,576 @@
+// Host runtime of the C ABI declared in include/fre.h: validation, device
+// memory, geometry, and the launch sequence of one time step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fre_internal.h"
+
+namespace fre {
+// scratch layout of the observables reduction (see fre_kernels.cuh)
+constexpr int kRedDoublesHost = 1024 * 16 + 32;
+}  // namespace fre
+
+struct fre_ctx {
+    fre_params p;
+    int q = 0;
+    int device_id = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    const fre::KernelSet *ks = nullptr;
+    fre::Geo G{};
+    fre::Phys P{};
+    fre::Buf buf[2]{};
+    void *phi[2]{};
+    void *mu = nullptr;
+    unsigned char *solid = nullptr;
+    int *ghost = nullptr;
+    int n_ghost = 0;
+    double *red = nullptr;
+    int red_blocks = 0;
+    fre_obs *obs_dev = nullptr;
+    fre_obs *obs_host = nullptr;
+    double *staging = nullptr;
+    std::vector<void *> allocs;
+    int cur = 0;        // buffer holding the state
+    int pp = 1;         // phi buffer holding phi of the previous step
+    bool local = true;  // state is pre-collision (no streaming pending)
+    bool initialised = false;
+    long long step = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+fre_status fail(fre_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define FRE_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(FRE_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Sizes {
+    int q, sz_store, sz_comp;
+    long long n, np;
+    size_t buf_bytes, field_bytes, solid_bytes;
+};
+
+bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
+    auto bad = [&](const char *m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (!p) return bad("params is NULL");
+    if (p->lattice != FRE_D2Q9 && p->lattice != FRE_D3Q19) return bad("unknown lattice");
+    if (p->precision < FRE_FP64 || p->precision > FRE_BF16DEV) return bad("unknown precision");
+    if (p->device < FRE_SHEAR || p->device > FRE_PERIODIC) return bad("unknown device");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bad("lattice sizes must be >= 1");
+    if (p->lattice == FRE_D2Q9 && p->nz != 1) return bad("D2Q9 needs nz = 1");
+    if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) return bad("tau_f and tau_g must be > 1/2");
+    if (!(p->A >= 0.0) || !(p->kappa >= 0.0)) return bad("A and kappa must be >= 0");
+    if (!std::isfinite(p->gamma_mob) || !std::isfinite(p->u_wall) || !(p->rho0 > 0.0))
+        return bad("gamma_mob and u_wall must be finite, rho0 > 0");
+    if (p->device == FRE_FOUR_ROLLER && (p->nx < 8 || p->ny < 8)) return bad("four-roller needs nx, ny >= 8");
+    long long n = (long long)p->nx * p->ny * p->nz;
+    if (n > (1LL << 31) - 1024) return bad("too many nodes (limit 2^31)");
+    s.q = p->lattice == FRE_D2Q9 ? 9 : 19;
+    s.n = n;
+    s.np = (n + 63) / 64 * 64;
+    s.sz_store = p->precision == FRE_FP64 ? 8 : (p->precision == FRE_FP32 ? 4 : 2);
+    s.sz_comp = p->precision == FRE_FP64 ? 8 : 4;
+    size_t plane = (size_t)s.np * s.sz_store;
+    if (p->precision == FRE_FP64 || p->precision == FRE_FP32) {
+        s.buf_bytes = 2 * (size_t)s.q * plane;
+    } else {
+        s.buf_bytes = (size_t)s.q * plane + (size_t)(s.q - 1) * plane + (size_t)s.np * 4;
+    }
+    s.field_bytes = (size_t)s.np * s.sz_comp;
+    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) : 0;
+    return true;
+}
+
+size_t total_bytes(const Sizes &s) {
+    return 2 * s.buf_bytes + 3 * s.field_bytes + s.solid_bytes + sizeof(double) * fre::kRedDoublesHost +
+           sizeof(fre_obs);
+}
+
+fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return FRE_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(FRE_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(*ptr);
+    e = cudaMemsetAsync(*ptr, 0, bytes, c->stream);
+    if (e != cudaSuccess) return fail(FRE_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    return FRE_OK;
+}
+
+// Four-roller geometry: roller id of every node and the solid nodes that
+// have a fluid stencil neighbour.
+void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<int> &ghost) {
+    const fre_params &p = c->p;
+    fre::Geo &G = c->G;
+    const double cx = 0.5 * (p.nx - 1), cy = 0.5 * (p.ny - 1);
+    const double ox = 0.25 * p.nx, oy = 0.25 * p.ny;
+    const double r = p.nx / 8.0;
+    const double om = p.u_wall / r;
+    const double xs[5] = {0, cx + ox, cx - ox, cx - ox, cx + ox};
+    const double ys[5] = {0, cy + oy, cy + oy, cy - oy, cy - oy};
+    const double ws[5] = {0, om, -om, om, -om};  // top right, top left, bottom left, bottom right
+    for (int k = 0; k < 5; ++k) {
+        G.rcx[k] = xs[k];
+        G.rcy[k] = ys[k];
+        G.om[k] = ws[k];
+    }
+    solid.assign((size_t)G.n, 0);
+    for (int z = 0; z < p.nz; ++z)
+        for (int y = 0; y < p.ny; ++y)
+            for (int x = 0; x < p.nx; ++x)
+                for (int k = 1; k <= 4; ++k) {
+                    double dx = x - xs[k], dy = y - ys[k];
+                    if (dx * dx + dy * dy <= r * r) {
+                        solid[((size_t)z * p.ny + y) * p.nx + x] = (unsigned char)k;
+                        break;
+                    }
+                }
+    const int q = c->q;
+    static const int c9[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+    static const int c19[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                   {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, 0, 1},
+                                   {-1, 0, -1}, {0, 1, 1},  {0, -1, -1}, {1, -1, 0}, {-1, 1, 0},
+                                   {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1}};
+    auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
+    ghost.clear();
+    for (int z = 0; z < p.nz; ++z)
+        for (int y = 0; y < p.ny; ++y)
+            for (int x = 0; x < p.nx; ++x) {
+                size_t n = ((size_t)z * p.ny + y) * p.nx + x;
+                if (!solid[n]) continue;
+                for (int j = 1; j < q; ++j) {
+                    const int *cj = q == 9 ? c9[j] : c19[j];
+                    size_t m = ((size_t)wrap(z + cj[2], p.nz) * p.ny + wrap(y + cj[1], p.ny)) * p.nx +
+                               wrap(x + cj[0], p.nx);
+                    if (!solid[m]) {
+                        ghost.push_back((int)n);
+                        break;
+                    }
+                }
+            }
+}
+
+fre::Launch launch_of(fre_ctx *c) {
+    fre::Launch L{};
+    L.G = c->G;
+    L.P = c->P;
+    L.src = c->buf[c->cur];
+    L.dst = c->buf[1 - c->cur];
+    L.phi_prev = c->phi[c->pp];
+    L.phi = c->phi[1 - c->pp];
+    L.mu = c->mu;
+    L.ghost = c->ghost;
+    L.n_ghost = c->n_ghost;
+    L.red = c->red;
+    L.red_blocks = c->red_blocks;
+    L.obs = c->obs_dev;
+    L.staging = c->staging;
+    L.stream = c->stream;
+    return L;
+}
+
+// phi and mu of the current state into phi[1 - pp] and mu.
+void current_phi_mu(fre_ctx *c, const fre::Launch &L) {
+    c->ks->phi(L, !c->local);
+    if (c->n_ghost) c->ks->ghost(L, L.phi);
+    c->ks->mu(L);
+    if (c->n_ghost) c->ks->ghost(L, L.mu);
+}
+
+fre_status check_launch(const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(FRE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+    return FRE_OK;
+}
+
+fre_status ensure_staging(fre_ctx *c) {
+    if (c->staging) return FRE_OK;
+    void *p = nullptr;
+    fre_status s = dev_alloc(c, &p, sizeof(double) * 6 * (size_t)c->G.n);
+    if (s != FRE_OK) return s;
+    c->staging = static_cast<double *>(p);
+    return FRE_OK;
+}
+
+fre_status enter(fre_ctx *c) {
+    if (!c) return fail(FRE_ERR_ARG, "context is NULL");
+    FRE_CUDA(cudaSetDevice(c->device_id));
+    return FRE_OK;
+}
+
+// phi field set -> ghosts -> mu -> ghosts -> equilibria into buffer 0
+fre_status finish_init(fre_ctx *c, int from_staging) {
+    c->cur = 0;
+    c->pp = 1;
+    fre::Launch L = launch_of(c);  // phi = phi[0], src = buf[0]
+    if (c->n_ghost) c->ks->ghost(L, L.phi);
+    c->ks->mu(L);
+    if (c->n_ghost) c->ks->ghost(L, L.mu);
+    c->ks->init_eq(L, from_staging);
+    fre_status s = check_launch("init");
+    if (s != FRE_OK) return s;
+    c->local = true;
+    c->initialised = true;
+    c->step = 0;
+    return FRE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fre_device_bytes(const fre_params *p) {
+    Sizes s;
+    if (!sizes_of(p, s, nullptr)) return 0;
+    return total_bytes(s);
+}
+
+fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
+    if (!out) return fail(FRE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    Sizes s;
+    std::string why;
+    if (!sizes_of(p, s, &why)) return fail(FRE_ERR_ARG, "fre_create: %s", why.c_str());
+    fre_ctx *c = new fre_ctx();
+    c->p = *p;
+    c->q = s.q;
+    auto bail = [&](fre_status st) {
+        fre_destroy(c);
+        return st;
+    };
+    if (cudaGetDevice(&c->device_id) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(FRE_ERR_CUDA, "fre_create: no CUDA device");
+    }
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return fail(FRE_ERR_CUDA, "fre_create: cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    c->ks = p->lattice == FRE_D2Q9 ? fre::kernels_d2q9(p->precision) : fre::kernels_d3q19(p->precision);
+    c->G.nx = p->nx;
+    c->G.ny = p->ny;
+    c->G.nz = p->nz;
+    c->G.device = p->device;
+    c->G.n = s.n;
+    c->G.np = s.np;
+    c->G.uwall = p->u_wall;
+    c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0};
+
+    const bool dev16 = p->precision == FRE_FP16DEV || p->precision == FRE_BF16DEV;
+    const size_t plane = (size_t)s.np * s.sz_store;
+    for (int b = 0; b < 2; ++b) {
+        void *ptr;
+        fre_status st = dev_alloc(c, &ptr, s.buf_bytes);
+        if (st != FRE_OK) return bail(st);
+        char *base = static_cast<char *>(ptr);
+        c->buf[b].f = base;
+        c->buf[b].g = base + (size_t)s.q * plane;
+        c->buf[b].g0 = dev16 ? reinterpret_cast<float *>(base + (size_t)(2 * s.q - 1) * plane) : nullptr;
+    }
+    for (int k = 0; k < 2; ++k) {
+        fre_status st = dev_alloc(c, &c->phi[k], s.field_bytes);
+        if (st != FRE_OK) return bail(st);
+    }
+    {
+        fre_status st = dev_alloc(c, &c->mu, s.field_bytes);
+        if (st != FRE_OK) return bail(st);
+        void *r;
+        st = dev_alloc(c, &r, sizeof(double) * fre::kRedDoublesHost);
+        if (st != FRE_OK) return bail(st);
+        c->red = static_cast<double *>(r);
+        void *o;
+        st = dev_alloc(c, &o, sizeof(fre_obs));
+        if (st != FRE_OK) return bail(st);
+        c->obs_dev = static_cast<fre_obs *>(o);
+    }
+    long long rb = (s.n + 255) / 256;
+    c->red_blocks = (int)(rb < 608 ? (rb < 1 ? 1 : rb) : 608);
+    if (cudaMallocHost(&c->obs_host, sizeof(fre_obs)) != cudaSuccess) {
+        cudaGetLastError();
+        c->obs_host = nullptr;
+        return bail(fail(FRE_ERR_OOM, "cudaMallocHost failed"));
+    }
+    if (p->device == FRE_FOUR_ROLLER) {
+        std::vector<unsigned char> solid;
+        std::vector<int> ghost;
+        build_rollers(c, solid, ghost);
+        void *d;
+        fre_status st = dev_alloc(c, &d, s.solid_bytes);
+        if (st != FRE_OK) return bail(st);
+        c->solid = static_cast<unsigned char *>(d);
+        if (cudaMemcpyAsync(c->solid, solid.data(), solid.size(), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
+            return bail(fail(FRE_ERR_CUDA, "upload of the roller mask failed"));
+        c->n_ghost = (int)ghost.size();
+        if (c->n_ghost) {
+            st = dev_alloc(c, &d, sizeof(int) * ghost.size());
+            if (st != FRE_OK) return bail(st);
+            c->ghost = static_cast<int *>(d);
+            if (cudaMemcpyAsync(c->ghost, ghost.data(), sizeof(int) * ghost.size(), cudaMemcpyHostToDevice,
+                                c->stream) != cudaSuccess)
+                return bail(fail(FRE_ERR_CUDA, "upload of the ghost list failed"));
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return bail(fail(FRE_ERR_CUDA, "geometry upload: %s", cudaGetErrorString(cudaGetLastError())));
+    }
+    c->G.solid = c->solid;
+    *out = c;
+    return FRE_OK;
+}
+
+fre_status fre_init_droplet(fre_ctx *c, double cx, double cy, double cz, double R) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (!(c->p.A > 0.0) || !(c->p.kappa > 0.0)) return fail(FRE_ERR_ARG, "fre_init_droplet needs A > 0, kappa > 0");
+    if (!(R > 0.0) || !std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(cz))
+        return fail(FRE_ERR_ARG, "fre_init_droplet: R must be > 0 and the centre finite");
+    c->cur = 0;
+    c->pp = 1;
+    fre::Launch L = launch_of(c);
+    L.phi = c->phi[0];
+    c->ks->set_phi(L, 1, cx, cy, cz, R);
+    return finish_init(c, 0);
+}
+
+fre_status fre_init_fields(fre_ctx *c, const double *rho, const double *ux, const double *uy, const double *uz,
+                           const double *phi) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (!rho || !ux || !uy || !phi) return fail(FRE_ERR_ARG, "fre_init_fields: rho, ux, uy, phi are required");
+    if (c->p.lattice == FRE_D3Q19 && !uz) return fail(FRE_ERR_ARG, "fre_init_fields: D3Q19 needs uz");
+    s = ensure_staging(c);
+    if (s != FRE_OK) return s;
+    const size_t N = (size_t)c->G.n, bytes = N * sizeof(double);
+    const double *src[5] = {rho, ux, uy, uz, phi};
+    for (int k = 0; k < 5; ++k) {
+        if (src[k]) {
+            FRE_CUDA(cudaMemcpyAsync(c->staging + k * N, src[k], bytes, cudaMemcpyHostToDevice, c->stream));
+        } else {
+            FRE_CUDA(cudaMemsetAsync(c->staging + k * N, 0, bytes, c->stream));
+        }
+    }
+    c->cur = 0;
+    c->pp = 1;
+    fre::Launch L = launch_of(c);
+    L.phi = c->phi[0];
+    c->ks->set_phi(L, 0, 0, 0, 0, 0);
+    s = finish_init(c, 1);
+    if (s != FRE_OK) return s;
+    FRE_CUDA(cudaStreamSynchronize(c->stream));
+    return FRE_OK;
+}
+
+fre_status fre_load_populations(fre_ctx *c, const double *f, const double *g) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (!f || !g) return fail(FRE_ERR_ARG, "fre_load_populations: f and g are required");
+    s = ensure_staging(c);
+    if (s != FRE_OK) return s;
+    c->cur = 0;
+    c->pp = 1;
+    fre::Launch L = launch_of(c);
+    const size_t N = (size_t)c->G.n;
+    for (int lat = 0; lat < 2; ++lat) {
+        const double *h = lat ? g : f;
+        for (int i = 0; i < c->q; ++i) {
+            FRE_CUDA(cudaMemcpyAsync(c->staging, h + i * N, N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            c->ks->load_plane(L, lat, i);
+        }
+    }
+    s = check_launch("fre_load_populations");
+    if (s != FRE_OK) return s;
+    FRE_CUDA(cudaStreamSynchronize(c->stream));
+    c->local = true;
+    c->initialised = true;
+    c->step = 0;
+    return FRE_OK;
+}
+
+fre_status fre_store_populations(fre_ctx *c, double *f, double *g) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (!c->initialised) return fail(FRE_ERR_STATE, "fre_store_populations: not initialised");
+    s = ensure_staging(c);
+    if (s != FRE_OK) return s;
+    fre::Launch L = launch_of(c);
+    const size_t N = (size_t)c->G.n;
+    for (int lat = 0; lat < 2; ++lat) {
+        double *h = lat ? g : f;
+        if (!h) continue;
+        for (int i = 0; i < c->q; ++i) {
+            c->ks->pull_plane(L, !c->local, lat, i);
+            FRE_CUDA(cudaMemcpyAsync(h + i * N, c->staging, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    s = check_launch("fre_store_populations");
+    if (s != FRE_OK) return s;
+    FRE_CUDA(cudaStreamSynchronize(c->stream));
+    return FRE_OK;
+}
+
+fre_status fre_step(fre_ctx *c, int nsteps) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (nsteps < 0) return fail(FRE_ERR_ARG, "fre_step: nsteps < 0");
+    if (!c->initialised) return fail(FRE_ERR_STATE, "fre_step: not initialised");
+    for (int t = 0; t < nsteps; ++t) {
+        fre::Launch L = launch_of(c);
+        const bool pull = !c->local;
+        c->ks->phi(L, pull);
+        if (c->n_ghost) c->ks->ghost(L, L.phi);
+        c->ks->mu(L);
+        if (c->n_ghost) c->ks->ghost(L, L.mu);
+        c->ks->update(L, pull);
+        c->cur ^= 1;
+        c->pp ^= 1;
+        c->local = false;
+        c->step++;
+    }
+    return check_launch("fre_step");
+}
+
+fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launches) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (nsteps < 0 || !ms) return fail(FRE_ERR_ARG, "fre_step_timed: nsteps < 0 or ms is NULL");
+    if (!c->initialised) return fail(FRE_ERR_STATE, "fre_step_timed: not initialised");
+    std::vector<cudaEvent_t> ev((size_t)3 * nsteps + 1);
+    for (auto &e : ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FRE_ERR_CUDA, "fre_step_timed: cudaEventCreate failed");
+        }
+    }
+    long long nl = 0;
+    cudaEventRecord(ev[0], c->stream);
+    for (int t = 0; t < nsteps; ++t) {
+        fre::Launch L = launch_of(c);
+        const bool pull = !c->local;
+        c->ks->phi(L, pull);
+        ++nl;
+        cudaEventRecord(ev[3 * t + 1], c->stream);
+        if (c->n_ghost) { c->ks->ghost(L, L.phi); ++nl; }
+        c->ks->mu(L);
+        ++nl;
+        if (c->n_ghost) { c->ks->ghost(L, L.mu); ++nl; }
+        cudaEventRecord(ev[3 * t + 2], c->stream);
+        c->ks->update(L, pull);
+        ++nl;
+        cudaEventRecord(ev[3 * t + 3], c->stream);
+        c->cur ^= 1;
+        c->pp ^= 1;
+        c->local = false;
+        c->step++;
+    }
+    s = check_launch("fre_step_timed");
+    cudaError_t e = cudaEventSynchronize(ev.back());
+    for (int k = 0; k < 4; ++k) ms[k] = 0.0;
+    if (s == FRE_OK && e == cudaSuccess) {
+        for (int t = 0; t < nsteps; ++t)
+            for (int k = 0; k < 3; ++k) {
+                float x = 0.f;
+                cudaEventElapsedTime(&x, ev[3 * t + k], ev[3 * t + k + 1]);
+                ms[k] += x;
+            }
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, ev[0], ev.back());
+        ms[3] = tot;
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (launches) *launches = nl;
+    if (s != FRE_OK) return s;
+    if (e != cudaSuccess) return fail(FRE_ERR_CUDA, "fre_step_timed: %s", cudaGetErrorString(e));
+    return FRE_OK;
+}
+
+fre_status fre_copy_fields(fre_ctx *c, double *rho, double *ux, double *uy, double *uz, double *phi, double *mu) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (!c->initialised) return fail(FRE_ERR_STATE, "fre_copy_fields: not initialised");
+    s = ensure_staging(c);
+    if (s != FRE_OK) return s;
+    fre::Launch L = launch_of(c);
+    current_phi_mu(c, L);
+    c->ks->macro(L, !c->local);
+    double *dst[6] = {rho, ux, uy, uz, phi, mu};
+    const size_t N = (size_t)c->G.n;
+    for (int k = 0; k < 6; ++k)
+        if (dst[k])
+            FRE_CUDA(cudaMemcpyAsync(dst[k], c->staging + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                     c->stream));
+    s = check_launch("fre_copy_fields");
+    if (s != FRE_OK) return s;
+    FRE_CUDA(cudaStreamSynchronize(c->stream));
+    return FRE_OK;
+}
+
+fre_status fre_observables(fre_ctx *c, fre_obs *out) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (!out) return fail(FRE_ERR_ARG, "fre_observables: out is NULL");
+    if (!c->initialised) return fail(FRE_ERR_STATE, "fre_observables: not initialised");
+    fre::Launch L = launch_of(c);
+    current_phi_mu(c, L);
+    c->ks->obs(L, !c->local);
+    FRE_CUDA(cudaMemcpyAsync(c->obs_host, c->obs_dev, sizeof(fre_obs), cudaMemcpyDeviceToHost, c->stream));
+    s = check_launch("fre_observables");
+    if (s != FRE_OK) return s;
+    FRE_CUDA(cudaStreamSynchronize(c->stream));
+    *out = *c->obs_host;
+    out->step = c->step;
+    if (out->status != 0)
+        return fail(FRE_ERR_UNSTABLE, "fre_observables: %s", out->status == 1 ? "non-finite values" : "|u| > 0.3");
+    return FRE_OK;
+}
+
+long long fre_step_count(const fre_ctx *c) { return c ? c->step : -1; }
+
+void fre_destroy(fre_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device_id);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->obs_host) cudaFreeHost(c->obs_host);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+const char *fre_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

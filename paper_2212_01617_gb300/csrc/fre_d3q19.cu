@@ -1,0 +1,16 @@
+// Kernel instantiations for the D3Q19 lattice (all storage formats).
+#include "fre_kernels.cuh"
+
+namespace fre {
+
+const KernelSet *kernels_d3q19(int precision) {
+    switch (precision) {
+        case FRE_FP64: return Launchers<19, FRE_FP64>::set();
+        case FRE_FP32: return Launchers<19, FRE_FP32>::set();
+        case FRE_FP16DEV: return Launchers<19, FRE_FP16DEV>::set();
+        case FRE_BF16DEV: return Launchers<19, FRE_BF16DEV>::set();
+        default: return nullptr;
+    }
+}
+
+}  // namespace fre

@@ -1,0 +1,75 @@
+// Internal types shared by the host runtime (fre_api.cu) and the kernel
+// translation units (fre_d2q9.cu, fre_d3q19.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fre.h"
+
+namespace fre {
+
+// Geometry of one lattice: sizes, device kind and the analytic walls.
+struct Geo {
+    int nx, ny, nz, device;
+    long long n;              // nodes
+    long long np;             // plane stride of the population arrays (elements)
+    const unsigned char *solid;  // roller id per node (0 = fluid); four-roller only
+    double rcx[5], rcy[5], om[5];  // roller centres and angular velocities (1..4)
+    double uwall;             // shear wall speed
+};
+
+// Physical parameters of the scheme (Sec. 2.2).
+struct Phys {
+    double tau_f, tau_g, A, kappa, Gamma, rho0;
+};
+
+// One population buffer (A or B).  FP64/FP32: f, g are [q][np] arrays of
+// the storage type.  16-bit formats: f is [q][np] of deviations
+// f_i - w_i rho0; g holds g_1..g_{q-1} as [q-1][np]; g0 is FP32 [np].
+struct Buf {
+    void *f;
+    void *g;
+    float *g0;
+};
+
+// Everything a kernel launch needs.  phi/mu are arrays of the compute type.
+struct Launch {
+    Geo G;
+    Phys P;
+    Buf src, dst;
+    const void *phi_prev;  // phi at the previous step (moving-wall term of g)
+    void *phi;             // phi at the current step
+    void *mu;              // mu at the current step
+    const int *ghost;      // roller solid nodes with fluid neighbours
+    int n_ghost;
+    double *red;           // reduction scratch
+    int red_blocks;
+    fre_obs *obs;          // device observables
+    double *staging;       // FP64 staging of host I/O (n doubles per field)
+    cudaStream_t stream;
+};
+
+// Per lattice and storage format: the kernels of one time step and of the
+// I/O paths.  `pull` selects streaming from the post-collision buffer (true)
+// or reading pre-collision populations in place (false, right after an
+// initialisation or a load).
+struct KernelSet {
+    void (*phi)(const Launch &, bool pull);           // phi = sum g (pulled)
+    void (*ghost)(const Launch &, void *field);       // roller solid stencil values
+    void (*mu)(const Launch &);                        // mu from phi
+    void (*update)(const Launch &, bool pull);        // fused pull + collide
+    void (*obs)(const Launch &, bool pull);           // observables -> L.obs
+    void (*macro)(const Launch &, bool pull);         // rho,u,phi,mu -> staging
+    void (*pull_plane)(const Launch &, bool pull, int lattice_g, int i);  // -> staging
+    void (*load_plane)(const Launch &, int lattice_g, int i);  // staging -> src
+    void (*set_phi)(const Launch &, int analytic, double cx, double cy, double cz, double R);
+    void (*init_eq)(const Launch &, int from_staging);  // f = f_eq, g = g_eq into src
+};
+
+const KernelSet *kernels_d2q9(int precision);
+const KernelSet *kernels_d3q19(int precision);
+
+}  // namespace fre

@@ -1,0 +1,736 @@
+// Kernels of the two-lattice free energy LBM time step (Simonis et al.,
+// arXiv:2212.01617, Sec. 2.2-2.3, Algorithm 1), templated on the velocity
+// set (Q = 9, 19) and the population storage format.
+//
+// Data layout (device memory, one context):
+//   populations  SoA planes [q][np], node n = (z*ny + y)*nx + x (x fastest),
+//                two buffers A/B (pull streaming A -> B, then swap);
+//   phi, mu      one value per node in the compute type; phi in two
+//                buffers (current step / previous step).
+// One time step = k_phi (pull g, phi = sum g) -> [roller ghosts] -> k_mu
+// (mu from the phi stencil) -> [roller ghosts] -> k_update (pull f and g,
+// moments, force from the phi/mu stencils, BGK + Guo for f, BGK for g, store
+// post-collision populations).  The state between steps is the
+// post-collision buffer; streaming happens as the next step pulls from it.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "fre_internal.h"
+#include "lattice.cuh"
+
+namespace fre {
+
+constexpr int kBlock = 256;
+
+template <int FMT>
+struct Fmt;
+template <>
+struct Fmt<FRE_FP64> {
+    using S = double;
+    using T = double;
+    static constexpr bool DEV = false;
+};
+template <>
+struct Fmt<FRE_FP32> {
+    using S = float;
+    using T = float;
+    static constexpr bool DEV = false;
+};
+template <>
+struct Fmt<FRE_FP16DEV> {
+    using S = __half;
+    using T = float;
+    static constexpr bool DEV = true;
+};
+template <>
+struct Fmt<FRE_BF16DEV> {
+    using S = __nv_bfloat16;
+    using T = float;
+    static constexpr bool DEV = true;
+};
+
+__device__ __forceinline__ float to_float(__half h) { return __half2float(h); }
+__device__ __forceinline__ float to_float(__nv_bfloat16 h) { return __bfloat162float(h); }
+template <typename S>
+__device__ __forceinline__ S from_float(float v);
+template <>
+__device__ __forceinline__ __half from_float<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// Population access for one buffer in a given storage format.
+template <int Q, int FMT>
+struct Pop {
+    using S = typename Fmt<FMT>::S;
+    using T = typename Fmt<FMT>::T;
+
+    __device__ __forceinline__ static T ldf(const Buf &b, long long np, int i, long long k, T rho0) {
+        const S *p = static_cast<const S *>(b.f) + (size_t)i * np + k;
+        if constexpr (!Fmt<FMT>::DEV) {
+            return __ldg(p);
+        } else {
+            return to_float(__ldg(p)) + T(Lat<Q>::w(i)) * rho0;
+        }
+    }
+    __device__ __forceinline__ static T ldg(const Buf &b, long long np, int i, long long k) {
+        if constexpr (!Fmt<FMT>::DEV) {
+            return __ldg(static_cast<const S *>(b.g) + (size_t)i * np + k);
+        } else {
+            if (i == 0) return __ldg(b.g0 + k);
+            return to_float(__ldg(static_cast<const S *>(b.g) + (size_t)(i - 1) * np + k));
+        }
+    }
+    __device__ __forceinline__ static void stf(const Buf &b, long long np, int i, long long k, T v, T rho0) {
+        S *p = static_cast<S *>(b.f) + (size_t)i * np + k;
+        if constexpr (!Fmt<FMT>::DEV) {
+            *p = v;
+        } else {
+            *p = from_float<S>(v - T(Lat<Q>::w(i)) * rho0);
+        }
+    }
+    __device__ __forceinline__ static void stg(const Buf &b, long long np, int i, long long k, T v) {
+        if constexpr (!Fmt<FMT>::DEV) {
+            static_cast<S *>(b.g)[(size_t)i * np + k] = v;
+        } else {
+            if (i == 0) {
+                b.g0[k] = v;
+            } else {
+                static_cast<S *>(b.g)[(size_t)(i - 1) * np + k] = from_float<S>(v);
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+__device__ __forceinline__ long long node_index(const Geo &G, int x, int y, int z) {
+    return ((long long)z * G.ny + y) * G.nx + x;
+}
+
+__device__ __forceinline__ void decode(const Geo &G, long long n, int &x, int &y, int &z) {
+    int r = (int)(n % ((long long)G.nx * G.ny));
+    x = r % G.nx;
+    y = r / G.nx;
+    z = (int)(n / ((long long)G.nx * G.ny));
+}
+
+__device__ __forceinline__ bool is_solid(const Geo &G, long long n) {
+    return G.device == FRE_FOUR_ROLLER && G.solid[n] != 0;
+}
+
+// Neighbour x + c_i of the phi/mu stencils: periodic in x and z; in y
+// periodic except for the shear device, whose stencil value behind a wall is
+// the mirror image across the half-way wall (the first fluid row).
+template <int Q>
+__device__ __forceinline__ long long stencil_nb(const Geo &G, int x, int y, int z, int i) {
+    int xn = wrapi(x + Lat<Q>::cx(i), G.nx);
+    int zn = wrapi(z + Lat<Q>::cz(i), G.nz);
+    int yn = y + Lat<Q>::cy(i);
+    if (G.device == FRE_SHEAR) {
+        yn = yn < 0 ? 0 : (yn >= G.ny ? G.ny - 1 : yn);
+    } else {
+        yn = wrapi(yn, G.ny);
+    }
+    return node_index(G, xn, yn, zn);
+}
+
+// Streaming source x - c_i.  Returns its index when it is fluid; returns -1
+// and the wall velocity at the link's wall point x - c_i/2 when it is solid.
+template <int Q, typename T>
+__device__ __forceinline__ long long pull_source(const Geo &G, int x, int y, int z, int i, T &uwx, T &uwy) {
+    int xs = x - Lat<Q>::cx(i), ys = y - Lat<Q>::cy(i), zs = z - Lat<Q>::cz(i);
+    if (G.device == FRE_SHEAR) {
+        if (ys < 0) {
+            uwx = T(-G.uwall);
+            uwy = T(0);
+            return -1;
+        }
+        if (ys >= G.ny) {
+            uwx = T(G.uwall);
+            uwy = T(0);
+            return -1;
+        }
+        return node_index(G, wrapi(xs, G.nx), ys, wrapi(zs, G.nz));
+    }
+    long long s = node_index(G, wrapi(xs, G.nx), wrapi(ys, G.ny), wrapi(zs, G.nz));
+    if (G.device == FRE_FOUR_ROLLER) {
+        int k = G.solid[s];
+        if (k) {
+            double xw = x - 0.5 * Lat<Q>::cx(i), yw = y - 0.5 * Lat<Q>::cy(i);
+            uwx = T(-G.om[k] * (yw - G.rcy[k]));
+            uwy = T(G.om[k] * (xw - G.rcx[k]));
+            return -1;
+        }
+    }
+    return s;
+}
+
+// Pre-collision populations of node n: pulled from the post-collision
+// buffer (with half-way bounce-back and the moving-wall term
+//   f_i = f*_ibar + 2 w_i rho0 (c_i . u_w)/cs^2,
+//   g_i = g*_ibar + 2 w_i phi(x, t-1) (c_i . u_w)/cs^2)
+// or read in place.
+template <int Q, int FMT, bool PULL, bool WANT_F>
+__device__ __forceinline__ void gather(const Launch &L, int x, int y, int z, long long n,
+                                       typename Fmt<FMT>::T *f, typename Fmt<FMT>::T *g) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
+    const T rho0 = T(L.P.rho0);
+    const long long np = L.G.np;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (!PULL) {
+            if (WANT_F) f[i] = P::ldf(L.src, np, i, n, rho0);
+            g[i] = P::ldg(L.src, np, i, n);
+            continue;
+        }
+        T uwx = T(0), uwy = T(0);
+        long long s = (i == 0) ? n : pull_source<Q, T>(L.G, x, y, z, i, uwx, uwy);
+        if (s >= 0) {
+            if (WANT_F) f[i] = P::ldf(L.src, np, i, s, rho0);
+            g[i] = P::ldg(L.src, np, i, s);
+        } else {
+            const int o = Lat<Q>::opp(i);
+            const T cu = T(Lat<Q>::cx(i)) * uwx + T(Lat<Q>::cy(i)) * uwy;
+            const T wi2 = T(2.0 * Lat<Q>::w(i) * 3.0);
+            if (WANT_F) f[i] = P::ldf(L.src, np, o, n, rho0) + wi2 * rho0 * cu;
+            const T php = static_cast<const T *>(L.phi_prev)[n];
+            g[i] = P::ldg(L.src, np, o, n) + wi2 * php * cu;
+        }
+    }
+}
+
+// Macroscopic state of a node: moments, force and velocity (Algorithm 1
+// up to the velocity).
+template <typename T>
+struct Macro {
+    T rho, phi, mu, ux, uy, uz, Fx, Fy, Fz;
+};
+
+template <int Q, int FMT>
+__device__ __forceinline__ Macro<typename Fmt<FMT>::T> macro_of(const Launch &L, int x, int y, int z, long long n,
+                                                                 const typename Fmt<FMT>::T *f,
+                                                                 const typename Fmt<FMT>::T *g) {
+    using T = typename Fmt<FMT>::T;
+    Macro<T> m;
+    T rho = T(0), ph = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        ph += g[i];
+        if (Lat<Q>::cx(i)) jx += T(Lat<Q>::cx(i)) * f[i];
+        if (Lat<Q>::cy(i)) jy += T(Lat<Q>::cy(i)) * f[i];
+        if (Lat<Q>::cz(i)) jz += T(Lat<Q>::cz(i)) * f[i];
+    }
+    // F = -phi grad(mu) = mu grad(phi) - grad(phi mu), isotropic gradients
+    const T *phif = static_cast<const T *>(L.phi);
+    const T *muf = static_cast<const T *>(L.mu);
+    T gpx = T(0), gpy = T(0), gpz = T(0), gqx = T(0), gqy = T(0), gqz = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        long long k = stencil_nb<Q>(L.G, x, y, z, i);
+        const T p = phif[k];
+        const T pm = p * muf[k];
+        const T w = T(Lat<Q>::w(i));
+        if (Lat<Q>::cx(i)) { gpx += w * T(Lat<Q>::cx(i)) * p; gqx += w * T(Lat<Q>::cx(i)) * pm; }
+        if (Lat<Q>::cy(i)) { gpy += w * T(Lat<Q>::cy(i)) * p; gqy += w * T(Lat<Q>::cy(i)) * pm; }
+        if (Lat<Q>::cz(i)) { gpz += w * T(Lat<Q>::cz(i)) * p; gqz += w * T(Lat<Q>::cz(i)) * pm; }
+    }
+    const T mu = muf[n];
+    m.Fx = T(3) * (mu * gpx - gqx);
+    m.Fy = T(3) * (mu * gpy - gqy);
+    m.Fz = T(3) * (mu * gpz - gqz);
+    const T inv = T(1) / rho;
+    m.ux = (jx + T(0.5) * m.Fx) * inv;
+    m.uy = (jy + T(0.5) * m.Fy) * inv;
+    m.uz = (jz + T(0.5) * m.Fz) * inv;
+    m.rho = rho;
+    m.phi = ph;
+    m.mu = mu;
+    return m;
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_phi(Launch L) {
+    using T = typename Fmt<FMT>::T;
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n || is_solid(L.G, n)) return;
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    T g[Q];
+    gather<Q, FMT, PULL, false>(L, x, y, z, n, nullptr, g);
+    T ph = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ph += g[i];
+    static_cast<T *>(L.phi)[n] = ph;
+}
+
+// Stencil values at roller solids: w-weighted mean over fluid neighbours.
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlock) k_ghost(Launch L, T *field) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n_ghost) return;
+    long long s = L.ghost[t];
+    int x, y, z;
+    decode(L.G, s, x, y, z);
+    T num = T(0), den = T(0);
+#pragma unroll
+    for (int j = 1; j < Q; ++j) {
+        long long m = stencil_nb<Q>(L.G, x, y, z, j);
+        if (L.G.solid[m]) continue;
+        num += T(Lat<Q>::w(j)) * field[m];
+        den += T(Lat<Q>::w(j));
+    }
+    field[s] = den > T(0) ? num / den : T(0);
+}
+
+// mu = A (phi^3 - phi) - kappa lap(phi), lap = (2/cs^2) sum w_i (phi(x+c_i) - phi(x))
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlock) k_mu(Launch L) {
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n || is_solid(L.G, n)) return;
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    const T *phi = static_cast<const T *>(L.phi);
+    const T p0 = phi[n];
+    T lap = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) lap += T(Lat<Q>::w(i)) * (phi[stencil_nb<Q>(L.G, x, y, z, i)] - p0);
+    lap *= T(6);
+    static_cast<T *>(L.mu)[n] = T(L.P.A) * (p0 * p0 * p0 - p0) - T(L.P.kappa) * lap;
+}
+
+// Fused pull + collide of f and g for one node (Algorithm 1).
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_update(Launch L) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n || is_solid(L.G, n)) return;
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    T f[Q], g[Q];
+    gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
+    const Macro<T> m = macro_of<Q, FMT>(L, x, y, z, n, f, g);
+
+    const T of = T(1.0 / L.P.tau_f), og = T(1.0 / L.P.tau_g);
+    const T kf = T(1.0 - 0.5 / L.P.tau_f);
+    const T gmu3 = T(3.0 * L.P.Gamma) * m.mu;
+    const T usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    const T uF = m.ux * m.Fx + m.uy * m.Fy + m.uz * m.Fz;
+    T fsum = T(0), gsum = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const T cx = T(Lat<Q>::cx(i)), cy = T(Lat<Q>::cy(i)), cz = T(Lat<Q>::cz(i));
+        const T w = T(Lat<Q>::w(i));
+        const T cu = cx * m.ux + cy * m.uy + cz * m.uz;
+        const T cF = cx * m.Fx + cy * m.Fy + cz * m.Fz;
+        const T poly = T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq;
+        const T feq = w * m.rho * (T(1) + poly);
+        // Guo: (1 - 1/2tau) w [3 (c - u).F + 9 (c.u)(c.F)]
+        const T S = kf * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+        const T fs = f[i] - (f[i] - feq) * of + S;
+        const T geq = w * (gmu3 + m.phi * poly);
+        const T gs = g[i] - (g[i] - geq) * og;
+        fsum += fs;
+        gsum += gs;
+        P::stf(L.dst, L.G.np, i, n, fs, T(L.P.rho0));
+        P::stg(L.dst, L.G.np, i, n, gs);
+    }
+    // rest populations close the collision invariants: sum f* = rho, sum g* = phi
+    P::stf(L.dst, L.G.np, 0, n, m.rho - fsum, T(L.P.rho0));
+    P::stg(L.dst, L.G.np, 0, n, m.phi - gsum);
+}
+
+// Macroscopic fields -> staging (FP64): rho, ux, uy, uz, phi, mu.
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_macro(Launch L) {
+    using T = typename Fmt<FMT>::T;
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n) return;
+    double *out = L.staging;
+    const long long N = L.G.n;
+    if (is_solid(L.G, n)) {
+        for (int k = 0; k < 6; ++k) out[k * N + n] = 0.0;
+        return;
+    }
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    T f[Q], g[Q];
+    gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
+    const Macro<T> m = macro_of<Q, FMT>(L, x, y, z, n, f, g);
+    out[0 * N + n] = m.rho;
+    out[1 * N + n] = m.ux;
+    out[2 * N + n] = m.uy;
+    out[3 * N + n] = m.uz;
+    out[4 * N + n] = m.phi;
+    out[5 * N + n] = m.mu;
+}
+
+// Pre-collision population i of f (lat_g = 0) or g (lat_g = 1) -> staging.
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_pull_plane(Launch L, int lat_g, int i) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n) return;
+    if (is_solid(L.G, n)) {
+        L.staging[n] = 0.0;
+        return;
+    }
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    const T rho0 = T(L.P.rho0);
+    T v = T(0);
+    if (!PULL || i == 0) {
+        v = lat_g ? P::ldg(L.src, L.G.np, i, n) : P::ldf(L.src, L.G.np, i, n, rho0);
+    } else {
+        T uwx = T(0), uwy = T(0);
+        long long s = -1;
+        // unrolled lookup of the direction so the velocity is a constant
+#pragma unroll
+        for (int j = 1; j < Q; ++j) {
+            if (j != i) continue;
+            s = pull_source<Q, T>(L.G, x, y, z, j, uwx, uwy);
+            if (s >= 0) {
+                v = lat_g ? P::ldg(L.src, L.G.np, j, s) : P::ldf(L.src, L.G.np, j, s, rho0);
+            } else {
+                const int o = Lat<Q>::opp(j);
+                const T cu = T(Lat<Q>::cx(j)) * uwx + T(Lat<Q>::cy(j)) * uwy;
+                const T wi2 = T(2.0 * Lat<Q>::w(j) * 3.0);
+                if (lat_g) {
+                    v = P::ldg(L.src, L.G.np, o, n) + wi2 * static_cast<const T *>(L.phi_prev)[n] * cu;
+                } else {
+                    v = P::ldf(L.src, L.G.np, o, n, rho0) + wi2 * rho0 * cu;
+                }
+            }
+        }
+    }
+    L.staging[n] = (double)v;
+}
+
+// staging -> pre-collision population i of the source buffer.
+template <int Q, int FMT>
+__global__ void __launch_bounds__(kBlock) k_load_plane(Launch L, int lat_g, int i) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n) return;
+    T v = is_solid(L.G, n) ? T(0) : T(L.staging[n]);
+    if (lat_g) {
+        P::stg(L.src, L.G.np, i, n, v);
+    } else {
+        P::stf(L.src, L.G.np, i, n, is_solid(L.G, n) ? T(0) : v, T(L.P.rho0));
+    }
+}
+
+// phi field: droplet tanh((R - |x - c|)/(sqrt(2) xi)) or staging field 4.
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlock) k_set_phi(Launch L, int analytic, double cx, double cy, double cz,
+                                                    double R) {
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n) return;
+    T *phi = static_cast<T *>(L.phi);
+    if (is_solid(L.G, n)) {
+        phi[n] = T(0);
+        return;
+    }
+    if (!analytic) {
+        phi[n] = T(L.staging[4 * L.G.n + n]);
+        return;
+    }
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    double dx = x - cx, dy = y - cy, dz = (Lat<Q>::D == 3) ? z - cz : 0.0;
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double xi = sqrt(L.P.kappa / L.P.A);
+    phi[n] = T(tanh((R - r) / (sqrt(2.0) * xi)));
+}
+
+// f = f_eq(rho, u), g = g_eq(phi, mu, u) into the source buffer.  rho, u
+// from staging fields 0..3, or rho0 and the analytic initial velocity.
+template <int Q, int FMT>
+__global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
+    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.G.n) return;
+    const long long N = L.G.n;
+    const T rho0 = T(L.P.rho0);
+    if (is_solid(L.G, n)) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            P::stf(L.src, L.G.np, i, n, T(0), rho0);
+            P::stg(L.src, L.G.np, i, n, T(0));
+        }
+        return;
+    }
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    T rho, ux, uy, uz;
+    if (from_staging) {
+        rho = T(L.staging[0 * N + n]);
+        ux = T(L.staging[1 * N + n]);
+        uy = T(L.staging[2 * N + n]);
+        uz = T(L.staging[3 * N + n]);
+    } else {
+        rho = rho0;
+        ux = (L.G.device == FRE_SHEAR) ? T(L.G.uwall * (2.0 * (y + 0.5) / L.G.ny - 1.0)) : T(0);
+        uy = T(0);
+        uz = T(0);
+    }
+    const T phi = static_cast<const T *>(L.phi)[n];
+    const T mu = static_cast<const T *>(L.mu)[n];
+    const T usq = ux * ux + uy * uy + uz * uz;
+    T gsum = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T cu = T(Lat<Q>::cx(i)) * ux + T(Lat<Q>::cy(i)) * uy + T(Lat<Q>::cz(i)) * uz;
+        const T poly = T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq;
+        const T w = T(Lat<Q>::w(i));
+        P::stf(L.src, L.G.np, i, n, w * rho * (T(1) + poly), rho0);
+        if (i > 0) {
+            const T ge = w * (T(3.0 * L.P.Gamma) * mu + phi * poly);
+            gsum += ge;
+            P::stg(L.src, L.G.np, i, n, ge);
+        }
+    }
+    P::stg(L.src, L.G.np, 0, n, phi - gsum);
+}
+
+// ------------------------------------------------------------ observables
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+constexpr int kObsVals = 10;   // rho, phi, vol, W, count, Wx, Wy, Wz, max|u|, non-finite
+constexpr int kMomVals = 6;    // central second moments
+constexpr int kRedBlocks = 1024;                      // max blocks of a reduction
+constexpr int kRedMom = kRedBlocks * kObsVals;        // offset of pass-2 partials
+constexpr int kRedTot = kRedBlocks * (kObsVals + kMomVals);  // offset of totals
+constexpr int kRedDoubles = kRedTot + 32;             // size of the scratch
+
+// Block reduction of NV values (sums except the two last, which are maxima
+// when MAXLAST is set) into red[blockIdx.x * NV + k].
+template <int NV, bool MAXLAST>
+__device__ __forceinline__ void block_reduce_store(double *v, double *red) {
+    __shared__ double sh[kBlock / 32][NV];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double r = (MAXLAST && k >= NV - 2) ? warp_max(v[k]) : warp_sum(v[k]);
+        if (lane == 0) sh[wid][k] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        double acc = sh[0][k];
+        for (int w = 1; w < kBlock / 32; ++w) acc = (MAXLAST && k >= NV - 2) ? fmax(acc, sh[w][k]) : acc + sh[w][k];
+        red[blockIdx.x * NV + k] = acc;
+    }
+}
+
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_obs1(Launch L) {
+    using T = typename Fmt<FMT>::T;
+    double v[kObsVals];
+#pragma unroll
+    for (int k = 0; k < kObsVals; ++k) v[k] = 0.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.G.n;
+         n += (long long)gridDim.x * blockDim.x) {
+        if (is_solid(L.G, n)) continue;
+        int x, y, z;
+        decode(L.G, n, x, y, z);
+        T f[Q], g[Q];
+        gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
+        const Macro<T> m = macro_of<Q, FMT>(L, x, y, z, n, f, g);
+        const double rho = m.rho, ph = m.phi;
+        const double u = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy + (double)m.uz * m.uz);
+        v[0] += rho;
+        v[1] += ph;
+        v[2] += 0.5 * (1.0 + ph);
+        if (ph > 0.0) {
+            const double w = 0.5 * (1.0 + ph);
+            v[3] += w;
+            v[4] += 1.0;
+            v[5] += w * x;
+            v[6] += w * y;
+            v[7] += w * z;
+        }
+        if (isfinite(rho) && isfinite(ph) && isfinite(u) && isfinite((double)m.mu)) {
+            v[8] = fmax(v[8], u);
+        } else {
+            v[9] = 1.0;
+        }
+    }
+    block_reduce_store<kObsVals, true>(v, L.red);
+}
+
+// Sum the per-block partials in a fixed order (deterministic).
+template <int NV, bool MAXLAST>
+__global__ void k_reduce_partials(const double *red, int nblocks, double *out) {
+    const int k = threadIdx.x;
+    if (k >= NV) return;
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        double x = red[b * NV + k];
+        acc = (MAXLAST && k >= NV - 2) ? fmax(acc, x) : acc + x;
+    }
+    out[k] = acc;
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlock) k_obs2(Launch L, const double *tot) {
+    double v[kMomVals];
+#pragma unroll
+    for (int k = 0; k < kMomVals; ++k) v[k] = 0.0;
+    const double W = tot[3];
+    const double X = W > 0 ? tot[5] / W : 0.0, Y = W > 0 ? tot[6] / W : 0.0, Z = W > 0 ? tot[7] / W : 0.0;
+    const T *phi = static_cast<const T *>(L.phi);
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.G.n;
+         n += (long long)gridDim.x * blockDim.x) {
+        if (is_solid(L.G, n)) continue;
+        const double ph = phi[n];
+        if (!(ph > 0.0)) continue;
+        int x, y, z;
+        decode(L.G, n, x, y, z);
+        const double w = 0.5 * (1.0 + ph);
+        const double dx = x - X, dy = y - Y, dz = z - Z;
+        v[0] += w * dx * dx;
+        v[1] += w * dy * dy;
+        v[2] += w * dz * dz;
+        v[3] += w * dx * dy;
+        v[4] += w * dx * dz;
+        v[5] += w * dy * dz;
+    }
+    block_reduce_store<kMomVals, false>(v, L.red + kRedMom);
+}
+
+// Pressure at a node: cs^2 rho + phi mu - (A/4)(phi^2 - 1)^2.
+template <int Q, int FMT, bool PULL>
+__device__ double pressure_at(const Launch &L, long long n) {
+    using T = typename Fmt<FMT>::T;
+    int x, y, z;
+    decode(L.G, n, x, y, z);
+    T f[Q], g[Q];
+    gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
+    double rho = 0.0;
+    for (int i = 0; i < Q; ++i) rho += (double)f[i];
+    const double ph = static_cast<const T *>(L.phi)[n];
+    const double mu = static_cast<const T *>(L.mu)[n];
+    return rho / 3.0 + ph * mu - 0.25 * L.P.A * (ph * ph - 1.0) * (ph * ph - 1.0);
+}
+
+template <int Q, int FMT, bool PULL>
+__global__ void k_obs_final(Launch L, const double *t1, const double *t2) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    fre_obs *o = L.obs;
+    o->mass = t1[0];
+    o->phi_sum = t1[1];
+    o->volume = t1[2];
+    o->drop_weight = t1[3];
+    o->drop_count = t1[4];
+    o->max_u = t1[8];
+    const int bad = t1[9] != 0.0;
+    const double W = t1[3];
+    for (int k = 0; k < 3; ++k) o->centroid[k] = 0.0;
+    for (int k = 0; k < 6; ++k) o->I[k] = 0.0;
+    o->D = o->theta_deg = o->p_centre = o->p_far = o->dp = 0.0;
+    if (W > 0.0) {
+        const double X[3] = {t1[5] / W, t1[6] / W, t1[7] / W};
+        for (int k = 0; k < 3; ++k) o->centroid[k] = X[k];
+        for (int k = 0; k < 6; ++k) o->I[k] = t2[k] / W;
+        const double a = o->I[0], b = o->I[1], c = o->I[3];
+        const double mm = 0.5 * (a + b), r = sqrt(0.25 * (a - b) * (a - b) + c * c);
+        double l1 = mm + r, l2 = mm - r;
+        if (l2 < 0.0) l2 = 0.0;
+        const double s1 = sqrt(l1), s2 = sqrt(l2);
+        o->D = (s1 + s2) > 0.0 ? (s1 - s2) / (s1 + s2) : 0.0;
+        o->theta_deg = 0.5 * atan2(2.0 * c, a - b) * (180.0 / 3.14159265358979323846);
+        const Geo &G = L.G;
+        int cx = wrapi((int)llround(X[0]), G.nx);
+        int cy = (int)llround(X[1]);
+        cy = cy < 0 ? 0 : (cy >= G.ny ? G.ny - 1 : cy);
+        int cz = wrapi((int)llround(X[2]), G.nz);
+        int fz = G.nz > 1 ? wrapi(cz + G.nz / 2, G.nz) : 0;
+        const long long nc = node_index(G, cx, cy, cz);
+        const long long nf = node_index(G, wrapi(cx + G.nx / 2, G.nx), cy, fz);
+        o->p_centre = pressure_at<Q, FMT, PULL>(L, nc);
+        o->p_far = pressure_at<Q, FMT, PULL>(L, nf);
+        o->dp = o->p_centre - o->p_far;
+    }
+    o->status = bad ? 1 : (o->max_u > 0.3 ? 2 : 0);
+}
+
+// ------------------------------------------------------------ launchers
+
+inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <int Q, int FMT>
+struct Launchers {
+    using T = typename Fmt<FMT>::T;
+
+    static void phi(const Launch &L, bool pull) {
+        if (pull) k_phi<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+        else k_phi<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+    }
+    static void ghost(const Launch &L, void *field) {
+        if (L.n_ghost > 0)
+            k_ghost<Q, T><<<grid_for(L.n_ghost), kBlock, 0, L.stream>>>(L, static_cast<T *>(field));
+    }
+    static void mu(const Launch &L) { k_mu<Q, T><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L); }
+    static void update(const Launch &L, bool pull) {
+        if (pull) k_update<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+        else k_update<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+    }
+    static void obs(const Launch &L, bool pull) {
+        const int nb = L.red_blocks;
+        double *t1 = L.red + kRedTot;
+        double *t2 = t1 + 16;
+        if (pull) k_obs1<Q, FMT, true><<<nb, kBlock, 0, L.stream>>>(L);
+        else k_obs1<Q, FMT, false><<<nb, kBlock, 0, L.stream>>>(L);
+        k_reduce_partials<kObsVals, true><<<1, 32, 0, L.stream>>>(L.red, nb, t1);
+        k_obs2<Q, T><<<nb, kBlock, 0, L.stream>>>(L, t1);
+        k_reduce_partials<kMomVals, false><<<1, 32, 0, L.stream>>>(L.red + kRedMom, nb, t2);
+        if (pull) k_obs_final<Q, FMT, true><<<1, 32, 0, L.stream>>>(L, t1, t2);
+        else k_obs_final<Q, FMT, false><<<1, 32, 0, L.stream>>>(L, t1, t2);
+    }
+    static void macro(const Launch &L, bool pull) {
+        if (pull) k_macro<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+        else k_macro<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+    }
+    static void pull_plane(const Launch &L, bool pull, int lat_g, int i) {
+        if (pull) k_pull_plane<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, lat_g, i);
+        else k_pull_plane<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, lat_g, i);
+    }
+    static void load_plane(const Launch &L, int lat_g, int i) {
+        k_load_plane<Q, FMT><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, lat_g, i);
+    }
+    static void set_phi(const Launch &L, int analytic, double cx, double cy, double cz, double R) {
+        k_set_phi<Q, T><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, analytic, cx, cy, cz, R);
+    }
+    static void init_eq(const Launch &L, int from_staging) {
+        k_init_eq<Q, FMT><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, from_staging);
+    }
+    static const KernelSet *set() {
+        static const KernelSet ks = {phi, ghost, mu, update, obs, macro, pull_plane, load_plane, set_phi, init_eq};
+        return &ks;
+    }
+};
+
+}  // namespace fre
