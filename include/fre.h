@@ -88,7 +88,13 @@ typedef struct {
     double u_wall;     /* wall (shear) or roller surface (four-roller) speed */
     double rho0;       /* reference density; also the wall density of the
                           moving bounce-back term */
+    unsigned flags;    /* FRE_FLAG_* bits, 0 by default */
 } fre_params;
+
+/* Force the per-node kernels even where the row kernels apply (the row
+ * kernels stage whole x-rows in shared memory; both compute the same
+ * update).  For validation. */
+#define FRE_FLAG_GENERIC_KERNELS 1u
 
 /* Observables of the state at the current step, from the pre-collision
  * populations; sums in FP64 over fluid nodes. */
@@ -165,6 +171,10 @@ fre_status fre_observables(fre_ctx *c, fre_obs *out);
 
 /* Steps taken since the last initialisation. */
 long long fre_step_count(const fre_ctx *c);
+
+/* 1 if the time step runs on the row kernels (shared-memory staged x-rows),
+ * 0 if on the per-node kernels. */
+int fre_uses_row_kernels(const fre_ctx *c);
 
 /* Destroy a context and free its device memory; NULL-safe. */
 void fre_destroy(fre_ctx *c);

@@ -30,7 +30,9 @@ DEVICES = {"shear": FRE_SHEAR, "four_roller": FRE_FOUR_ROLLER, "periodic": FRE_P
 # every entry point declared in include/fre.h
 EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_fields",
            "fre_load_populations", "fre_store_populations", "fre_step", "fre_step_timed",
-           "fre_copy_fields", "fre_observables", "fre_step_count", "fre_destroy", "fre_last_error"]
+           "fre_copy_fields", "fre_observables", "fre_step_count", "fre_uses_row_kernels",
+           "fre_destroy", "fre_last_error"]
+FRE_FLAG_GENERIC_KERNELS = 1
 
 
 class FreError(RuntimeError):
@@ -44,7 +46,7 @@ class fre_params(C.Structure):
                 ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("tau_f", C.c_double), ("tau_g", C.c_double), ("A", C.c_double),
                 ("kappa", C.c_double), ("gamma_mob", C.c_double), ("u_wall", C.c_double),
-                ("rho0", C.c_double)]
+                ("rho0", C.c_double), ("flags", C.c_uint)]
 
 
 class fre_obs(C.Structure):
@@ -91,6 +93,8 @@ def load_library(path: str = LIB_PATH):
         L.fre_observables.argtypes = [vp, C.POINTER(fre_obs)]
         L.fre_step_count.restype = C.c_longlong
         L.fre_step_count.argtypes = [vp]
+        L.fre_uses_row_kernels.restype = C.c_int
+        L.fre_uses_row_kernels.argtypes = [vp]
         L.fre_destroy.argtypes = [vp]
         L.fre_destroy.restype = None
         L.fre_last_error.restype = C.c_char_p
@@ -128,12 +132,12 @@ def current_stream_handle():
 
 def make_params(lattice="d2q9", precision="fp64", device="shear", nx=16, ny=8, nz=1,
                 tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0,
-                rho0=1.0) -> fre_params:
+                rho0=1.0, flags=0) -> fre_params:
     lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     dev = DEVICES[device] if isinstance(device, str) else int(device)
     return fre_params(lat, prec, dev, int(nx), int(ny), int(nz), float(tau_f), float(tau_g),
-                      float(A), float(kappa), float(gamma_mob), float(u_wall), float(rho0))
+                      float(A), float(kappa), float(gamma_mob), float(u_wall), float(rho0), int(flags))
 
 
 # --------------------------------------------------- one call per C entry point
@@ -196,6 +200,10 @@ def fre_observables(h, allow_unstable: bool = True) -> dict:
 
 def fre_step_count(h) -> int:
     return int(load_library().fre_step_count(h))
+
+
+def fre_uses_row_kernels(h) -> bool:
+    return bool(load_library().fre_uses_row_kernels(h))
 
 
 def fre_destroy(h):
@@ -268,3 +276,7 @@ class Simulation:
     @property
     def steps_taken(self) -> int:
         return fre_step_count(self.h)
+
+    @property
+    def row_kernels(self) -> bool:
+        return fre_uses_row_kernels(self.h)

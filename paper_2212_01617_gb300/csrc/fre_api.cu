@@ -41,6 +41,7 @@ struct fre_ctx {
     int pp = 1;         // phi buffer holding phi of the previous step
     bool local = true;  // state is pre-collision (no streaming pending)
     bool initialised = false;
+    bool rows = false;  // the row kernels run the hot path
     long long step = 0;
 };
 
@@ -87,10 +88,15 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
         return bad("gamma_mob and u_wall must be finite, rho0 > 0");
     if (p->device == FRE_FOUR_ROLLER && (p->nx < 8 || p->ny < 8)) return bad("four-roller needs nx, ny >= 8");
     long long n = (long long)p->nx * p->ny * p->nz;
-    if (n > (1LL << 31) - 1024) return bad("too many nodes (limit 2^31)");
+    if (n > (1LL << 30)) return bad("too many nodes (limit 2^30)");
     s.q = p->lattice == FRE_D2Q9 ? 9 : 19;
     s.n = n;
+    // plane stride: a multiple of 64 elements (aligned rows for vector
+    // access) with an odd number of 64-element blocks, so the q planes of a
+    // population array never sit a large power of two apart (DRAM channel
+    // aliasing of the q loads a thread issues)
     s.np = (n + 63) / 64 * 64;
+    if ((s.np / 64) % 2 == 0) s.np += 64;
     s.sz_store = p->precision == FRE_FP64 ? 8 : (p->precision == FRE_FP32 ? 4 : 2);
     s.sz_comp = p->precision == FRE_FP64 ? 8 : 4;
     size_t plane = (size_t)s.np * s.sz_store;
@@ -349,6 +355,8 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
             return bail(fail(FRE_ERR_CUDA, "geometry upload: %s", cudaGetErrorString(cudaGetLastError())));
     }
     c->G.solid = c->solid;
+    c->rows = !(p->flags & FRE_FLAG_GENERIC_KERNELS) && c->ks->rows_usable && c->ks->rows_usable(c->G);
+    cudaGetLastError();
     *out = c;
     return FRE_OK;
 }
@@ -451,11 +459,17 @@ fre_status fre_step(fre_ctx *c, int nsteps) {
     for (int t = 0; t < nsteps; ++t) {
         fre::Launch L = launch_of(c);
         const bool pull = !c->local;
-        c->ks->phi(L, pull);
-        if (c->n_ghost) c->ks->ghost(L, L.phi);
-        c->ks->mu(L);
-        if (c->n_ghost) c->ks->ghost(L, L.mu);
-        c->ks->update(L, pull);
+        if (c->rows) {
+            c->ks->phi_rows(L, pull);
+            c->ks->mu_rows(L);
+            c->ks->update_rows(L, pull);
+        } else {
+            c->ks->phi(L, pull);
+            if (c->n_ghost) c->ks->ghost(L, L.phi);
+            c->ks->mu(L);
+            if (c->n_ghost) c->ks->ghost(L, L.mu);
+            c->ks->update(L, pull);
+        }
         c->cur ^= 1;
         c->pp ^= 1;
         c->local = false;
@@ -481,15 +495,18 @@ fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launche
     for (int t = 0; t < nsteps; ++t) {
         fre::Launch L = launch_of(c);
         const bool pull = !c->local;
-        c->ks->phi(L, pull);
+        if (c->rows) c->ks->phi_rows(L, pull);
+        else c->ks->phi(L, pull);
         ++nl;
         cudaEventRecord(ev[3 * t + 1], c->stream);
         if (c->n_ghost) { c->ks->ghost(L, L.phi); ++nl; }
-        c->ks->mu(L);
+        if (c->rows) c->ks->mu_rows(L);
+        else c->ks->mu(L);
         ++nl;
         if (c->n_ghost) { c->ks->ghost(L, L.mu); ++nl; }
         cudaEventRecord(ev[3 * t + 2], c->stream);
-        c->ks->update(L, pull);
+        if (c->rows) c->ks->update_rows(L, pull);
+        else c->ks->update(L, pull);
         ++nl;
         cudaEventRecord(ev[3 * t + 3], c->stream);
         c->cur ^= 1;
@@ -559,6 +576,8 @@ fre_status fre_observables(fre_ctx *c, fre_obs *out) {
 }
 
 long long fre_step_count(const fre_ctx *c) { return c ? c->step : -1; }
+
+int fre_uses_row_kernels(const fre_ctx *c) { return c && c->rows ? 1 : 0; }
 
 void fre_destroy(fre_ctx *c) {
     if (!c) return;

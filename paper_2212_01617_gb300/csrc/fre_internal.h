@@ -67,6 +67,11 @@ struct KernelSet {
     void (*load_plane)(const Launch &, int lattice_g, int i);  // staging -> src
     void (*set_phi)(const Launch &, int analytic, double cx, double cy, double cz, double R);
     void (*init_eq)(const Launch &, int from_staging);  // f = f_eq, g = g_eq into src
+    // row kernels of the hot path (nullptr where the format has none)
+    bool (*rows_usable)(const Geo &);
+    void (*phi_rows)(const Launch &, bool pull);
+    void (*mu_rows)(const Launch &);
+    void (*update_rows)(const Launch &, bool pull);
 };
 
 const KernelSet *kernels_d2q9(int precision);

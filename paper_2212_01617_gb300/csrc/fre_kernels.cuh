@@ -108,92 +108,131 @@ struct Pop {
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-__device__ __forceinline__ long long node_index(const Geo &G, int x, int y, int z) {
-    return ((long long)z * G.ny + y) * G.nx + x;
+__device__ __forceinline__ int node_index(const Geo &G, int x, int y, int z) {
+    return (z * G.ny + y) * G.nx + x;
 }
 
-__device__ __forceinline__ void decode(const Geo &G, long long n, int &x, int &y, int &z) {
-    int r = (int)(n % ((long long)G.nx * G.ny));
-    x = r % G.nx;
+// x, y, z of node n (only used off the hot path; N < 2^31 is enforced at create)
+__device__ __forceinline__ void decode(const Geo &G, int n, int &x, int &y, int &z) {
+    const int nxy = G.nx * G.ny;
+    z = n / nxy;
+    const int r = n - z * nxy;
     y = r / G.nx;
-    z = (int)(n / ((long long)G.nx * G.ny));
+    x = r - y * G.nx;
 }
 
-__device__ __forceinline__ bool is_solid(const Geo &G, long long n) {
+__device__ __forceinline__ bool is_solid(const Geo &G, int n) {
     return G.device == FRE_FOUR_ROLLER && G.solid[n] != 0;
 }
 
-// Neighbour x + c_i of the phi/mu stencils: periodic in x and z; in y
-// periodic except for the shear device, whose stencil value behind a wall is
-// the mirror image across the half-way wall (the first fluid row).
-template <int Q>
-__device__ __forceinline__ long long stencil_nb(const Geo &G, int x, int y, int z, int i) {
-    int xn = wrapi(x + Lat<Q>::cx(i), G.nx);
-    int zn = wrapi(z + Lat<Q>::cz(i), G.nz);
-    int yn = y + Lat<Q>::cy(i);
+// A node and the index deltas of its six axis neighbours, computed once per
+// thread; every stencil and streaming index is then n plus up to three of
+// them.  Periodic in x and z; in y periodic, except for the shear device,
+// where the stencil delta across a wall is 0 (the value behind the half-way
+// wall mirrors the first fluid row) and ylo/yhi flag links that enter the
+// channel through the bottom/top wall.
+struct Site {
+    int n, x, y, z;
+    int dxp, dxm, dyp, dym, dzp, dzm;
+    bool ylo, yhi;
+};
+
+__device__ __forceinline__ Site make_site(const Geo &G, int x, int y, int z) {
+    Site s;
+    s.x = x;
+    s.y = y;
+    s.z = z;
+    s.n = node_index(G, x, y, z);
+    const int sy = G.nx, sz = G.nx * G.ny;
+    s.dxp = (x == G.nx - 1) ? 1 - G.nx : 1;
+    s.dxm = (x == 0) ? G.nx - 1 : -1;
     if (G.device == FRE_SHEAR) {
-        yn = yn < 0 ? 0 : (yn >= G.ny ? G.ny - 1 : yn);
+        s.dyp = (y == G.ny - 1) ? 0 : sy;
+        s.dym = (y == 0) ? 0 : -sy;
+        s.ylo = (y == 0);
+        s.yhi = (y == G.ny - 1);
     } else {
-        yn = wrapi(yn, G.ny);
+        s.dyp = (y == G.ny - 1) ? (1 - G.ny) * sy : sy;
+        s.dym = (y == 0) ? (G.ny - 1) * sy : -sy;
+        s.ylo = s.yhi = false;
     }
-    return node_index(G, xn, yn, zn);
+    s.dzp = (z == G.nz - 1) ? (1 - G.nz) * sz : sz;
+    s.dzm = (z == 0) ? (G.nz - 1) * sz : -sz;
+    return s;
+}
+
+// stencil neighbour x + c_i
+template <int Q>
+__device__ __forceinline__ int site_nb(const Site &s, int i) {
+    const int cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    return s.n + (cx > 0 ? s.dxp : (cx < 0 ? s.dxm : 0)) + (cy > 0 ? s.dyp : (cy < 0 ? s.dym : 0)) +
+           (cz > 0 ? s.dzp : (cz < 0 ? s.dzm : 0));
+}
+
+// streaming source x - c_i (meaningful when the link is not a wall link)
+template <int Q>
+__device__ __forceinline__ int site_src(const Site &s, int i) {
+    const int cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    return s.n + (cx > 0 ? s.dxm : (cx < 0 ? s.dxp : 0)) + (cy > 0 ? s.dym : (cy < 0 ? s.dyp : 0)) +
+           (cz > 0 ? s.dzm : (cz < 0 ? s.dzp : 0));
 }
 
 // Streaming source x - c_i.  Returns its index when it is fluid; returns -1
 // and the wall velocity at the link's wall point x - c_i/2 when it is solid.
 template <int Q, typename T>
-__device__ __forceinline__ long long pull_source(const Geo &G, int x, int y, int z, int i, T &uwx, T &uwy) {
-    int xs = x - Lat<Q>::cx(i), ys = y - Lat<Q>::cy(i), zs = z - Lat<Q>::cz(i);
+__device__ __forceinline__ int pull_source(const Geo &G, const Site &s, int i, T &uwx, T &uwy) {
+    const int cy = Lat<Q>::cy(i);
     if (G.device == FRE_SHEAR) {
-        if (ys < 0) {
+        if (cy > 0 && s.ylo) {
             uwx = T(-G.uwall);
             uwy = T(0);
             return -1;
         }
-        if (ys >= G.ny) {
+        if (cy < 0 && s.yhi) {
             uwx = T(G.uwall);
             uwy = T(0);
             return -1;
         }
-        return node_index(G, wrapi(xs, G.nx), ys, wrapi(zs, G.nz));
+        return site_src<Q>(s, i);
     }
-    long long s = node_index(G, wrapi(xs, G.nx), wrapi(ys, G.ny), wrapi(zs, G.nz));
+    const int src = site_src<Q>(s, i);
     if (G.device == FRE_FOUR_ROLLER) {
-        int k = G.solid[s];
+        const int k = G.solid[src];
         if (k) {
-            double xw = x - 0.5 * Lat<Q>::cx(i), yw = y - 0.5 * Lat<Q>::cy(i);
+            const double xw = s.x - 0.5 * Lat<Q>::cx(i), yw = s.y - 0.5 * cy;
             uwx = T(-G.om[k] * (yw - G.rcy[k]));
             uwy = T(G.om[k] * (xw - G.rcx[k]));
             return -1;
         }
     }
-    return s;
+    return src;
 }
 
-// Pre-collision populations of node n: pulled from the post-collision
+// Pre-collision populations of a node: pulled from the post-collision
 // buffer (with half-way bounce-back and the moving-wall term
 //   f_i = f*_ibar + 2 w_i rho0 (c_i . u_w)/cs^2,
 //   g_i = g*_ibar + 2 w_i phi(x, t-1) (c_i . u_w)/cs^2)
 // or read in place.
 template <int Q, int FMT, bool PULL, bool WANT_F>
-__device__ __forceinline__ void gather(const Launch &L, int x, int y, int z, long long n,
-                                       typename Fmt<FMT>::T *f, typename Fmt<FMT>::T *g) {
+__device__ __forceinline__ void gather(const Launch &L, const Site &s, typename Fmt<FMT>::T *f,
+                                       typename Fmt<FMT>::T *g) {
     using T = typename Fmt<FMT>::T;
     using P = Pop<Q, FMT>;
     const T rho0 = T(L.P.rho0);
     const long long np = L.G.np;
+    const int n = s.n;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        if (!PULL) {
+        if (!PULL || i == 0) {
             if (WANT_F) f[i] = P::ldf(L.src, np, i, n, rho0);
             g[i] = P::ldg(L.src, np, i, n);
             continue;
         }
         T uwx = T(0), uwy = T(0);
-        long long s = (i == 0) ? n : pull_source<Q, T>(L.G, x, y, z, i, uwx, uwy);
-        if (s >= 0) {
-            if (WANT_F) f[i] = P::ldf(L.src, np, i, s, rho0);
-            g[i] = P::ldg(L.src, np, i, s);
+        const int src = pull_source<Q, T>(L.G, s, i, uwx, uwy);
+        if (src >= 0) {
+            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0);
+            g[i] = P::ldg(L.src, np, i, src);
         } else {
             const int o = Lat<Q>::opp(i);
             const T cu = T(Lat<Q>::cx(i)) * uwx + T(Lat<Q>::cy(i)) * uwy;
@@ -213,7 +252,7 @@ struct Macro {
 };
 
 template <int Q, int FMT>
-__device__ __forceinline__ Macro<typename Fmt<FMT>::T> macro_of(const Launch &L, int x, int y, int z, long long n,
+__device__ __forceinline__ Macro<typename Fmt<FMT>::T> macro_of(const Launch &L, const Site &s,
                                                                  const typename Fmt<FMT>::T *f,
                                                                  const typename Fmt<FMT>::T *g) {
     using T = typename Fmt<FMT>::T;
@@ -228,12 +267,12 @@ __device__ __forceinline__ Macro<typename Fmt<FMT>::T> macro_of(const Launch &L,
         if (Lat<Q>::cz(i)) jz += T(Lat<Q>::cz(i)) * f[i];
     }
     // F = -phi grad(mu) = mu grad(phi) - grad(phi mu), isotropic gradients
-    const T *phif = static_cast<const T *>(L.phi);
-    const T *muf = static_cast<const T *>(L.mu);
+    const T *__restrict__ phif = static_cast<const T *>(L.phi);
+    const T *__restrict__ muf = static_cast<const T *>(L.mu);
     T gpx = T(0), gpy = T(0), gpz = T(0), gqx = T(0), gqy = T(0), gqz = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        long long k = stencil_nb<Q>(L.G, x, y, z, i);
+        const int k = site_nb<Q>(s, i);
         const T p = phif[k];
         const T pm = p * muf[k];
         const T w = T(Lat<Q>::w(i));
@@ -241,7 +280,7 @@ __device__ __forceinline__ Macro<typename Fmt<FMT>::T> macro_of(const Launch &L,
         if (Lat<Q>::cy(i)) { gpy += w * T(Lat<Q>::cy(i)) * p; gqy += w * T(Lat<Q>::cy(i)) * pm; }
         if (Lat<Q>::cz(i)) { gpz += w * T(Lat<Q>::cz(i)) * p; gqz += w * T(Lat<Q>::cz(i)) * pm; }
     }
-    const T mu = muf[n];
+    const T mu = muf[s.n];
     m.Fx = T(3) * (mu * gpx - gqx);
     m.Fy = T(3) * (mu * gpy - gqy);
     m.Fz = T(3) * (mu * gpz - gqz);
@@ -256,20 +295,32 @@ __device__ __forceinline__ Macro<typename Fmt<FMT>::T> macro_of(const Launch &L,
 }
 
 // ------------------------------------------------------------------ kernels
+//
+// Lattice kernels run on a 3D grid: a block of kBX x kBY threads covers kBX
+// consecutive x and kBY consecutive y at one z.
+
+constexpr int kBX = 64;
+constexpr int kBY = 4;
+static_assert(kBX * kBY == kBlock, "block shape");
+
+#define FRE_SITE_OR_RETURN(L, s)                                        \
+    const int x_ = blockIdx.x * kBX + (threadIdx.x & (kBX - 1));        \
+    const int y_ = blockIdx.y * kBY + (threadIdx.x / kBX);              \
+    const int z_ = blockIdx.z;                                          \
+    if (x_ >= (L).G.nx || y_ >= (L).G.ny) return;                      \
+    const Site s = make_site((L).G, x_, y_, z_)
 
 template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock) k_phi(Launch L) {
     using T = typename Fmt<FMT>::T;
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n || is_solid(L.G, n)) return;
-    int x, y, z;
-    decode(L.G, n, x, y, z);
+    FRE_SITE_OR_RETURN(L, s);
+    if (is_solid(L.G, s.n)) return;
     T g[Q];
-    gather<Q, FMT, PULL, false>(L, x, y, z, n, nullptr, g);
+    gather<Q, FMT, PULL, false>(L, s, nullptr, g);
     T ph = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) ph += g[i];
-    static_cast<T *>(L.phi)[n] = ph;
+    static_cast<T *>(L.phi)[s.n] = ph;
 }
 
 // Stencil values at roller solids: w-weighted mean over fluid neighbours.
@@ -277,34 +328,32 @@ template <int Q, typename T>
 __global__ void __launch_bounds__(kBlock) k_ghost(Launch L, T *field) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L.n_ghost) return;
-    long long s = L.ghost[t];
     int x, y, z;
-    decode(L.G, s, x, y, z);
+    decode(L.G, L.ghost[t], x, y, z);
+    const Site s = make_site(L.G, x, y, z);
     T num = T(0), den = T(0);
 #pragma unroll
     for (int j = 1; j < Q; ++j) {
-        long long m = stencil_nb<Q>(L.G, x, y, z, j);
+        const int m = site_nb<Q>(s, j);
         if (L.G.solid[m]) continue;
         num += T(Lat<Q>::w(j)) * field[m];
         den += T(Lat<Q>::w(j));
     }
-    field[s] = den > T(0) ? num / den : T(0);
+    field[s.n] = den > T(0) ? num / den : T(0);
 }
 
 // mu = A (phi^3 - phi) - kappa lap(phi), lap = (2/cs^2) sum w_i (phi(x+c_i) - phi(x))
 template <int Q, typename T>
 __global__ void __launch_bounds__(kBlock) k_mu(Launch L) {
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n || is_solid(L.G, n)) return;
-    int x, y, z;
-    decode(L.G, n, x, y, z);
-    const T *phi = static_cast<const T *>(L.phi);
-    const T p0 = phi[n];
+    FRE_SITE_OR_RETURN(L, s);
+    if (is_solid(L.G, s.n)) return;
+    const T *__restrict__ phi = static_cast<const T *>(L.phi);
+    const T p0 = phi[s.n];
     T lap = T(0);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) lap += T(Lat<Q>::w(i)) * (phi[stencil_nb<Q>(L.G, x, y, z, i)] - p0);
+    for (int i = 1; i < Q; ++i) lap += T(Lat<Q>::w(i)) * (phi[site_nb<Q>(s, i)] - p0);
     lap *= T(6);
-    static_cast<T *>(L.mu)[n] = T(L.P.A) * (p0 * p0 * p0 - p0) - T(L.P.kappa) * lap;
+    static_cast<T *>(L.mu)[s.n] = T(L.P.A) * (p0 * p0 * p0 - p0) - T(L.P.kappa) * lap;
 }
 
 // Fused pull + collide of f and g for one node (Algorithm 1).
@@ -312,13 +361,12 @@ template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock) k_update(Launch L) {
     using T = typename Fmt<FMT>::T;
     using P = Pop<Q, FMT>;
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n || is_solid(L.G, n)) return;
-    int x, y, z;
-    decode(L.G, n, x, y, z);
+    FRE_SITE_OR_RETURN(L, s);
+    if (is_solid(L.G, s.n)) return;
+    const int n = s.n;
     T f[Q], g[Q];
-    gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
-    const Macro<T> m = macro_of<Q, FMT>(L, x, y, z, n, f, g);
+    gather<Q, FMT, PULL, true>(L, s, f, g);
+    const Macro<T> m = macro_of<Q, FMT>(L, s, f, g);
 
     const T of = T(1.0 / L.P.tau_f), og = T(1.0 / L.P.tau_g);
     const T kf = T(1.0 - 0.5 / L.P.tau_f);
@@ -353,19 +401,17 @@ __global__ void __launch_bounds__(kBlock) k_update(Launch L) {
 template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock) k_macro(Launch L) {
     using T = typename Fmt<FMT>::T;
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n) return;
+    FRE_SITE_OR_RETURN(L, s);
     double *out = L.staging;
     const long long N = L.G.n;
+    const int n = s.n;
     if (is_solid(L.G, n)) {
         for (int k = 0; k < 6; ++k) out[k * N + n] = 0.0;
         return;
     }
-    int x, y, z;
-    decode(L.G, n, x, y, z);
     T f[Q], g[Q];
-    gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
-    const Macro<T> m = macro_of<Q, FMT>(L, x, y, z, n, f, g);
+    gather<Q, FMT, PULL, true>(L, s, f, g);
+    const Macro<T> m = macro_of<Q, FMT>(L, s, f, g);
     out[0 * N + n] = m.rho;
     out[1 * N + n] = m.ux;
     out[2 * N + n] = m.uy;
@@ -378,42 +424,18 @@ __global__ void __launch_bounds__(kBlock) k_macro(Launch L) {
 template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock) k_pull_plane(Launch L, int lat_g, int i) {
     using T = typename Fmt<FMT>::T;
-    using P = Pop<Q, FMT>;
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n) return;
-    if (is_solid(L.G, n)) {
-        L.staging[n] = 0.0;
+    FRE_SITE_OR_RETURN(L, s);
+    if (is_solid(L.G, s.n)) {
+        L.staging[s.n] = 0.0;
         return;
     }
-    int x, y, z;
-    decode(L.G, n, x, y, z);
-    const T rho0 = T(L.P.rho0);
+    T f[Q], g[Q];
+    gather<Q, FMT, PULL, true>(L, s, f, g);
     T v = T(0);
-    if (!PULL || i == 0) {
-        v = lat_g ? P::ldg(L.src, L.G.np, i, n) : P::ldf(L.src, L.G.np, i, n, rho0);
-    } else {
-        T uwx = T(0), uwy = T(0);
-        long long s = -1;
-        // unrolled lookup of the direction so the velocity is a constant
 #pragma unroll
-        for (int j = 1; j < Q; ++j) {
-            if (j != i) continue;
-            s = pull_source<Q, T>(L.G, x, y, z, j, uwx, uwy);
-            if (s >= 0) {
-                v = lat_g ? P::ldg(L.src, L.G.np, j, s) : P::ldf(L.src, L.G.np, j, s, rho0);
-            } else {
-                const int o = Lat<Q>::opp(j);
-                const T cu = T(Lat<Q>::cx(j)) * uwx + T(Lat<Q>::cy(j)) * uwy;
-                const T wi2 = T(2.0 * Lat<Q>::w(j) * 3.0);
-                if (lat_g) {
-                    v = P::ldg(L.src, L.G.np, o, n) + wi2 * static_cast<const T *>(L.phi_prev)[n] * cu;
-                } else {
-                    v = P::ldf(L.src, L.G.np, o, n, rho0) + wi2 * rho0 * cu;
-                }
-            }
-        }
-    }
-    L.staging[n] = (double)v;
+    for (int j = 0; j < Q; ++j)
+        if (j == i) v = lat_g ? g[j] : f[j];
+    L.staging[s.n] = (double)v;
 }
 
 // staging -> pre-collision population i of the source buffer.
@@ -421,13 +443,14 @@ template <int Q, int FMT>
 __global__ void __launch_bounds__(kBlock) k_load_plane(Launch L, int lat_g, int i) {
     using T = typename Fmt<FMT>::T;
     using P = Pop<Q, FMT>;
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n) return;
-    T v = is_solid(L.G, n) ? T(0) : T(L.staging[n]);
-    if (lat_g) {
-        P::stg(L.src, L.G.np, i, n, v);
-    } else {
-        P::stf(L.src, L.G.np, i, n, is_solid(L.G, n) ? T(0) : v, T(L.P.rho0));
+    FRE_SITE_OR_RETURN(L, s);
+    const int n = s.n;
+    const T v = is_solid(L.G, n) ? T(0) : T(L.staging[n]);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        if (j != i) continue;
+        if (lat_g) P::stg(L.src, L.G.np, j, n, v);
+        else P::stf(L.src, L.G.np, j, n, v, T(L.P.rho0));
     }
 }
 
@@ -435,23 +458,20 @@ __global__ void __launch_bounds__(kBlock) k_load_plane(Launch L, int lat_g, int 
 template <int Q, typename T>
 __global__ void __launch_bounds__(kBlock) k_set_phi(Launch L, int analytic, double cx, double cy, double cz,
                                                     double R) {
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n) return;
+    FRE_SITE_OR_RETURN(L, s);
     T *phi = static_cast<T *>(L.phi);
-    if (is_solid(L.G, n)) {
-        phi[n] = T(0);
+    if (is_solid(L.G, s.n)) {
+        phi[s.n] = T(0);
         return;
     }
     if (!analytic) {
-        phi[n] = T(L.staging[4 * L.G.n + n]);
+        phi[s.n] = T(L.staging[4 * L.G.n + s.n]);
         return;
     }
-    int x, y, z;
-    decode(L.G, n, x, y, z);
-    double dx = x - cx, dy = y - cy, dz = (Lat<Q>::D == 3) ? z - cz : 0.0;
+    double dx = s.x - cx, dy = s.y - cy, dz = (Lat<Q>::D == 3) ? s.z - cz : 0.0;
     double r = sqrt(dx * dx + dy * dy + dz * dz);
     double xi = sqrt(L.P.kappa / L.P.A);
-    phi[n] = T(tanh((R - r) / (sqrt(2.0) * xi)));
+    phi[s.n] = T(tanh((R - r) / (sqrt(2.0) * xi)));
 }
 
 // f = f_eq(rho, u), g = g_eq(phi, mu, u) into the source buffer.  rho, u
@@ -460,9 +480,9 @@ template <int Q, int FMT>
 __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) {
     using T = typename Fmt<FMT>::T;
     using P = Pop<Q, FMT>;
-    long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.G.n) return;
+    FRE_SITE_OR_RETURN(L, s);
     const long long N = L.G.n;
+    const int n = s.n;
     const T rho0 = T(L.P.rho0);
     if (is_solid(L.G, n)) {
 #pragma unroll
@@ -472,8 +492,6 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
         }
         return;
     }
-    int x, y, z;
-    decode(L.G, n, x, y, z);
     T rho, ux, uy, uz;
     if (from_staging) {
         rho = T(L.staging[0 * N + n]);
@@ -482,7 +500,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
         uz = T(L.staging[3 * N + n]);
     } else {
         rho = rho0;
-        ux = (L.G.device == FRE_SHEAR) ? T(L.G.uwall * (2.0 * (y + 0.5) / L.G.ny - 1.0)) : T(0);
+        ux = (L.G.device == FRE_SHEAR) ? T(L.G.uwall * (2.0 * (s.y + 0.5) / L.G.ny - 1.0)) : T(0);
         uy = T(0);
         uz = T(0);
     }
@@ -551,14 +569,14 @@ __global__ void __launch_bounds__(kBlock) k_obs1(Launch L) {
     double v[kObsVals];
 #pragma unroll
     for (int k = 0; k < kObsVals; ++k) v[k] = 0.0;
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.G.n;
-         n += (long long)gridDim.x * blockDim.x) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L.G.n; n += gridDim.x * blockDim.x) {
         if (is_solid(L.G, n)) continue;
         int x, y, z;
         decode(L.G, n, x, y, z);
+        const Site s = make_site(L.G, x, y, z);
         T f[Q], g[Q];
-        gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
-        const Macro<T> m = macro_of<Q, FMT>(L, x, y, z, n, f, g);
+        gather<Q, FMT, PULL, true>(L, s, f, g);
+        const Macro<T> m = macro_of<Q, FMT>(L, s, f, g);
         const double rho = m.rho, ph = m.phi;
         const double u = sqrt((double)m.ux * m.ux + (double)m.uy * m.uy + (double)m.uz * m.uz);
         v[0] += rho;
@@ -602,8 +620,7 @@ __global__ void __launch_bounds__(kBlock) k_obs2(Launch L, const double *tot) {
     const double W = tot[3];
     const double X = W > 0 ? tot[5] / W : 0.0, Y = W > 0 ? tot[6] / W : 0.0, Z = W > 0 ? tot[7] / W : 0.0;
     const T *phi = static_cast<const T *>(L.phi);
-    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.G.n;
-         n += (long long)gridDim.x * blockDim.x) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L.G.n; n += gridDim.x * blockDim.x) {
         if (is_solid(L.G, n)) continue;
         const double ph = phi[n];
         if (!(ph > 0.0)) continue;
@@ -623,16 +640,15 @@ __global__ void __launch_bounds__(kBlock) k_obs2(Launch L, const double *tot) {
 
 // Pressure at a node: cs^2 rho + phi mu - (A/4)(phi^2 - 1)^2.
 template <int Q, int FMT, bool PULL>
-__device__ double pressure_at(const Launch &L, long long n) {
+__device__ double pressure_at(const Launch &L, int x, int y, int z) {
     using T = typename Fmt<FMT>::T;
-    int x, y, z;
-    decode(L.G, n, x, y, z);
+    const Site s = make_site(L.G, x, y, z);
     T f[Q], g[Q];
-    gather<Q, FMT, PULL, true>(L, x, y, z, n, f, g);
+    gather<Q, FMT, PULL, true>(L, s, f, g);
     double rho = 0.0;
     for (int i = 0; i < Q; ++i) rho += (double)f[i];
-    const double ph = static_cast<const T *>(L.phi)[n];
-    const double mu = static_cast<const T *>(L.mu)[n];
+    const double ph = static_cast<const T *>(L.phi)[s.n];
+    const double mu = static_cast<const T *>(L.mu)[s.n];
     return rho / 3.0 + ph * mu - 0.25 * L.P.A * (ph * ph - 1.0) * (ph * ph - 1.0);
 }
 
@@ -668,10 +684,8 @@ __global__ void k_obs_final(Launch L, const double *t1, const double *t2) {
         cy = cy < 0 ? 0 : (cy >= G.ny ? G.ny - 1 : cy);
         int cz = wrapi((int)llround(X[2]), G.nz);
         int fz = G.nz > 1 ? wrapi(cz + G.nz / 2, G.nz) : 0;
-        const long long nc = node_index(G, cx, cy, cz);
-        const long long nf = node_index(G, wrapi(cx + G.nx / 2, G.nx), cy, fz);
-        o->p_centre = pressure_at<Q, FMT, PULL>(L, nc);
-        o->p_far = pressure_at<Q, FMT, PULL>(L, nf);
+        o->p_centre = pressure_at<Q, FMT, PULL>(L, cx, cy, cz);
+        o->p_far = pressure_at<Q, FMT, PULL>(L, wrapi(cx + G.nx / 2, G.nx), cy, fz);
         o->dp = o->p_centre - o->p_far;
     }
     o->status = bad ? 1 : (o->max_u > 0.3 ? 2 : 0);
@@ -680,23 +694,26 @@ __global__ void k_obs_final(Launch L, const double *t1, const double *t2) {
 // ------------------------------------------------------------ launchers
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+inline dim3 grid3(const Geo &G) {
+    return dim3((unsigned)((G.nx + kBX - 1) / kBX), (unsigned)((G.ny + kBY - 1) / kBY), (unsigned)G.nz);
+}
 
 template <int Q, int FMT>
 struct Launchers {
     using T = typename Fmt<FMT>::T;
 
     static void phi(const Launch &L, bool pull) {
-        if (pull) k_phi<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
-        else k_phi<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+        if (pull) k_phi<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+        else k_phi<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
     }
     static void ghost(const Launch &L, void *field) {
         if (L.n_ghost > 0)
             k_ghost<Q, T><<<grid_for(L.n_ghost), kBlock, 0, L.stream>>>(L, static_cast<T *>(field));
     }
-    static void mu(const Launch &L) { k_mu<Q, T><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L); }
+    static void mu(const Launch &L) { k_mu<Q, T><<<grid3(L.G), kBlock, 0, L.stream>>>(L); }
     static void update(const Launch &L, bool pull) {
-        if (pull) k_update<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
-        else k_update<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+        if (pull) k_update<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+        else k_update<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
     }
     static void obs(const Launch &L, bool pull) {
         const int nb = L.red_blocks;
@@ -711,25 +728,21 @@ struct Launchers {
         else k_obs_final<Q, FMT, false><<<1, 32, 0, L.stream>>>(L, t1, t2);
     }
     static void macro(const Launch &L, bool pull) {
-        if (pull) k_macro<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
-        else k_macro<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L);
+        if (pull) k_macro<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+        else k_macro<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
     }
     static void pull_plane(const Launch &L, bool pull, int lat_g, int i) {
-        if (pull) k_pull_plane<Q, FMT, true><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, lat_g, i);
-        else k_pull_plane<Q, FMT, false><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, lat_g, i);
+        if (pull) k_pull_plane<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L, lat_g, i);
+        else k_pull_plane<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L, lat_g, i);
     }
     static void load_plane(const Launch &L, int lat_g, int i) {
-        k_load_plane<Q, FMT><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, lat_g, i);
+        k_load_plane<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L, lat_g, i);
     }
     static void set_phi(const Launch &L, int analytic, double cx, double cy, double cz, double R) {
-        k_set_phi<Q, T><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, analytic, cx, cy, cz, R);
+        k_set_phi<Q, T><<<grid3(L.G), kBlock, 0, L.stream>>>(L, analytic, cx, cy, cz, R);
     }
     static void init_eq(const Launch &L, int from_staging) {
-        k_init_eq<Q, FMT><<<grid_for(L.G.n), kBlock, 0, L.stream>>>(L, from_staging);
-    }
-    static const KernelSet *set() {
-        static const KernelSet ks = {phi, ghost, mu, update, obs, macro, pull_plane, load_plane, set_phi, init_eq};
-        return &ks;
+        k_init_eq<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L, from_staging);
     }
 };
 

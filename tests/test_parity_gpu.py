@@ -44,8 +44,17 @@ def pair(fre, orc, lattice, device, nx, ny, nz, precision="fp64", **kw):
 
 
 def compare_fields(sim, o, tol, fields=FIELDS):
+    """Relative L-inf per field; the velocity components share one scale,
+    max |u| of the oracle (a component that vanishes by symmetry has no
+    scale of its own)."""
     a, b = sim.fields(), o.fields()
-    errs = {k: rel_linf(a[k], b[k]) for k in fields}
+    uscale = max(np.abs(b[k]).max() for k in ("ux", "uy", "uz"))
+    errs = {}
+    for k in fields:
+        if k in ("ux", "uy", "uz"):
+            errs[k] = np.abs(a[k] - b[k]).max() / uscale
+        else:
+            errs[k] = rel_linf(a[k], b[k])
     bad = {k: v for k, v in errs.items() if not v < tol}
     assert not bad, f"relative L-inf above {tol}: {bad} (all: {errs})"
     return errs
@@ -146,12 +155,17 @@ def test_fp32_vs_fp64_oracle_d3q19(fre, orc):
 
 
 def test_fp32_vs_fp64_oracle_d2q9_c0(fre, orc):
+    """FP32 on the 100x50 D2Q9 case.  Plain FP32 populations (up to 4/9) carry
+    an absolute rounding of ~3e-8 per value; after 500 steps u is off by
+    ~1e-7 absolute, i.e. ~1e-5 of the small wall speed 0.01.  Bound: 3e-5
+    relative for u, 1e-5 for rho and phi."""
     sim, o = pair(fre, orc, "d2q9", "shear", 100, 50, 1, precision="fp32", u_wall=0.01)
     sim.init_droplet(49.5, 24.5, 0.0, 10.0)
     o.init_droplet(49.5, 24.5, 0.0, 10.0)
     sim.step(500)
     o.step(500)
-    compare_fields(sim, o, 1e-5)
+    compare_fields(sim, o, 1e-5, ("rho", "phi"))
+    compare_fields(sim, o, 3e-5, ("ux", "uy"))
     sim.close()
 
 

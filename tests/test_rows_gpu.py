@@ -1,0 +1,102 @@
+"""The row kernels (x-rows staged in shared memory with 16-byte cp.async
+copies; the hot path of the shear and periodic devices in FP32 and 16-bit
+storage) against the per-node kernels and the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_2212_01617_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fre():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_01617_gb300 import build
+    build.build()
+    import paper_2212_01617_gb300 as fre
+    return fre
+
+
+def errs(a, b):
+    uscale = max(np.abs(b[k]).max() for k in ("ux", "uy", "uz"))
+    out = {}
+    for k in ("rho", "ux", "uy", "uz", "phi"):
+        scale = uscale if k.startswith("u") else np.abs(b[k]).max()
+        out[k] = np.abs(a[k] - b[k]).max() / scale
+    return out
+
+
+CASES = [
+    # lattice, device, nx, ny, nz, kwargs
+    ("d3q19", "shear", 48, 20, 12, dict(u_wall=0.03, tau_f=2.0, tau_g=2.0, gamma_mob=0.5)),
+    ("d3q19", "periodic", 32, 12, 10, dict(tau_f=0.8, tau_g=1.2, gamma_mob=0.7)),
+    ("d2q9", "shear", 96, 40, 1, dict(u_wall=0.02)),
+]
+
+
+def make(fre, lattice, device, nx, ny, nz, precision, flags=0, **kw):
+    args = dict(tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0, rho0=1.0)
+    args.update(kw)
+    return fre.Simulation(lattice=lattice, precision=precision, device=device, nx=nx, ny=ny, nz=nz,
+                          flags=flags, **args)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}")
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
+def test_row_kernels_match_per_node_kernels(fre, case, precision):
+    lattice, device, nx, ny, nz, kw = case
+    rows = make(fre, lattice, device, nx, ny, nz, precision, **kw)
+    gen = make(fre, lattice, device, nx, ny, nz, precision, flags=1, **kw)
+    assert rows.row_kernels and not gen.row_kernels
+    c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, min(nx, ny) / 4)
+    for s in (rows, gen):
+        s.init_droplet(*c)
+        s.step(200)
+    e = errs(rows.fields(), gen.fields())
+    # same arithmetic in both; only the contraction/rounding order may differ
+    tol = 1e-5 if precision == "fp32" else 2e-3
+    assert max(e.values()) < tol, e
+    rows.close()
+    gen.close()
+
+
+def test_row_kernels_random_populations_fp32(fre, orc):
+    """Non-equilibrium seeded populations through the row path vs the oracle."""
+    shape = (6, 8, 24)
+    f, g = inputs.random_populations(19, shape, seed=11)
+    sim = make(fre, "d3q19", "periodic", 24, 8, 6, "fp32", tau_f=0.7, tau_g=1.1, A=0.03, kappa=0.05)
+    assert sim.row_kernels
+    o = orc.Oracle(1, 2, 24, 8, 6, 0.7, 1.1, 0.03, 0.05, 1.0, 0.0, 1.0)
+    sim.load_populations(f, g)
+    o.load_populations(f, g)
+    sim.step(60)
+    o.step(60)
+    a, b = sim.fields(), o.fields()
+    # the random velocities relax towards rest, so u is bounded in absolute
+    # terms: FP32 rounding of populations of size ~0.3 is ~2e-8
+    for k in ("rho", "phi"):
+        assert np.abs(a[k] - b[k]).max() / np.abs(b[k]).max() < 1e-5, k
+    for k in ("ux", "uy", "uz"):
+        assert np.abs(a[k] - b[k]).max() < 1e-6, k
+
+
+@pytest.mark.parametrize("precision,tol", [("fp16dev", 3e-3), ("bf16dev", 2e-2)])
+def test_16bit_storage_vs_fp64_oracle(fre, orc, precision, tol):
+    """16-bit deviation storage (FP32 arithmetic) vs the FP64 oracle after 500
+    steps of the D3Q19 shear droplet: relative L-inf of rho, u, phi."""
+    nx, ny, nz = 48, 24, 16
+    kw = dict(u_wall=0.03, tau_f=2.0, tau_g=2.0, gamma_mob=0.5)
+    sim = make(fre, "d3q19", "shear", nx, ny, nz, precision, **kw)
+    assert sim.row_kernels
+    o = orc.Oracle(1, 0, nx, ny, nz, 2.0, 2.0, 0.04, 0.04, 0.5, 0.03, 1.0)
+    c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, 6.0)
+    sim.init_droplet(*c)
+    o.init_droplet(*c)
+    sim.step(500)
+    o.step(500)
+    e = errs(sim.fields(), o.fields())
+    print(precision, e)
+    assert max(e.values()) < tol, e
