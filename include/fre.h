@@ -95,6 +95,13 @@ typedef struct {
  * kernels stage whole x-rows in shared memory; both compute the same
  * update).  For validation. */
 #define FRE_FLAG_GENERIC_KERNELS 1u
+/* Run the update on x-chunk work units instead of whole x-rows (both stage
+ * their rows in shared memory with bulk copies; for validation/tuning). */
+#define FRE_FLAG_CHUNKED_UPDATE 2u
+/* Bits 8..15: log2 of the x-chunk width of the row kernels (0 = automatic:
+ * 128 when nx allows it, else the whole row).  A tuning knob; every valid
+ * width computes the same update. */
+#define FRE_FLAG_CHUNK_SHIFT 8
 
 /* Observables of the state at the current step, from the pre-collision
  * populations; sums in FP64 over fluid nodes. */

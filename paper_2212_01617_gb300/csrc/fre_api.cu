@@ -35,6 +35,7 @@ struct fre_ctx {
     int red_blocks = 0;
     fre_obs *obs_dev = nullptr;
     fre_obs *obs_host = nullptr;
+    int *err_dev = nullptr;  // set by a kernel whose bounded wait timed out
     double *staging = nullptr;
     std::vector<void *> allocs;
     int cur = 0;        // buffer holding the state
@@ -42,6 +43,8 @@ struct fre_ctx {
     bool local = true;  // state is pre-collision (no streaming pending)
     bool initialised = false;
     bool rows = false;  // the row kernels run the hot path
+    int row_w = 0;      // their chunk width
+    bool fullrow = false;  // the update runs on the full-row kernel
     long long step = 0;
 };
 
@@ -200,6 +203,8 @@ fre::Launch launch_of(fre_ctx *c) {
     L.obs = c->obs_dev;
     L.staging = c->staging;
     L.stream = c->stream;
+    L.W = c->row_w;
+    L.err = c->err_dev;
     return L;
 }
 
@@ -214,6 +219,18 @@ void current_phi_mu(fre_ctx *c, const fre::Launch &L) {
 fre_status check_launch(const char *where) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(FRE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+    return FRE_OK;
+}
+
+// After a synchronisation: report a kernel whose bounded wait timed out.
+fre_status check_device_error(fre_ctx *c) {
+    int e = 0;
+    if (cudaMemcpy(&e, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(FRE_ERR_CUDA, "reading the device error word: %s", cudaGetErrorString(cudaGetLastError()));
+    if (e) {
+        cudaMemset(c->err_dev, 0, sizeof(int));
+        return fail(FRE_ERR_CUDA, "a pipelined kernel gave up waiting for its bulk copies (code %d)", e);
+    }
     return FRE_OK;
 }
 
@@ -323,6 +340,10 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
         st = dev_alloc(c, &o, sizeof(fre_obs));
         if (st != FRE_OK) return bail(st);
         c->obs_dev = static_cast<fre_obs *>(o);
+        void *e;
+        st = dev_alloc(c, &e, sizeof(int) * 4);
+        if (st != FRE_OK) return bail(st);
+        c->err_dev = static_cast<int *>(e);
     }
     long long rb = (s.n + 255) / 256;
     c->red_blocks = (int)(rb < 608 ? (rb < 1 ? 1 : rb) : 608);
@@ -355,7 +376,13 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
             return bail(fail(FRE_ERR_CUDA, "geometry upload: %s", cudaGetErrorString(cudaGetLastError())));
     }
     c->G.solid = c->solid;
-    c->rows = !(p->flags & FRE_FLAG_GENERIC_KERNELS) && c->ks->rows_usable && c->ks->rows_usable(c->G);
+    if (!(p->flags & FRE_FLAG_GENERIC_KERNELS) && c->ks->row_width) {
+        const unsigned sh = (p->flags >> FRE_FLAG_CHUNK_SHIFT) & 0xffu;
+        c->row_w = c->ks->row_width(c->G, sh ? (1 << sh) : 0);
+        c->rows = c->row_w > 0;
+    }
+    c->fullrow = c->rows && !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable &&
+                 c->ks->fullrow_usable(c->G);
     cudaGetLastError();
     *out = c;
     return FRE_OK;
@@ -448,7 +475,7 @@ fre_status fre_store_populations(fre_ctx *c, double *f, double *g) {
     s = check_launch("fre_store_populations");
     if (s != FRE_OK) return s;
     FRE_CUDA(cudaStreamSynchronize(c->stream));
-    return FRE_OK;
+    return check_device_error(c);
 }
 
 fre_status fre_step(fre_ctx *c, int nsteps) {
@@ -459,7 +486,11 @@ fre_status fre_step(fre_ctx *c, int nsteps) {
     for (int t = 0; t < nsteps; ++t) {
         fre::Launch L = launch_of(c);
         const bool pull = !c->local;
-        if (c->rows) {
+        if (c->fullrow) {
+            c->ks->phi_fullrow(L, pull);
+            c->ks->mu_fullrow(L);
+            c->ks->update_fullrow(L, pull);
+        } else if (c->rows) {
             c->ks->phi_rows(L, pull);
             c->ks->mu_rows(L);
             c->ks->update_rows(L, pull);
@@ -495,17 +526,20 @@ fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launche
     for (int t = 0; t < nsteps; ++t) {
         fre::Launch L = launch_of(c);
         const bool pull = !c->local;
-        if (c->rows) c->ks->phi_rows(L, pull);
+        if (c->fullrow) c->ks->phi_fullrow(L, pull);
+        else if (c->rows) c->ks->phi_rows(L, pull);
         else c->ks->phi(L, pull);
         ++nl;
         cudaEventRecord(ev[3 * t + 1], c->stream);
         if (c->n_ghost) { c->ks->ghost(L, L.phi); ++nl; }
-        if (c->rows) c->ks->mu_rows(L);
+        if (c->fullrow) c->ks->mu_fullrow(L);
+        else if (c->rows) c->ks->mu_rows(L);
         else c->ks->mu(L);
         ++nl;
         if (c->n_ghost) { c->ks->ghost(L, L.mu); ++nl; }
         cudaEventRecord(ev[3 * t + 2], c->stream);
-        if (c->rows) c->ks->update_rows(L, pull);
+        if (c->fullrow) c->ks->update_fullrow(L, pull);
+        else if (c->rows) c->ks->update_rows(L, pull);
         else c->ks->update(L, pull);
         ++nl;
         cudaEventRecord(ev[3 * t + 3], c->stream);
@@ -532,7 +566,7 @@ fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launche
     if (launches) *launches = nl;
     if (s != FRE_OK) return s;
     if (e != cudaSuccess) return fail(FRE_ERR_CUDA, "fre_step_timed: %s", cudaGetErrorString(e));
-    return FRE_OK;
+    return check_device_error(c);
 }
 
 fre_status fre_copy_fields(fre_ctx *c, double *rho, double *ux, double *uy, double *uz, double *phi, double *mu) {
@@ -553,7 +587,7 @@ fre_status fre_copy_fields(fre_ctx *c, double *rho, double *ux, double *uy, doub
     s = check_launch("fre_copy_fields");
     if (s != FRE_OK) return s;
     FRE_CUDA(cudaStreamSynchronize(c->stream));
-    return FRE_OK;
+    return check_device_error(c);
 }
 
 fre_status fre_observables(fre_ctx *c, fre_obs *out) {
@@ -568,6 +602,8 @@ fre_status fre_observables(fre_ctx *c, fre_obs *out) {
     s = check_launch("fre_observables");
     if (s != FRE_OK) return s;
     FRE_CUDA(cudaStreamSynchronize(c->stream));
+    s = check_device_error(c);
+    if (s != FRE_OK) return s;
     *out = *c->obs_host;
     out->step = c->step;
     if (out->status != 0)

@@ -1,14 +1,14 @@
 // Kernel instantiations for the D2Q9 lattice (all storage formats).
-#include "fre_rows.cuh"
+#include "fre_ws.cuh"
 
 namespace fre {
 
 const KernelSet *kernels_d2q9(int precision) {
     switch (precision) {
-        case FRE_FP64: return kernel_set<9, FRE_FP64>();
-        case FRE_FP32: return kernel_set<9, FRE_FP32>();
-        case FRE_FP16DEV: return kernel_set<9, FRE_FP16DEV>();
-        case FRE_BF16DEV: return kernel_set<9, FRE_BF16DEV>();
+        case FRE_FP64: return kernel_set_ws<9, FRE_FP64>();
+        case FRE_FP32: return kernel_set_ws<9, FRE_FP32>();
+        case FRE_FP16DEV: return kernel_set_ws<9, FRE_FP16DEV>();
+        case FRE_BF16DEV: return kernel_set_ws<9, FRE_BF16DEV>();
         default: return nullptr;
     }
 }

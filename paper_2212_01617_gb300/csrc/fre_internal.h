@@ -48,6 +48,8 @@ struct Launch {
     double *red;           // reduction scratch
     int red_blocks;
     fre_obs *obs;          // device observables
+    int W;                 // chunk width of the row kernels
+    int *err;              // device error word (pipeline wait timed out)
     double *staging;       // FP64 staging of host I/O (n doubles per field)
     cudaStream_t stream;
 };
@@ -68,10 +70,15 @@ struct KernelSet {
     void (*set_phi)(const Launch &, int analytic, double cx, double cy, double cz, double R);
     void (*init_eq)(const Launch &, int from_staging);  // f = f_eq, g = g_eq into src
     // row kernels of the hot path (nullptr where the format has none)
-    bool (*rows_usable)(const Geo &);
+    int (*row_width)(const Geo &, int pref);  // chunk width of the row kernels, 0 = n/a
     void (*phi_rows)(const Launch &, bool pull);
     void (*mu_rows)(const Launch &);
     void (*update_rows)(const Launch &, bool pull);
+    // full-row variant of the update (one bulk copy per population row)
+    bool (*fullrow_usable)(const Geo &);
+    void (*update_fullrow)(const Launch &, bool pull);
+    void (*phi_fullrow)(const Launch &, bool pull);
+    void (*mu_fullrow)(const Launch &);
 };
 
 const KernelSet *kernels_d2q9(int precision);

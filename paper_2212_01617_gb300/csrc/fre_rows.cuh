@@ -45,31 +45,53 @@ __host__ __device__ constexpr int n_stencil_rows() {
     return Lat<Q>::D == 2 ? 3 : 9;
 }
 
-// Row layout of staged populations: f rows then g rows; in 16-bit formats
-// the g0 row is FP32 and sits after the 16-bit rows.
+// Shared-memory layout of one work unit: a chunk of W consecutive x of one
+// row (y, z).  Each staged row holds the W chunk values plus a 16-byte halo
+// on each side (H = 16 / element size elements), filled from the periodic
+// neighbours in x, so a shift by c_ix is a plain offset.  f rows come first,
+// then g rows (in 16-bit formats rows 1..q-1, then the FP32 g0 row), then
+// the FP32 phi and mu stencil rows.
 template <int Q, int FMT>
-struct RowLayout {
+struct ChunkLayout {
     using S = typename Fmt<FMT>::S;
     static constexpr bool DEV = Fmt<FMT>::DEV;
-    __host__ __device__ static size_t pop_bytes(int nx) {
-        return DEV ? (size_t)(2 * Q - 1) * nx * sizeof(S) + (size_t)nx * 4 : (size_t)2 * Q * nx * sizeof(S);
-    }
-    __host__ __device__ static size_t field_off(int nx) { return (pop_bytes(nx) + 127) / 128 * 128; }
-    __host__ __device__ static size_t total_bytes(int nx, int n_field_rows) {
-        return field_off(nx) + (size_t)n_field_rows * nx * 4;
-    }
+    static constexpr int HS = 16 / (int)sizeof(S);
+    __host__ __device__ static unsigned rw_s(int W) { return (unsigned)((W + 2 * HS) * sizeof(S)); }
+    __host__ __device__ static unsigned rw_f(int W) { return (unsigned)((W + 8) * 4); }
+    __host__ __device__ static unsigned g_off(int W) { return Q * rw_s(W); }
+    // offset of the FP32 g0 row from the start of the g rows (16-bit formats)
+    __host__ __device__ static unsigned g0_rel(int W) { return (Q - 1) * rw_s(W); }
+    __host__ __device__ static unsigned g_bytes(int W) { return DEV ? g0_rel(W) + rw_f(W) : Q * rw_s(W); }
+    __host__ __device__ static unsigned pop_bytes(int W) { return g_off(W) + g_bytes(W); }
+    __host__ __device__ static unsigned field_off(int W) { return (pop_bytes(W) + 127u) / 128u * 128u; }
+    __host__ __device__ static unsigned total(int W, int nfield) { return field_off(W) + nfield * rw_f(W); }
 };
 
-// Issue the cp.async copies of `nrows` rows described by (src, dst, bytes):
-// warp w copies rows w, w + nwarps, ...; its lanes take the 16-byte chunks.
-__device__ __forceinline__ void stage_rows(const char *const *src, const unsigned *dst_off, const unsigned *bytes,
-                                           int nrows, unsigned char *smem) {
+// One staged row: global address of its x = 0 element, smem byte offset of
+// the staged row (halo included) and element size.
+struct RowDesc {
+    const char *src;
+    unsigned dst;
+    unsigned esz;
+};
+
+// Issue the cp.async copies of `nrows` staged rows for the chunk [x0, x0+W):
+// warp w takes rows w, w + nwarps, ...; lane c copies 16-byte chunk c, where
+// chunk 0 is the left halo, chunk C-1 the right halo.
+__device__ __forceinline__ void stage_chunk(const RowDesc *rows, int nrows, unsigned char *smem, int x0, int W,
+                                            int nx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int r = warp; r < nrows; r += nw) {
-        const unsigned chunks = bytes[r] >> 4;
-        const char *s = src[r];
-        unsigned char *d = smem + dst_off[r];
-        for (unsigned c = lane; c < chunks; c += 32) cp_async16(d + 16 * c, s + 16 * c);
+        const RowDesc d = rows[r];
+        const int H = 16 / (int)d.esz;
+        const int C = (int)(W * d.esz / 16) + 2;
+        for (int c = lane; c < C; c += 32) {
+            int xg;
+            if (c == 0) xg = x0 >= H ? x0 - H : nx - H;
+            else if (c == C - 1) xg = (x0 + W < nx) ? x0 + W : 0;
+            else xg = x0 + (c - 1) * H;
+            cp_async16(smem + d.dst + 16 * c, d.src + (size_t)xg * d.esz);
+        }
     }
 }
 
@@ -91,159 +113,185 @@ __device__ __forceinline__ bool src_row(const Geo &G, int y, int z, int i, bool 
     return true;
 }
 
-// Build the copy table of the population rows of lattice `lat` (0 f, 1 g)
-// for row (y, z).  Wall links stage the local row of the opposite
-// population.  Returns the wall-link mask.
+// Staged row of population i of lattice `lat` (0 f, 1 g) for the work row
+// (y, z); smem offset relative to `base` (the start of this lattice's rows).
+// A wall link stages the local row of the opposite population and sets
+// *wall.
 template <int Q, int FMT>
-__device__ unsigned pop_table(const Launch &L, const Buf &b, int lat, int y, int z, bool pull, const char **src,
-                              unsigned *dst, unsigned *bytes, int base_slot) {
+__device__ __forceinline__ RowDesc pop_row(const Launch &L, const Buf &b, int lat, int i, int y, int z, bool pull,
+                                           int W, unsigned base, bool *wall) {
     using S = typename Fmt<FMT>::S;
-    const int nx = L.G.nx;
-    unsigned wall = 0;
-    for (int i = 0; i < Q; ++i) {
-        int ys, zs, pi = i;
-        if (!src_row<Q>(L.G, y, z, i, pull, ys, zs)) {
-            wall |= 1u << i;
-            ys = y;
-            zs = z;
-            pi = Lat<Q>::opp(i);
-        }
-        const size_t row = ((size_t)zs * L.G.ny + ys) * nx;
-        const int slot = base_slot + i;
-        if (lat == 0) {
-            src[slot] = static_cast<const char *>(b.f) + ((size_t)pi * L.G.np + row) * sizeof(S);
-            dst[slot] = (unsigned)((size_t)i * nx * sizeof(S));
-            bytes[slot] = (unsigned)(nx * sizeof(S));
-        } else if (!Fmt<FMT>::DEV) {
-            src[slot] = static_cast<const char *>(b.g) + ((size_t)pi * L.G.np + row) * sizeof(S);
-            dst[slot] = (unsigned)((size_t)(Q + i) * nx * sizeof(S));
-            bytes[slot] = (unsigned)(nx * sizeof(S));
-        } else if (pi == 0) {
-            src[slot] = reinterpret_cast<const char *>(b.g0 + row);
-            dst[slot] = (unsigned)((size_t)(2 * Q - 1) * nx * sizeof(S));
-            bytes[slot] = (unsigned)(nx * 4);
-        } else {
-            src[slot] = static_cast<const char *>(b.g) + ((size_t)(pi - 1) * L.G.np + row) * sizeof(S);
-            // slot i of the 16-bit g rows; i = 0 can only carry the g0 row
-            dst[slot] = (unsigned)((size_t)(Q + i - 1) * nx * sizeof(S));
-            bytes[slot] = (unsigned)(nx * sizeof(S));
-        }
+    using CL = ChunkLayout<Q, FMT>;
+    int ys, zs, pi = i;
+    *wall = false;
+    if (!src_row<Q>(L.G, y, z, i, pull, ys, zs)) {
+        *wall = true;
+        ys = y;
+        zs = z;
+        pi = Lat<Q>::opp(i);
     }
-    return wall;
+    const size_t row = ((size_t)zs * L.G.ny + ys) * L.G.nx;
+    RowDesc d;
+    if (lat == 0) {
+        d.src = static_cast<const char *>(b.f) + ((size_t)pi * L.G.np + row) * sizeof(S);
+        d.dst = base + i * CL::rw_s(W);
+        d.esz = sizeof(S);
+    } else if (!Fmt<FMT>::DEV) {
+        d.src = static_cast<const char *>(b.g) + ((size_t)pi * L.G.np + row) * sizeof(S);
+        d.dst = base + i * CL::rw_s(W);
+        d.esz = sizeof(S);
+    } else if (pi == 0) {  // only for i = 0 (opp(i) = 0 iff i = 0)
+        d.src = reinterpret_cast<const char *>(b.g0 + row);
+        d.dst = base + CL::g0_rel(W);
+        d.esz = 4;
+    } else {
+        d.src = static_cast<const char *>(b.g) + ((size_t)(pi - 1) * L.G.np + row) * sizeof(S);
+        d.dst = base + (i - 1) * CL::rw_s(W);
+        d.esz = sizeof(S);
+    }
+    return d;
 }
 
-// Read population i of f / g at x from the staged rows.  fbase points at
-// the f rows, gbase at the g rows (Q rows of the storage type; in 16-bit
-// formats rows 1..Q-1 come first and the FP32 g0 row last).
+// Stencil rows (y + cy, z + cz) of a FP32 field, slot k, at smem base.
+template <int Q>
+__device__ __forceinline__ RowDesc field_row(const Launch &L, const float *field, int y, int z, int k, int W,
+                                             unsigned base) {
+    const int cy = (Lat<Q>::D == 2 ? k : k % 3) - 1, cz = Lat<Q>::D == 2 ? 0 : k / 3 - 1;
+    int yn = y + cy;
+    yn = (L.G.device == FRE_SHEAR) ? (yn < 0 ? 0 : (yn >= L.G.ny ? L.G.ny - 1 : yn)) : wrapi(yn, L.G.ny);
+    const int zn = wrapi(z + cz, L.G.nz);
+    RowDesc d;
+    d.src = reinterpret_cast<const char *>(field + ((size_t)zn * L.G.ny + yn) * L.G.nx);
+    d.dst = base + (unsigned)k * (unsigned)((W + 8) * 4);
+    d.esz = 4;
+    return d;
+}
+
+// Staged values at local x (-1 <= xl <= W).  fbase / gbase: start of the
+// f / g rows.
 template <int Q, int FMT>
-__device__ __forceinline__ float row_f(const unsigned char *fbase, int nx, int i, int xs, float rho0) {
+__device__ __forceinline__ float row_f(const unsigned char *fbase, int W, int i, int xl, float rho0) {
     using S = typename Fmt<FMT>::S;
-    const S v = reinterpret_cast<const S *>(fbase)[(size_t)i * nx + xs];
+    using CL = ChunkLayout<Q, FMT>;
+    const S v = reinterpret_cast<const S *>(fbase + i * CL::rw_s(W))[CL::HS + xl];
     if constexpr (Fmt<FMT>::DEV) return to_float(v) + float(Lat<Q>::w(i)) * rho0;
     else return v;
 }
+// raw staged f of slot i (a wall slot holds population opp(i))
 template <int Q, int FMT>
-__device__ __forceinline__ float row_g(const unsigned char *gbase, int nx, int i, int xs) {
+__device__ __forceinline__ float row_f_slot(const unsigned char *fbase, int W, int i, int xl, float wr) {
     using S = typename Fmt<FMT>::S;
+    using CL = ChunkLayout<Q, FMT>;
+    const S v = reinterpret_cast<const S *>(fbase + i * CL::rw_s(W))[CL::HS + xl];
+    if constexpr (Fmt<FMT>::DEV) return to_float(v) + wr;
+    else return v;
+}
+template <int Q, int FMT>
+__device__ __forceinline__ float row_g(const unsigned char *gbase, int W, int i, int xl) {
+    using S = typename Fmt<FMT>::S;
+    using CL = ChunkLayout<Q, FMT>;
     if constexpr (Fmt<FMT>::DEV) {
-        if (i == 0) return reinterpret_cast<const float *>(gbase + (size_t)(Q - 1) * nx * sizeof(S))[xs];
-        return to_float(reinterpret_cast<const S *>(gbase)[(size_t)(i - 1) * nx + xs]);
+        if (i == 0) return reinterpret_cast<const float *>(gbase + CL::g0_rel(W))[4 + xl];
+        return to_float(reinterpret_cast<const S *>(gbase + (i - 1) * CL::rw_s(W))[CL::HS + xl]);
     } else {
-        return reinterpret_cast<const S *>(gbase)[(size_t)i * nx + xs];
+        return reinterpret_cast<const S *>(gbase + i * CL::rw_s(W))[CL::HS + xl];
     }
+}
+__device__ __forceinline__ float row_field(const unsigned char *fbase, int W, int k, int xl) {
+    return reinterpret_cast<const float *>(fbase + (unsigned)k * (unsigned)((W + 8) * 4))[4 + xl];
+}
+
+// work unit of block b: chunk c of row r
+struct Unit {
+    int y, z, x0;
+    size_t row;  // global index of (0, y, z)
+};
+__device__ __forceinline__ Unit unit_of(const Geo &G, int W) {
+    const int nch = G.nx / W;
+    const int b = blockIdx.x;
+    const int r = b / nch;
+    Unit u;
+    u.x0 = (b - r * nch) * W;
+    u.y = r % G.ny;
+    u.z = r / G.ny;
+    u.row = (size_t)r * G.nx;
+    return u;
 }
 
 // ----------------------------------------------------------- phi pass
 
 template <int Q, int FMT, bool PULL>
-__global__ void __launch_bounds__(kRowThreads) k_phi_rows(Launch L) {
+__global__ void __launch_bounds__(kRowThreads) k_phi_rows(Launch L, int W) {
     extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ const char *tsrc[2 * 19];
-    __shared__ unsigned tdst[2 * 19], tbytes[2 * 19];
+    __shared__ RowDesc rows[19];
     __shared__ unsigned wall_s;
-    const int nx = L.G.nx;
-    const int r = blockIdx.x;
-    const int y = r % L.G.ny, z = r / L.G.ny;
-    using S = typename Fmt<FMT>::S;
-    const unsigned goff = (unsigned)((size_t)Q * nx * sizeof(S));  // start of the g rows in the full layout
-    if (threadIdx.x == 0) {
-        wall_s = pop_table<Q, FMT>(L, L.src, 1, y, z, PULL, tsrc, tdst, tbytes, 0);
-        for (int i = 0; i < Q; ++i) tdst[i] -= goff;  // only the g rows are staged here
+    const Unit u = unit_of(L.G, W);
+    if (threadIdx.x == 0) wall_s = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) {
+        bool w;
+        rows[k] = pop_row<Q, FMT>(L, L.src, 1, k, u.y, u.z, PULL, W, 0u, &w);
+        if (w) atomicOr(&wall_s, 1u << k);
     }
     __syncthreads();
-    stage_rows(tsrc, tdst, tbytes, Q, sm);
+    stage_chunk(rows, Q, sm, u.x0, W, L.G.nx);
     cp_async_wait_all();
     __syncthreads();
     const unsigned wall = wall_s;
     const float *php = static_cast<const float *>(L.phi_prev);
-    float *phi = static_cast<float *>(L.phi);
-    const size_t row = (size_t)r * nx;
-    for (int p = threadIdx.x; p < nx / 2; p += blockDim.x) {
+    float *phi = static_cast<float *>(L.phi) + u.row + u.x0;
+    for (int p = threadIdx.x; p < W / 2; p += blockDim.x) {
         float out[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int x = 2 * p + k;
+            const int xl = 2 * p + k;
             float s = 0.f;
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 float gi;
                 if (PULL && (wall >> i) & 1u) {
                     const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
-                    gi = row_g<Q, FMT>(sm, nx, i, x) + float(2.0 * Lat<Q>::w(i) * 3.0) * php[row + x] *
-                                                           float(Lat<Q>::cx(i)) * uw;
+                    gi = row_g<Q, FMT>(sm, W, i, xl) +
+                         float(2.0 * Lat<Q>::w(i) * 3.0) * php[u.row + u.x0 + xl] * float(Lat<Q>::cx(i)) * uw;
                 } else {
-                    const int xs = PULL ? wrapi(x - Lat<Q>::cx(i), nx) : x;
-                    gi = row_g<Q, FMT>(sm, nx, i, xs);
+                    gi = row_g<Q, FMT>(sm, W, i, PULL ? xl - Lat<Q>::cx(i) : xl);
                 }
                 s += gi;
             }
             out[k] = s;
         }
-        reinterpret_cast<float2 *>(phi + row)[p] = make_float2(out[0], out[1]);
+        reinterpret_cast<float2 *>(phi)[p] = make_float2(out[0], out[1]);
     }
 }
 
 // ------------------------------------------------------------ mu pass
 
 template <int Q>
-__global__ void __launch_bounds__(kRowThreads) k_mu_rows(Launch L) {
+__global__ void __launch_bounds__(kRowThreads) k_mu_rows(Launch L, int W) {
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int NS = n_stencil_rows<Q>();
-    __shared__ const char *tsrc[NS];
-    __shared__ unsigned tdst[NS], tbytes[NS];
-    const int nx = L.G.nx;
-    const int r = blockIdx.x;
-    const int y = r % L.G.ny, z = r / L.G.ny;
-    const float *phi = static_cast<const float *>(L.phi);
-    if (threadIdx.x < NS) {
-        const int k = threadIdx.x;
-        const int cy = (Lat<Q>::D == 2 ? k : k % 3) - 1, cz = Lat<Q>::D == 2 ? 0 : k / 3 - 1;
-        int yn = y + cy;
-        yn = (L.G.device == FRE_SHEAR) ? (yn < 0 ? 0 : (yn >= L.G.ny ? L.G.ny - 1 : yn)) : wrapi(yn, L.G.ny);
-        const int zn = wrapi(z + cz, L.G.nz);
-        tsrc[k] = reinterpret_cast<const char *>(phi + ((size_t)zn * L.G.ny + yn) * nx);
-        tdst[k] = (unsigned)((size_t)k * nx * 4);
-        tbytes[k] = (unsigned)(nx * 4);
-    }
+    __shared__ RowDesc rows[NS];
+    const Unit u = unit_of(L.G, W);
+    if (threadIdx.x < NS)
+        rows[threadIdx.x] = field_row<Q>(L, static_cast<const float *>(L.phi), u.y, u.z, threadIdx.x, W, 0u);
     __syncthreads();
-    stage_rows(tsrc, tdst, tbytes, NS, sm);
+    stage_chunk(rows, NS, sm, u.x0, W, L.G.nx);
     cp_async_wait_all();
     __syncthreads();
-    const float *ph = reinterpret_cast<const float *>(sm);
-    float *mu = static_cast<float *>(L.mu) + (size_t)r * nx;
+    float *mu = static_cast<float *>(L.mu) + u.row + u.x0;
     const float A = float(L.P.A), kap = float(L.P.kappa);
     constexpr int c0 = stencil_slot<Q>(0, 0);
-    for (int p = threadIdx.x; p < nx / 2; p += blockDim.x) {
+    for (int p = threadIdx.x; p < W / 2; p += blockDim.x) {
         float out[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int x = 2 * p + k;
-            const float p0 = ph[c0 * nx + x];
+            const int xl = 2 * p + k;
+            const float p0 = row_field(sm, W, c0, xl);
             float lap = 0.f;
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int slot = stencil_slot<Q>(Lat<Q>::cy(i), Lat<Q>::cz(i));
-                lap += float(Lat<Q>::w(i)) * (ph[slot * nx + wrapi(x + Lat<Q>::cx(i), nx)] - p0);
+                lap += float(Lat<Q>::w(i)) * (row_field(sm, W, slot, xl + Lat<Q>::cx(i)) - p0);
             }
             lap *= 6.f;
             out[k] = A * (p0 * p0 * p0 - p0) - kap * lap;
@@ -270,58 +318,52 @@ __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16 *p, float a,
 }
 
 template <int Q, int FMT, bool PULL>
-__global__ void __launch_bounds__(kRowThreads) k_update_rows(Launch L) {
+__global__ void __launch_bounds__(kRowThreads) k_update_rows(Launch L, int W) {
     using S = typename Fmt<FMT>::S;
+    using CL = ChunkLayout<Q, FMT>;
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int NS = n_stencil_rows<Q>();
     constexpr int NR = 2 * Q + 2 * NS;
-    __shared__ const char *tsrc[NR];
-    __shared__ unsigned tdst[NR], tbytes[NR];
+    __shared__ RowDesc rows[NR];
     __shared__ unsigned wall_s;
-    const int nx = L.G.nx;
-    const int r = blockIdx.x;
-    const int y = r % L.G.ny, z = r / L.G.ny;
-    const size_t foff = RowLayout<Q, FMT>::field_off(nx);
-    if (threadIdx.x == 0) {
-        unsigned w = pop_table<Q, FMT>(L, L.src, 0, y, z, PULL, tsrc, tdst, tbytes, 0);
-        pop_table<Q, FMT>(L, L.src, 1, y, z, PULL, tsrc, tdst, tbytes, Q);
-        wall_s = w;
-    }
-    if (threadIdx.x < 2 * NS) {
-        const int k = threadIdx.x % NS, fld = threadIdx.x / NS;  // fld 0: phi, 1: mu
-        const int cy = (Lat<Q>::D == 2 ? k : k % 3) - 1, cz = Lat<Q>::D == 2 ? 0 : k / 3 - 1;
-        int yn = y + cy;
-        yn = (L.G.device == FRE_SHEAR) ? (yn < 0 ? 0 : (yn >= L.G.ny ? L.G.ny - 1 : yn)) : wrapi(yn, L.G.ny);
-        const int zn = wrapi(z + cz, L.G.nz);
-        const float *base = static_cast<const float *>(fld ? L.mu : L.phi);
-        const int slot = 2 * Q + fld * NS + k;
-        tsrc[slot] = reinterpret_cast<const char *>(base + ((size_t)zn * L.G.ny + yn) * nx);
-        tdst[slot] = (unsigned)(foff + (size_t)(fld * NS + k) * nx * 4);
-        tbytes[slot] = (unsigned)(nx * 4);
+    const Unit u = unit_of(L.G, W);
+    const unsigned foff = CL::field_off(W);
+    if (threadIdx.x == 0) wall_s = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < NR; k += blockDim.x) {
+        if (k < 2 * Q) {
+            const int lat = k >= Q, i = k - lat * Q;
+            bool w;
+            rows[k] = pop_row<Q, FMT>(L, L.src, lat, i, u.y, u.z, PULL, W, lat ? CL::g_off(W) : 0u, &w);
+            if (w && !lat) atomicOr(&wall_s, 1u << i);
+        } else {
+            const int j = k - 2 * Q, fld = j / NS, m = j - fld * NS;  // fld 0: phi, 1: mu
+            const float *base = static_cast<const float *>(fld ? L.mu : L.phi);
+            rows[k] = field_row<Q>(L, base, u.y, u.z, m, W, foff + fld * NS * CL::rw_f(W));
+        }
     }
     __syncthreads();
-    stage_rows(tsrc, tdst, tbytes, NR, sm);
+    stage_chunk(rows, NR, sm, u.x0, W, L.G.nx);
     cp_async_wait_all();
     __syncthreads();
 
     const unsigned wall = wall_s;
-    const unsigned char *gb = sm + (size_t)Q * nx * sizeof(S);
-    const float *phs = reinterpret_cast<const float *>(sm + foff);
-    const float *mus = phs + (size_t)NS * nx;
+    const unsigned char *gb = sm + CL::g_off(W);
+    const unsigned char *phs = sm + foff;
+    const unsigned char *mus = sm + foff + NS * CL::rw_f(W);
     const float *php = static_cast<const float *>(L.phi_prev);
     const float rho0 = float(L.P.rho0);
     const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
     const float kf = float(1.0 - 0.5 / L.P.tau_f);
     const float g3 = float(3.0 * L.P.Gamma);
-    const size_t row = (size_t)r * nx;
     const long long np = L.G.np;
     constexpr int c0 = stencil_slot<Q>(0, 0);
 
-    for (int p = threadIdx.x; p < nx / 2; p += blockDim.x) {
+    for (int p = threadIdx.x; p < W / 2; p += blockDim.x) {
         float fs[2][Q], gs[2][Q];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
-            const int x = 2 * p + k;
+            const int xl = 2 * p + k;
             float f[Q], g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -330,21 +372,14 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(Launch L) {
                     const float cu = float(Lat<Q>::cx(i)) * uw;
                     const float w2 = float(2.0 * Lat<Q>::w(i) * 3.0);
                     // slot i holds the local row of population opp(i)
-                    const int o = Lat<Q>::opp(i);
-                    float fo, go;
-                    if constexpr (Fmt<FMT>::DEV) {
-                        fo = to_float(reinterpret_cast<const S *>(sm)[(size_t)i * nx + x]) +
-                             float(Lat<Q>::w(o)) * rho0;
-                    } else {
-                        fo = reinterpret_cast<const S *>(sm)[(size_t)i * nx + x];
-                    }
-                    go = row_g<Q, FMT>(gb, nx, i, x);
+                    const float fo = row_f_slot<Q, FMT>(sm, W, i, xl, float(Lat<Q>::w(Lat<Q>::opp(i))) * rho0);
+                    const float go = row_g<Q, FMT>(gb, W, i, xl);
                     f[i] = fo + w2 * rho0 * cu;
-                    g[i] = go + w2 * php[row + x] * cu;
+                    g[i] = go + w2 * php[u.row + u.x0 + xl] * cu;
                 } else {
-                    const int xs = PULL ? wrapi(x - Lat<Q>::cx(i), nx) : x;
-                    f[i] = row_f<Q, FMT>(sm, nx, i, xs, rho0);
-                    g[i] = row_g<Q, FMT>(gb, nx, i, xs);
+                    const int xs = PULL ? xl - Lat<Q>::cx(i) : xl;
+                    f[i] = row_f<Q, FMT>(sm, W, i, xs, rho0);
+                    g[i] = row_g<Q, FMT>(gb, W, i, xs);
                 }
             }
             float rho = 0.f, ph = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -360,15 +395,15 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(Launch L) {
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int slot = stencil_slot<Q>(Lat<Q>::cy(i), Lat<Q>::cz(i));
-                const int xn = wrapi(x + Lat<Q>::cx(i), nx);
-                const float pv = phs[slot * nx + xn];
-                const float pm = pv * mus[slot * nx + xn];
+                const int xn = xl + Lat<Q>::cx(i);
+                const float pv = row_field(phs, W, slot, xn);
+                const float pm = pv * row_field(mus, W, slot, xn);
                 const float w = float(Lat<Q>::w(i));
                 if (Lat<Q>::cx(i)) { gpx += w * float(Lat<Q>::cx(i)) * pv; gqx += w * float(Lat<Q>::cx(i)) * pm; }
                 if (Lat<Q>::cy(i)) { gpy += w * float(Lat<Q>::cy(i)) * pv; gqy += w * float(Lat<Q>::cy(i)) * pm; }
                 if (Lat<Q>::cz(i)) { gpz += w * float(Lat<Q>::cz(i)) * pv; gqz += w * float(Lat<Q>::cz(i)) * pm; }
             }
-            const float mu = mus[c0 * nx + x];
+            const float mu = row_field(mus, W, c0, xl);
             const float Fx = 3.f * (mu * gpx - gqx), Fy = 3.f * (mu * gpy - gqy), Fz = 3.f * (mu * gpz - gqz);
             const float inv = 1.f / rho;
             const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
@@ -397,7 +432,7 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(Launch L) {
             gs[k][0] = ph - gsum;
         }
         // 2-wide stores of the node pair
-        const size_t off = row + 2 * p;
+        const size_t off = u.row + u.x0 + 2 * p;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S *fp = static_cast<S *>(L.dst.f) + (size_t)i * np + off;
@@ -419,18 +454,36 @@ __global__ void __launch_bounds__(kRowThreads) k_update_rows(Launch L) {
 
 // -------------------------------------------------------------- launch
 
+// Chunk width: 128 x per work unit when nx allows it (small shared-memory
+// footprint, several blocks per SM to overlap staging with compute), else
+// the whole row.  `pref` (a power of two, 0 = automatic) overrides.
+inline int chunk_width(const Geo &G, int elem_bytes, int pref) {
+    auto ok = [&](int W) { return W >= 2 && G.nx % W == 0 && (W * elem_bytes) % 16 == 0 && W % 2 == 0; };
+    if (pref > 0 && ok(pref)) return pref;
+    if (ok(128)) return 128;
+    return G.nx;
+}
+
 template <int Q, int FMT>
 struct RowLaunchers {
     using S = typename Fmt<FMT>::S;
-    static size_t smem_phi(int nx) { return RowLayout<Q, FMT>::pop_bytes(nx) - (size_t)Q * nx * sizeof(S); }
-    static size_t smem_mu(int nx) { return (size_t)n_stencil_rows<Q>() * nx * 4; }
-    static size_t smem_update(int nx) { return RowLayout<Q, FMT>::total_bytes(nx, 2 * n_stencil_rows<Q>()); }
+    using CL = ChunkLayout<Q, FMT>;
+    static constexpr int kMaxSmem = 200 * 1024;
+    static size_t smem_phi(int W) { return CL::g_bytes(W); }
+    static size_t smem_mu(int W) { return (size_t)n_stencil_rows<Q>() * CL::rw_f(W); }
+    static size_t smem_update(int W) { return CL::total(W, 2 * n_stencil_rows<Q>()); }
+    static int threads(int W) {
+        int t = W / 2;
+        t = (t + 31) / 32 * 32;
+        return t < kRowThreads ? t : kRowThreads;
+    }
 
-    static bool usable(const Geo &G) {
+    static bool usable(const Geo &G, int W) {
         if (G.device == FRE_FOUR_ROLLER) return false;
-        if ((G.nx * sizeof(S)) % 16 != 0 || G.nx % 2 != 0) return false;
+        if (G.nx % 2 != 0 || (G.nx * sizeof(S)) % 16 != 0 || G.nx < 16 / (int)sizeof(S)) return false;
         if ((G.np * sizeof(S)) % 16 != 0) return false;
-        return smem_update(G.nx) <= 200 * 1024;
+        if (G.nx % W != 0 || (W * sizeof(S)) % 16 != 0) return false;
+        return smem_update(W) <= (size_t)kMaxSmem;
     }
     static bool configure() {
         // opt in to the large dynamic shared memory once per process
@@ -438,7 +491,7 @@ struct RowLaunchers {
         static bool ok = true;
         if (!done) {
             done = true;
-            const int mx = 200 * 1024;
+            const int mx = kMaxSmem;
             ok &= cudaFuncSetAttribute(k_phi_rows<Q, FMT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess;
             ok &= cudaFuncSetAttribute(k_phi_rows<Q, FMT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess;
             ok &= cudaFuncSetAttribute(k_mu_rows<Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx) == cudaSuccess;
@@ -447,25 +500,25 @@ struct RowLaunchers {
         }
         return ok;
     }
+    static unsigned blocks(const Launch &L) { return (unsigned)((size_t)L.G.ny * L.G.nz * (L.G.nx / L.W)); }
     static void phi(const Launch &L, bool pull) {
-        const unsigned rows = (unsigned)(L.G.ny * L.G.nz);
-        if (pull) k_phi_rows<Q, FMT, true><<<rows, kRowThreads, smem_phi(L.G.nx), L.stream>>>(L);
-        else k_phi_rows<Q, FMT, false><<<rows, kRowThreads, smem_phi(L.G.nx), L.stream>>>(L);
+        if (pull) k_phi_rows<Q, FMT, true><<<blocks(L), threads(L.W), smem_phi(L.W), L.stream>>>(L, L.W);
+        else k_phi_rows<Q, FMT, false><<<blocks(L), threads(L.W), smem_phi(L.W), L.stream>>>(L, L.W);
     }
-    static void mu(const Launch &L) {
-        const unsigned rows = (unsigned)(L.G.ny * L.G.nz);
-        k_mu_rows<Q><<<rows, kRowThreads, smem_mu(L.G.nx), L.stream>>>(L);
-    }
+    static void mu(const Launch &L) { k_mu_rows<Q><<<blocks(L), threads(L.W), smem_mu(L.W), L.stream>>>(L, L.W); }
     static void update(const Launch &L, bool pull) {
-        const unsigned rows = (unsigned)(L.G.ny * L.G.nz);
-        if (pull) k_update_rows<Q, FMT, true><<<rows, kRowThreads, smem_update(L.G.nx), L.stream>>>(L);
-        else k_update_rows<Q, FMT, false><<<rows, kRowThreads, smem_update(L.G.nx), L.stream>>>(L);
+        if (pull) k_update_rows<Q, FMT, true><<<blocks(L), threads(L.W), smem_update(L.W), L.stream>>>(L, L.W);
+        else k_update_rows<Q, FMT, false><<<blocks(L), threads(L.W), smem_update(L.W), L.stream>>>(L, L.W);
     }
 };
 
 template <int Q, int FMT>
 struct RowEntry {
-    static bool usable(const Geo &G) { return RowLaunchers<Q, FMT>::usable(G) && RowLaunchers<Q, FMT>::configure(); }
+    // chunk width for this geometry (0: the row kernels do not apply)
+    static int width(const Geo &G, int pref) {
+        const int W = chunk_width(G, (int)sizeof(typename Fmt<FMT>::S), pref);
+        return (RowLaunchers<Q, FMT>::usable(G, W) && RowLaunchers<Q, FMT>::configure()) ? W : 0;
+    }
 };
 
 // All kernels of one lattice and storage format.
@@ -474,13 +527,14 @@ const KernelSet *kernel_set() {
     using GL = Launchers<Q, FMT>;
     if constexpr (FMT == FRE_FP64) {
         static const KernelSet ks = {GL::phi, GL::ghost, GL::mu, GL::update, GL::obs, GL::macro, GL::pull_plane,
-                                     GL::load_plane, GL::set_phi, GL::init_eq, nullptr, nullptr, nullptr, nullptr};
+                                     GL::load_plane, GL::set_phi, GL::init_eq, nullptr, nullptr, nullptr, nullptr,
+                                     nullptr, nullptr, nullptr, nullptr};
         return &ks;
     } else {
         using RL = RowLaunchers<Q, FMT>;
         static const KernelSet ks = {GL::phi, GL::ghost, GL::mu, GL::update, GL::obs, GL::macro, GL::pull_plane,
-                                     GL::load_plane, GL::set_phi, GL::init_eq, RowEntry<Q, FMT>::usable, RL::phi,
-                                     RL::mu, RL::update};
+                                     GL::load_plane, GL::set_phi, GL::init_eq, RowEntry<Q, FMT>::width, RL::phi,
+                                     RL::mu, RL::update, nullptr, nullptr, nullptr, nullptr};
         return &ks;
     }
 }

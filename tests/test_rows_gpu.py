@@ -31,9 +31,10 @@ def errs(a, b):
 
 CASES = [
     # lattice, device, nx, ny, nz, kwargs
-    ("d3q19", "shear", 48, 20, 12, dict(u_wall=0.03, tau_f=2.0, tau_g=2.0, gamma_mob=0.5)),
-    ("d3q19", "periodic", 32, 12, 10, dict(tau_f=0.8, tau_g=1.2, gamma_mob=0.7)),
-    ("d2q9", "shear", 96, 40, 1, dict(u_wall=0.02)),
+    ("d3q19", "shear", 64, 20, 12, dict(u_wall=0.03, tau_f=2.0, tau_g=2.0, gamma_mob=0.5)),
+    ("d3q19", "periodic", 96, 12, 10, dict(tau_f=0.8, tau_g=1.2, gamma_mob=0.7)),
+    ("d2q9", "shear", 256, 40, 1, dict(u_wall=0.02)),
+    ("d2q9", "periodic", 384, 24, 1, dict(tau_f=0.7)),
 ]
 
 
@@ -65,11 +66,11 @@ def test_row_kernels_match_per_node_kernels(fre, case, precision):
 
 def test_row_kernels_random_populations_fp32(fre, orc):
     """Non-equilibrium seeded populations through the row path vs the oracle."""
-    shape = (6, 8, 24)
+    shape = (6, 8, 32)
     f, g = inputs.random_populations(19, shape, seed=11)
-    sim = make(fre, "d3q19", "periodic", 24, 8, 6, "fp32", tau_f=0.7, tau_g=1.1, A=0.03, kappa=0.05)
+    sim = make(fre, "d3q19", "periodic", 32, 8, 6, "fp32", tau_f=0.7, tau_g=1.1, A=0.03, kappa=0.05)
     assert sim.row_kernels
-    o = orc.Oracle(1, 2, 24, 8, 6, 0.7, 1.1, 0.03, 0.05, 1.0, 0.0, 1.0)
+    o = orc.Oracle(1, 2, 32, 8, 6, 0.7, 1.1, 0.03, 0.05, 1.0, 0.0, 1.0)
     sim.load_populations(f, g)
     o.load_populations(f, g)
     sim.step(60)
@@ -87,7 +88,7 @@ def test_row_kernels_random_populations_fp32(fre, orc):
 def test_16bit_storage_vs_fp64_oracle(fre, orc, precision, tol):
     """16-bit deviation storage (FP32 arithmetic) vs the FP64 oracle after 500
     steps of the D3Q19 shear droplet: relative L-inf of rho, u, phi."""
-    nx, ny, nz = 48, 24, 16
+    nx, ny, nz = 64, 24, 16
     kw = dict(u_wall=0.03, tau_f=2.0, tau_g=2.0, gamma_mob=0.5)
     sim = make(fre, "d3q19", "shear", nx, ny, nz, precision, **kw)
     assert sim.row_kernels
