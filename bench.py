@@ -37,7 +37,7 @@ DROPLET = (255.5, 127.5, 127.5, 48.0)
 # algorithmic bytes per node update: read + write of f and g once (q = 19)
 ALG_BYTES = {"fp32": 2 * 2 * 19 * 4, "fp16dev": 2 * (19 * 2 + 18 * 2 + 4),
              "bf16dev": 2 * (19 * 2 + 18 * 2 + 4), "fp64": 2 * 2 * 19 * 8}
-KERNEL_SRC = os.path.join(ROOT, "paper_2212_01617_gb300", "csrc", "fre_kernels.cuh")
+CSRC = os.path.join(ROOT, "paper_2212_01617_gb300", "csrc")
 
 
 def log(*a):
@@ -54,8 +54,13 @@ def measured_peak_gbs():
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the device sources (the ncu traffic figure is valid for it only)."""
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cuh", ".cu", ".h")):
+            with open(os.path.join(CSRC, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(precision: str):
@@ -178,9 +183,10 @@ def time_steps(fre, precision, steps, warmup, ws, local):
     ms = e0.elapsed_time(e1)
     ms_max = max_over_ranks(ws, ms)
     obs = sim.observables()
+    path = sim.kernel_path
     sim.close()
     return dict(ms=ms_max, ms_local=ms, ms_phi=ms_phi, ms_mu=ms_mu, ms_update=ms_upd, ms_seq=ms_tot,
-                launches=launches, clocks=clk, obs=obs, n=n)
+                launches=launches, clocks=clk, obs=obs, n=n, path=path)
 
 
 def time_e2e(fre, precision, steps, obs_every=100):
@@ -354,7 +360,7 @@ def main():
                 "update_frac_of_measured_hbm": ALG_BYTES[prec] * rr["n"] / t / 1e9 / peak,
                 "step_alg_frac_of_measured_hbm": ALG_BYTES[prec] * rr["n"] / (rr["ms"] / args.steps * 1e-3)
                 / 1e9 / peak,
-                "D_after_run": rr["obs"]["D"], "mass": rr["obs"]["mass"],
+                "D_after_run": rr["obs"]["D"], "mass": rr["obs"]["mass"], "kernel_path": rr["path"],
             }
         if "fp32" in runs and "fp16dev" in runs:
             variants["fp16dev_speedup_vs_fp32"] = variants["fp16dev"]["mlups"] / variants["fp32"]["mlups"]
@@ -366,7 +372,9 @@ def main():
             "data": "synthetic", "config": base_config(main_prec),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": f"k_update<19,{main_prec},pull> (fused pull + collide of f and g)",
+                         "kernel": (f"k_wsrow<19,{main_prec},update,pull> (fused pull + collide of f and g; "
+                                    "warp-specialised, bulk-copy staged x-rows)" if r["path"] == 2 else
+                                    f"update kernel, path {r['path']}"),
                          "algorithmic_bytes_per_launch": ALG_BYTES[main_prec] * n,
                          "peak_source": peak_src,
                          "step_achieved": step_achieved, "step_frac": step_achieved / peak},

@@ -183,6 +183,12 @@ long long fre_step_count(const fre_ctx *c);
  * 0 if on the per-node kernels. */
 int fre_uses_row_kernels(const fre_ctx *c);
 
+/* Kernels of the time step: 0 per-node kernels (any geometry and format),
+ * 1 warp-specialised kernels on x-chunks, 2 warp-specialised kernels on
+ * whole x-rows (shear/periodic devices, FP32 and 16-bit storage, nx a
+ * multiple of 64 up to 512); -1 for a NULL context. */
+int fre_kernel_path(const fre_ctx *c);
+
 /* Destroy a context and free its device memory; NULL-safe. */
 void fre_destroy(fre_ctx *c);
 

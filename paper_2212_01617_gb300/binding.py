@@ -31,6 +31,7 @@ DEVICES = {"shear": FRE_SHEAR, "four_roller": FRE_FOUR_ROLLER, "periodic": FRE_P
 EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_fields",
            "fre_load_populations", "fre_store_populations", "fre_step", "fre_step_timed",
            "fre_copy_fields", "fre_observables", "fre_step_count", "fre_uses_row_kernels",
+           "fre_kernel_path",
            "fre_destroy", "fre_last_error"]
 FRE_FLAG_GENERIC_KERNELS = 1
 
@@ -95,6 +96,8 @@ def load_library(path: str = LIB_PATH):
         L.fre_step_count.argtypes = [vp]
         L.fre_uses_row_kernels.restype = C.c_int
         L.fre_uses_row_kernels.argtypes = [vp]
+        L.fre_kernel_path.restype = C.c_int
+        L.fre_kernel_path.argtypes = [vp]
         L.fre_destroy.argtypes = [vp]
         L.fre_destroy.restype = None
         L.fre_last_error.restype = C.c_char_p
@@ -206,6 +209,10 @@ def fre_uses_row_kernels(h) -> bool:
     return bool(load_library().fre_uses_row_kernels(h))
 
 
+def fre_kernel_path(h) -> int:
+    return int(load_library().fre_kernel_path(h))
+
+
 def fre_destroy(h):
     if h:
         load_library().fre_destroy(h)
@@ -280,3 +287,7 @@ class Simulation:
     @property
     def row_kernels(self) -> bool:
         return fre_uses_row_kernels(self.h)
+
+    @property
+    def kernel_path(self) -> int:
+        return fre_kernel_path(self.h)

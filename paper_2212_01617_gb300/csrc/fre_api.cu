@@ -615,6 +615,8 @@ long long fre_step_count(const fre_ctx *c) { return c ? c->step : -1; }
 
 int fre_uses_row_kernels(const fre_ctx *c) { return c && c->rows ? 1 : 0; }
 
+int fre_kernel_path(const fre_ctx *c) { return !c ? -1 : (c->fullrow ? 2 : (c->rows ? 1 : 0)); }
+
 void fre_destroy(fre_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device_id);

@@ -407,23 +407,40 @@ namespace fre {
 //                   values come from global memory (re-read by the nine
 //                   neighbouring rows, they stay in L2)
 
+// Axial stencil slots (cy, cz) with cy == 0 or cz == 0: the only ones whose
+// directions carry an x shift.  D3Q19: (0,0) (1,0) (-1,0) (0,1) (0,-1);
+// D2Q9: (0,0) (1,0) (-1,0).
+template <int Q>
+__host__ __device__ constexpr int n_axial() { return Lat<Q>::D == 2 ? 3 : 5; }
+__host__ __device__ constexpr int axial_slot(int cy, int cz) {
+    return (cy == 0 && cz == 0) ? 0 : (cz == 0 ? (cy > 0 ? 1 : 2) : (cy == 0 ? (cz > 0 ? 3 : 4) : -1));
+}
+__host__ __device__ constexpr int axial_cy(int a) { return a == 1 ? 1 : (a == 2 ? -1 : 0); }
+__host__ __device__ constexpr int axial_cz(int a) { return a == 3 ? 1 : (a == 4 ? -1 : 0); }
+
 template <int Q, int FMT, int KIND>
 struct FullRowLayout {
     using S = typename Fmt<FMT>::S;
     static constexpr bool DEV = Fmt<FMT>::DEV;
     static constexpr int NS = n_stencil_rows<Q>();
+    static constexpr int NA = n_axial<Q>();
     __host__ __device__ static unsigned rowb(int nx) { return (unsigned)(nx * sizeof(S)); }
     // start of the g rows
     __host__ __device__ static unsigned g_off(int nx) { return KIND == WS_UPDATE ? Q * rowb(nx) : 0u; }
     __host__ __device__ static unsigned g_bytes(int nx) {
         return DEV ? (Q - 1) * rowb(nx) + (unsigned)nx * 4 : Q * rowb(nx);
     }
+    // update: axial phi rows then axial mu rows after the populations
+    __host__ __device__ static unsigned f_off(int nx) { return (g_off(nx) + g_bytes(nx) + 15u) / 16u * 16u; }
     __host__ __device__ static unsigned bytes(int nx) {
         if (KIND == WS_MU) return NS * (unsigned)nx * 4;
+        if (KIND == WS_UPDATE) return f_off(nx) + 2 * NA * (unsigned)nx * 4;
         return g_off(nx) + g_bytes(nx);
     }
     __host__ __device__ static unsigned stage(int nx) { return (bytes(nx) + 127u) / 128u * 128u; }
-    __host__ __device__ static int nrows() { return KIND == WS_UPDATE ? 2 * Q : (KIND == WS_PHI ? Q : NS); }
+    __host__ __device__ static int nrows() {
+        return KIND == WS_UPDATE ? 2 * Q + 2 * NA : (KIND == WS_PHI ? Q : NS);
+    }
 };
 
 __device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
@@ -484,6 +501,18 @@ __global__ void __launch_bounds__(544, 1) k_wsrow(Launch L, int nunits) {
             unsigned dst[2], nb[2];
             int cnt = 0;
             for (int r = lane; r < FL::nrows(); r += 32, ++cnt) {
+                if (KIND == WS_UPDATE && r >= 2 * Q) {
+                    const int j = r - 2 * Q, fld = j / FL::NA, a = j - fld * FL::NA;
+                    int yn = y + axial_cy(a);
+                    yn = (L.G.device == FRE_SHEAR) ? (yn < 0 ? 0 : (yn >= L.G.ny ? L.G.ny - 1 : yn))
+                                                   : wrapi(yn, L.G.ny);
+                    const int zn = wrapi(z + axial_cz(a), L.G.nz);
+                    const float *base = static_cast<const float *>(fld ? L.mu : L.phi);
+                    src[cnt] = reinterpret_cast<const char *>(base + ((size_t)zn * L.G.ny + yn) * nx);
+                    dst[cnt] = FL::f_off(nx) + (unsigned)(j * nx * 4);
+                    nb[cnt] = (unsigned)(nx * 4);
+                    continue;
+                }
                 if (KIND == WS_MU) {
                     const int cy = (Lat<Q>::D == 2 ? r : r % 3) - 1, cz = Lat<Q>::D == 2 ? 0 : r / 3 - 1;
                     int yn = y + cy;
@@ -640,18 +669,29 @@ __global__ void __launch_bounds__(544, 1) k_wsrow(Launch L, int nunits) {
                     if (Lat<Q>::cy(i)) jy += float(Lat<Q>::cy(i)) * f[i];
                     if (Lat<Q>::cz(i)) jz += float(Lat<Q>::cz(i)) * f[i];
                 }
+                const float *phs = reinterpret_cast<const float *>(cur + FL::f_off(nx));
+                const float *mus = phs + FL::NA * nx;
                 float gpx = 0.f, gpy = 0.f, gpz = 0.f, gqx = 0.f, gqy = 0.f, gqz = 0.f;
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
-                    const int kn = site_nb<Q>(st, i);
-                    const float pv = __ldg(phif + kn);
-                    const float pm = pv * __ldg(muf + kn);
+                    const int a = axial_slot(Lat<Q>::cy(i), Lat<Q>::cz(i));
+                    float pv, mv;
+                    if (a >= 0) {
+                        const int xn = wrap_x(x + Lat<Q>::cx(i), nx);
+                        pv = phs[a * nx + xn];
+                        mv = mus[a * nx + xn];
+                    } else {
+                        const int kn = site_nb<Q>(st, i);
+                        pv = __ldg(phif + kn);
+                        mv = __ldg(muf + kn);
+                    }
+                    const float pm = pv * mv;
                     const float w = float(Lat<Q>::w(i));
                     if (Lat<Q>::cx(i)) { gpx += w * float(Lat<Q>::cx(i)) * pv; gqx += w * float(Lat<Q>::cx(i)) * pm; }
                     if (Lat<Q>::cy(i)) { gpy += w * float(Lat<Q>::cy(i)) * pv; gqy += w * float(Lat<Q>::cy(i)) * pm; }
                     if (Lat<Q>::cz(i)) { gpz += w * float(Lat<Q>::cz(i)) * pv; gqz += w * float(Lat<Q>::cz(i)) * pm; }
                 }
-                const float mu = __ldg(muf + st.n);
+                const float mu = mus[x];
                 const float Fx = 3.f * (mu * gpx - gqx), Fy = 3.f * (mu * gpy - gqy), Fz = 3.f * (mu * gpz - gqz);
                 const float inv = 1.f / rho;
                 const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
@@ -714,10 +754,14 @@ template <int Q, int FMT>
 struct WsRowLaunchers {
     using S = typename Fmt<FMT>::S;
     static constexpr int kMaxSmem = 200 * 1024;
+    // stages per block: the update takes as many as fit (one block per SM);
+    // the lighter phi and mu passes take two, so that two blocks (two
+    // producer warps issuing bulk copies) share an SM
     template <int KIND>
     static int nst(int nx) {
         const unsigned sb = FullRowLayout<Q, FMT, KIND>::stage(nx);
         const int n = (int)(kMaxSmem / sb);
+        if (KIND != WS_UPDATE) return n >= 2 ? 2 : n;
         return n >= 4 ? 4 : (n >= 3 ? 3 : (n >= 2 ? 2 : n));
     }
     static bool usable(const Geo &G) {
