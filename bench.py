@@ -294,6 +294,23 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def profile_case(spec: str, precisions, steps: int = 3):
+    """Small case of the benchmark kernels for ncu captures: a D3Q19 shear
+    lattice of the given size (e.g. 512x64x32), droplet, `steps` steps."""
+    import torch
+    import paper_2212_01617_gb300 as fre
+    nx, ny, nz = (int(v) for v in spec.split("x"))
+    w = dict(WORKLOAD, nx=nx, ny=ny, nz=nz)
+    for prec in precisions:
+        sim = fre.Simulation(precision=prec, **w)
+        sim.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, min(ny, nz) * 0.375)
+        sim.step(steps)
+        torch.cuda.synchronize()
+        print(f"profile case {spec} {prec}: path {sim.kernel_path}, D = {sim.observables()['D']:.6f}", flush=True)
+        sim.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,7 +322,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    help="NXxNYxNZ: run a few steps of a small case (ncu captures) and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case, [p for p in args.precisions.split(",") if p])
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
