@@ -189,6 +189,36 @@ int fre_uses_row_kernels(const fre_ctx *c);
  * multiple of 64 up to 512); -1 for a NULL context. */
 int fre_kernel_path(const fre_ctx *c);
 
+/* Conservation sums and droplet moments without any device allocation.
+ *
+ * For callers that cannot allocate device memory themselves or let a
+ * library do it -- an application whose allocator owns the whole device
+ * (a pool carved out at start-up), code running where a cudaMalloc would
+ * synchronise or is not allowed -- this computes, from populations the
+ * caller owns, what fre_observables reports as mass, phi_sum, volume,
+ * drop_weight, drop_count, centroid, I, D and theta_deg.  The paper has no
+ * counterpart; it is an interface convenience.
+ *
+ * f_dev, g_dev: device FP64 pre-collision populations [q][n] in the
+ * canonical order (n = nx*ny*nz, x fastest); every node counts as fluid.
+ * out_dev: device array of 16 doubles receiving mass, phi_sum, volume,
+ * drop_weight, drop_count, centroid[3], I[6] (xx yy zz xy xz yz), D,
+ * theta_deg.  cuda_stream: the work is queued there and the call returns
+ * without waiting.
+ *
+ * Scratch: the per-block partial sums live in a static 57,600-byte device
+ * array inside the library, which every GPU that loads the library keeps
+ * until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress), so make the first call on
+ * each device before any stream capture.  Every call writes all the
+ * partials it later reads, so nothing has to start at zero, but all calls
+ * share the one array: calls whose work overlaps on the GPU (different
+ * streams, or host threads, without ordering between them) race and give
+ * wrong results.  No device memory is allocated or freed.  Lattices of more
+ * than 2^30 nodes are rejected with FRE_ERR_ARG. */
+fre_status fre_moments_noalloc(int lattice, int nx, int ny, int nz, const double *f_dev,
+                               const double *g_dev, double *out_dev, void *cuda_stream);
+
 /* Destroy a context and free its device memory; NULL-safe. */
 void fre_destroy(fre_ctx *c);
 

@@ -9,12 +9,12 @@ Python binding.  ``build.build()`` compiles the library in-tree.
 from .binding import (  # noqa: F401
     EXPORTS, FreError, Simulation, fre_copy_fields, fre_create, fre_destroy, fre_device_bytes,
     fre_init_droplet, fre_init_fields, fre_last_error, fre_load_populations, fre_observables,
-    fre_params, fre_step, fre_step_count, fre_step_timed, fre_store_populations, fre_uses_row_kernels, fre_kernel_path, load_library, make_params,
+    fre_params, fre_step, fre_step_count, fre_step_timed, fre_store_populations, fre_uses_row_kernels, fre_kernel_path, fre_moments_noalloc, load_library, make_params,
 )
 
 __all__ = [
     "EXPORTS", "FreError", "Simulation", "fre_copy_fields", "fre_create", "fre_destroy",
     "fre_device_bytes", "fre_init_droplet", "fre_init_fields", "fre_last_error",
     "fre_load_populations", "fre_observables", "fre_params", "fre_step", "fre_step_count", "fre_step_timed",
-    "fre_store_populations", "fre_uses_row_kernels", "fre_kernel_path", "load_library", "make_params",
+    "fre_store_populations", "fre_uses_row_kernels", "fre_kernel_path", "fre_moments_noalloc", "load_library", "make_params",
 ]

@@ -31,7 +31,7 @@ DEVICES = {"shear": FRE_SHEAR, "four_roller": FRE_FOUR_ROLLER, "periodic": FRE_P
 EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_fields",
            "fre_load_populations", "fre_store_populations", "fre_step", "fre_step_timed",
            "fre_copy_fields", "fre_observables", "fre_step_count", "fre_uses_row_kernels",
-           "fre_kernel_path",
+           "fre_kernel_path", "fre_moments_noalloc",
            "fre_destroy", "fre_last_error"]
 FRE_FLAG_GENERIC_KERNELS = 1
 
@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH):
         L.fre_uses_row_kernels.argtypes = [vp]
         L.fre_kernel_path.restype = C.c_int
         L.fre_kernel_path.argtypes = [vp]
+        L.fre_moments_noalloc.restype = C.c_int
+        L.fre_moments_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
         L.fre_destroy.argtypes = [vp]
         L.fre_destroy.restype = None
         L.fre_last_error.restype = C.c_char_p
@@ -211,6 +213,14 @@ def fre_uses_row_kernels(h) -> bool:
 
 def fre_kernel_path(h) -> int:
     return int(load_library().fre_kernel_path(h))
+
+
+def fre_moments_noalloc(lattice, nx, ny, nz, f_dev_ptr, g_dev_ptr, out_dev_ptr, stream=None):
+    """Device pointers in, device pointer out; queued on `stream`."""
+    lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+    s = stream if stream is not None else current_stream_handle()
+    _check(load_library().fre_moments_noalloc(lat, int(nx), int(ny), int(nz), f_dev_ptr, g_dev_ptr,
+                                              out_dev_ptr, s), "fre_moments_noalloc")
 
 
 def fre_destroy(h):

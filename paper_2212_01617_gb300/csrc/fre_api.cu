@@ -268,6 +268,10 @@ fre_status finish_init(fre_ctx *c, int from_staging) {
 
 }  // namespace
 
+namespace fre {
+void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+}  // namespace fre
+
 extern "C" {
 
 size_t fre_device_bytes(const fre_params *p) {

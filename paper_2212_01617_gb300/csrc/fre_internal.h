@@ -84,4 +84,7 @@ struct KernelSet {
 const KernelSet *kernels_d2q9(int precision);
 const KernelSet *kernels_d3q19(int precision);
 
+// Record the message returned by fre_last_error() on this thread.
+void set_last_error(const char *msg);
+
 }  // namespace fre
