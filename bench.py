@@ -315,6 +315,101 @@ def profile_case(spec: str, precisions, steps: int = 3):
     return 0
 
 
+# D2Q9 batch of uneven cases: interface A = kappa = 0.01 (xi = 1), sigma =
+# sqrt(8 kappa A / 9); tau_f = 2 (dynamic viscosity rho0 cs^2 (tau_f - 1/2) = 0.5)
+BATCH_PHYS = dict(tau_f=2.0, tau_g=1.0, A=0.01, kappa=0.01, gamma_mob=1.0, rho0=1.0)
+
+
+def batch_case_params(c):
+    """Lattice, droplet and wall speed of one drawn batch case.  Shear: H = Ny
+    = Nx/2, rate G = 2 u_w / H, R = (R/H) H.  Four-roller: Ny = Nx, H = Nx/2,
+    rate G = u_w / (Nx/4), R = (R/H) H.  Ca = mu G R / sigma gives
+    u_w = Ca sigma / (2 mu (R/H)) for both."""
+    nx = c["nx"]
+    ny = nx // 2 if c["device"] == "shear" else nx
+    H = ny if c["device"] == "shear" else nx / 2
+    sigma = (8.0 * BATCH_PHYS["kappa"] * BATCH_PHYS["A"] / 9.0) ** 0.5
+    mu_visc = BATCH_PHYS["rho0"] * (BATCH_PHYS["tau_f"] - 0.5) / 3.0
+    u_w = c["ca"] * sigma / (2.0 * mu_visc * c["r_over_h"])
+    params = dict(BATCH_PHYS, lattice="d2q9", device=c["device"], nx=nx, ny=ny, nz=1, u_wall=u_w)
+    drop = ((nx - 1) / 2, (ny - 1) / 2, 0.0, c["r_over_h"] * H)
+    return params, drop
+
+
+def run_batch_workload(args):
+    """64 uneven D2Q9 cases (half shear, half four-roller), FP32: one batch
+    (autotuned batched or per-slot launches, CUDA-graph replays) against one
+    context per case stepped on its own (one launch per kernel per case)."""
+    import torch
+    import paper_2212_01617_gb300 as fre
+    from paper_2212_01617_gb300 import inputs
+    cases = [batch_case_params(c) for c in inputs.batch_cases(64)]
+    nodes = sum(p["nx"] * p["ny"] for p, _ in cases)
+    # one stream for the batch and for every per-case context: the events
+    # bracket all the work and the per-case launches run one after another
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        return _batch_workload(args, fre, cases, nodes, stream)
+
+
+def _batch_workload(args, fre, cases, nodes, stream):
+    import torch
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    b = fre.Batch("d2q9", "fp32")
+    for p, d in cases:
+        b.add(*d, **p)
+    b.step(max(args.warmup, 40))  # includes the autotuner's timed candidates
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_batch = e0.elapsed_time(e1)
+    tuning = b.tuning()
+    b.close()
+
+    sims = []
+    for p, d in cases:
+        sim = fre.Simulation(precision="fp32", **{k: v for k, v in p.items() if k != "precision"})
+        sim.init_droplet(*d)
+        sims.append(sim)
+    for sim in sims:
+        sim.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for sim in sims:
+        sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for sim in sims:
+        sim.close()
+    mode = {0: "batched", 1: "per-slot"}[tuning["mode"]]
+    line = {"metric": "batched D2Q9 FRE-LBM MLUPS, 64 uneven cases", "value": nodes * args.steps / ms_batch / 1e3,
+            "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 40),
+            "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64 D2Q9 cases, Nx uniform in 64..512 (even), shear Ny=Nx/2, four-roller "
+                                   "Ny=Nx, Ca U(0.05,0.5), R/H U(0.1,0.3), FP32", "nodes": nodes,
+                       "l2": "state of all cases (~0.4 GB) larger than L2; no flush"},
+            "sequential": {"value": nodes * args.steps / ms_seq / 1e3, "unit": "MLUPS",
+                           "ms_per_step": ms_seq / args.steps,
+                           "what": "one context per case, each stepped on its own kernels"},
+            "speedup_vs_sequential": ms_seq / ms_batch,
+            "tuning": {"mode": mode, "bx": tuning["bx"],
+                       "ms_per_step_candidates": dict(zip(["batched bx32", "batched bx64", "batched bx128",
+                                                           "per-slot"], tuning["ms_per_step"]))},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,7 +423,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     help="NXxNYxNZ: run a few steps of a small case (ncu captures) and exit")
+    ap.add_argument("--workload", choices=["lattice", "batch"], default="lattice",
+                    help="lattice: the 512x256x256 D3Q19 lattice (default); batch: 64 uneven D2Q9 cases")
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch_workload(args)
     if args.profile_case:
         return profile_case(args.profile_case, [p for p in args.precisions.split(",") if p])
     if args.warmup < 3:

@@ -219,6 +219,63 @@ int fre_kernel_path(const fre_ctx *c);
 fre_status fre_moments_noalloc(int lattice, int nx, int ny, int nz, const double *f_dev,
                                const double *g_dev, double *out_dev, void *cuda_stream);
 
+/* ---------------------------------------------------------------- batches
+ *
+ * A batch holds many independent simulations ("slots") of one lattice and
+ * storage format and advances all of them together, for many small or
+ * uneven cases (independent droplets, a request stream).  Slots are full
+ * contexts created with the batch's stream; a batch step runs either one
+ * launch per kernel covering every slot (per-node kernels with a
+ * block-to-slot table on the device) or each slot's own fastest kernels;
+ * an autotuner times both (and the block width of the first) on the live
+ * slot set, and steady steps replay a CUDA graph of two steps.  Every slot
+ * computes exactly the update of a context stepped alone; only rounding
+ * order may differ between kernel families. */
+typedef struct fre_batch fre_batch;
+
+/* Create an empty batch.  budget_bytes bounds the device memory of its
+ * slots (fre_device_bytes of each); cuda_stream as in fre_create. */
+fre_status fre_batch_create(int lattice, int precision, void *cuda_stream, size_t budget_bytes,
+                            fre_batch **out);
+
+/* Admit one case: create a context with *p (its lattice and precision must
+ * match the batch) and initialise a droplet as fre_init_droplet does.
+ * FRE_ERR_BUDGET (nothing allocated) when it would exceed the budget.
+ * *slot receives its slot index (freed slots are reused). */
+fre_status fre_batch_add(fre_batch *b, const fre_params *p, double cx, double cy, double cz, double R,
+                         int *slot);
+
+/* Finish a slot and free its device memory (synchronises the stream). */
+fre_status fre_batch_remove(fre_batch *b, int slot);
+
+/* Advance every slot nsteps steps; asynchronous except for the first call
+ * after the slot set changed, which may tune (with real steps). */
+fre_status fre_batch_step(fre_batch *b, int nsteps);
+
+/* Observables of one slot (as fre_observables; synchronises). */
+fre_status fre_batch_observables(fre_batch *b, int slot, fre_obs *out);
+
+/* The context of a slot (owned by the batch; do not destroy). */
+fre_ctx *fre_batch_context(fre_batch *b, int slot);
+
+/* Active slot indices into slots[0..max_slots); returns their number. */
+int fre_batch_slots(const fre_batch *b, int *slots, int max_slots);
+
+/* Device bytes held by the slots. */
+size_t fre_batch_bytes_in_use(const fre_batch *b);
+
+/* Autotuner result: mode (0 one launch per kernel for all slots, 1 each
+ * slot's own kernels), block width, and ms per step measured for the four
+ * candidates (batched width 32, 64, 128; per-slot).  FRE_ERR_STATE if the
+ * current slot set has not been tuned yet. */
+fre_status fre_batch_tuning(const fre_batch *b, int *mode, int *bx, double *ms_per_step);
+
+/* Wait for the batch's queued work. */
+fre_status fre_batch_synchronize(fre_batch *b);
+
+/* Destroy the batch and every slot; NULL-safe. */
+void fre_batch_destroy(fre_batch *b);
+
 /* Destroy a context and free its device memory; NULL-safe. */
 void fre_destroy(fre_ctx *c);
 

@@ -32,6 +32,9 @@ EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_field
            "fre_load_populations", "fre_store_populations", "fre_step", "fre_step_timed",
            "fre_copy_fields", "fre_observables", "fre_step_count", "fre_uses_row_kernels",
            "fre_kernel_path", "fre_moments_noalloc",
+           "fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
+           "fre_batch_observables", "fre_batch_context", "fre_batch_slots", "fre_batch_bytes_in_use",
+           "fre_batch_tuning", "fre_batch_synchronize", "fre_batch_destroy",
            "fre_destroy", "fre_last_error"]
 FRE_FLAG_GENERIC_KERNELS = 1
 
@@ -103,6 +106,25 @@ def load_library(path: str = LIB_PATH):
         L.fre_destroy.argtypes = [vp]
         L.fre_destroy.restype = None
         L.fre_last_error.restype = C.c_char_p
+        L.fre_batch_create.argtypes = [C.c_int, C.c_int, vp, C.c_size_t, C.POINTER(vp)]
+        L.fre_batch_add.argtypes = [vp, C.POINTER(fre_params), C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.POINTER(C.c_int)]
+        L.fre_batch_remove.argtypes = [vp, C.c_int]
+        L.fre_batch_step.argtypes = [vp, C.c_int]
+        L.fre_batch_observables.argtypes = [vp, C.c_int, C.POINTER(fre_obs)]
+        L.fre_batch_context.restype = vp
+        L.fre_batch_context.argtypes = [vp, C.c_int]
+        L.fre_batch_slots.restype = C.c_int
+        L.fre_batch_slots.argtypes = [vp, C.POINTER(C.c_int), C.c_int]
+        L.fre_batch_bytes_in_use.restype = C.c_size_t
+        L.fre_batch_bytes_in_use.argtypes = [vp]
+        L.fre_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.fre_batch_synchronize.argtypes = [vp]
+        L.fre_batch_destroy.argtypes = [vp]
+        L.fre_batch_destroy.restype = None
+        for name in ("fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
+                     "fre_batch_observables", "fre_batch_tuning", "fre_batch_synchronize"):
+            getattr(L, name).restype = C.c_int
         for name in ("fre_create", "fre_init_droplet", "fre_init_fields", "fre_load_populations",
                      "fre_store_populations", "fre_step", "fre_step_timed", "fre_copy_fields",
                      "fre_observables"):
@@ -301,3 +323,98 @@ class Simulation:
     @property
     def kernel_path(self) -> int:
         return fre_kernel_path(self.h)
+
+
+class Batch:
+    """Many independent simulations of one lattice and storage format advanced
+    together (C ABI fre_batch_*)."""
+
+    def __init__(self, lattice="d2q9", precision="fp32", budget_bytes=150 << 30, stream=None):
+        self.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = C.c_void_p()
+        st = stream if stream is not None else current_stream_handle()
+        _check(load_library().fre_batch_create(self.lattice, self.precision, C.c_void_p(st) if st else None,
+                                               int(budget_bytes), C.byref(h)), "fre_batch_create")
+        self.h = h.value
+        self._shape = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().fre_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def add(self, cx, cy, cz, R, **params) -> int:
+        params.setdefault("lattice", self.lattice)
+        params.setdefault("precision", self.precision)
+        p = make_params(**params)
+        slot = C.c_int(-1)
+        _check(load_library().fre_batch_add(self.h, C.byref(p), cx, cy, cz, R, C.byref(slot)), "fre_batch_add")
+        self._shape[slot.value] = (p.nz, p.ny, p.nx)
+        return slot.value
+
+    def remove(self, slot: int):
+        _check(load_library().fre_batch_remove(self.h, int(slot)), "fre_batch_remove")
+        self._shape.pop(int(slot), None)
+
+    def step(self, nsteps: int = 1):
+        _check(load_library().fre_batch_step(self.h, int(nsteps)), "fre_batch_step")
+
+    def observables(self, slot: int, allow_unstable: bool = True) -> dict:
+        o = fre_obs()
+        s = load_library().fre_batch_observables(self.h, int(slot), C.byref(o))
+        if not (s == FRE_OK or (allow_unstable and s == FRE_ERR_UNSTABLE)):
+            _check(s, "fre_batch_observables")
+        return o.as_dict()
+
+    def context(self, slot: int) -> int:
+        return load_library().fre_batch_context(self.h, int(slot))
+
+    def fields(self, slot: int) -> dict:
+        shape = self._shape[slot]
+        n = int(np.prod(shape))
+        out = {k: np.zeros(n) for k in ("rho", "ux", "uy", "uz", "phi", "mu")}
+        fre_copy_fields(self.context(slot), *[out[k] for k in ("rho", "ux", "uy", "uz", "phi", "mu")])
+        return {k: v.reshape(shape) for k, v in out.items()}
+
+    def populations(self, slot: int):
+        shape = self._shape[slot]
+        q = 9 if self.lattice == FRE_D2Q9 else 19
+        n = int(np.prod(shape))
+        f, g = np.zeros(q * n), np.zeros(q * n)
+        fre_store_populations(self.context(slot), f, g)
+        return f.reshape((q,) + shape), g.reshape((q,) + shape)
+
+    def steps_taken(self, slot: int) -> int:
+        return int(load_library().fre_step_count(self.context(slot)))
+
+    def slots(self):
+        L = load_library()
+        n = L.fre_batch_slots(self.h, None, 0)
+        arr = (C.c_int * max(n, 1))()
+        L.fre_batch_slots(self.h, arr, n)
+        return [arr[i] for i in range(n)]
+
+    def bytes_in_use(self) -> int:
+        return int(load_library().fre_batch_bytes_in_use(self.h))
+
+    def tuning(self):
+        mode, bx = C.c_int(0), C.c_int(0)
+        ms = np.zeros(4)
+        s = load_library().fre_batch_tuning(self.h, C.byref(mode), C.byref(bx), _dptr(ms))
+        return {"tuned": s == FRE_OK, "mode": mode.value, "bx": bx.value, "ms_per_step": ms.tolist()}
+
+    def synchronize(self):
+        _check(load_library().fre_batch_synchronize(self.h), "fre_batch_synchronize")

@@ -9,44 +9,12 @@
 #include <string>
 #include <vector>
 
-#include "fre_internal.h"
+#include "fre_ctx.h"
 
 namespace fre {
 // scratch layout of the observables reduction (see fre_kernels.cuh)
 constexpr int kRedDoublesHost = 1024 * 16 + 32;
 }  // namespace fre
-
-struct fre_ctx {
-    fre_params p;
-    int q = 0;
-    int device_id = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    const fre::KernelSet *ks = nullptr;
-    fre::Geo G{};
-    fre::Phys P{};
-    fre::Buf buf[2]{};
-    void *phi[2]{};
-    void *mu = nullptr;
-    unsigned char *solid = nullptr;
-    int *ghost = nullptr;
-    int n_ghost = 0;
-    double *red = nullptr;
-    int red_blocks = 0;
-    fre_obs *obs_dev = nullptr;
-    fre_obs *obs_host = nullptr;
-    int *err_dev = nullptr;  // set by a kernel whose bounded wait timed out
-    double *staging = nullptr;
-    std::vector<void *> allocs;
-    int cur = 0;        // buffer holding the state
-    int pp = 1;         // phi buffer holding phi of the previous step
-    bool local = true;  // state is pre-collision (no streaming pending)
-    bool initialised = false;
-    bool rows = false;  // the row kernels run the hot path
-    int row_w = 0;      // their chunk width
-    bool fullrow = false;  // the update runs on the full-row kernel
-    long long step = 0;
-};
 
 namespace {
 
@@ -187,7 +155,9 @@ void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<in
             }
 }
 
-fre::Launch launch_of(fre_ctx *c) {
+}  // namespace
+
+fre::Launch fre::ctx_launch(fre_ctx *c) {
     fre::Launch L{};
     L.G = c->G;
     L.P = c->P;
@@ -207,6 +177,36 @@ fre::Launch launch_of(fre_ctx *c) {
     L.err = c->err_dev;
     return L;
 }
+
+// Issue the kernels of one time step on the context stream and advance the
+// host-side state (buffer parity, step counter).
+void fre::ctx_launch_step(fre_ctx *c) {
+    fre::Launch L = ctx_launch(c);
+    const bool pull = !c->local;
+    if (c->fullrow) {
+        c->ks->phi_fullrow(L, pull);
+        c->ks->mu_fullrow(L);
+        c->ks->update_fullrow(L, pull);
+    } else if (c->rows) {
+        c->ks->phi_rows(L, pull);
+        c->ks->mu_rows(L);
+        c->ks->update_rows(L, pull);
+    } else {
+        c->ks->phi(L, pull);
+        if (c->n_ghost) c->ks->ghost(L, L.phi);
+        c->ks->mu(L);
+        if (c->n_ghost) c->ks->ghost(L, L.mu);
+        c->ks->update(L, pull);
+    }
+    c->cur ^= 1;
+    c->pp ^= 1;
+    c->local = false;
+    c->step++;
+}
+
+namespace {
+
+fre::Launch launch_of(fre_ctx *c) { return fre::ctx_launch(c); }
 
 // phi and mu of the current state into phi[1 - pp] and mu.
 void current_phi_mu(fre_ctx *c, const fre::Launch &L) {
@@ -487,29 +487,7 @@ fre_status fre_step(fre_ctx *c, int nsteps) {
     if (s != FRE_OK) return s;
     if (nsteps < 0) return fail(FRE_ERR_ARG, "fre_step: nsteps < 0");
     if (!c->initialised) return fail(FRE_ERR_STATE, "fre_step: not initialised");
-    for (int t = 0; t < nsteps; ++t) {
-        fre::Launch L = launch_of(c);
-        const bool pull = !c->local;
-        if (c->fullrow) {
-            c->ks->phi_fullrow(L, pull);
-            c->ks->mu_fullrow(L);
-            c->ks->update_fullrow(L, pull);
-        } else if (c->rows) {
-            c->ks->phi_rows(L, pull);
-            c->ks->mu_rows(L);
-            c->ks->update_rows(L, pull);
-        } else {
-            c->ks->phi(L, pull);
-            if (c->n_ghost) c->ks->ghost(L, L.phi);
-            c->ks->mu(L);
-            if (c->n_ghost) c->ks->ghost(L, L.mu);
-            c->ks->update(L, pull);
-        }
-        c->cur ^= 1;
-        c->pp ^= 1;
-        c->local = false;
-        c->step++;
-    }
+    for (int t = 0; t < nsteps; ++t) fre::ctx_launch_step(c);
     return check_launch("fre_step");
 }
 

@@ -1,0 +1,496 @@
+// Batch runtime of the C ABI (include/fre.h, fre_batch_*): many independent
+// simulations ("slots") of one lattice and storage format on one stream.
+//
+// A batch step advances every active slot.  Two execution modes:
+//   batched   -- one launch per kernel for all slots (per-node kernels,
+//                block -> slot table on the device; block width BX tuned);
+//   per-slot  -- each slot's own fastest kernels, back to back.
+// The autotuner times the candidates on the live slot set (the timed steps
+// are real steps) and keeps the fastest.  Steady-state steps replay a CUDA
+// graph of two consecutive steps (even and odd buffer parity), so the host
+// cost of a step does not grow with the number of slots.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "fre_ctx.h"
+
+struct fre_batch {
+    int lattice = 0, precision = 0;
+    int device_id = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t budget = 0, in_use = 0;
+    std::vector<fre_ctx *> slots;
+    std::vector<size_t> slot_bytes;
+    const fre::BatchKernels *bk = nullptr;
+    // device tables of the batched mode
+    fre::Launch *d_cases[2] = {nullptr, nullptr};
+    int *d_bstart = nullptr, *d_gstart = nullptr;
+    int cap = 0;
+    std::vector<int> order;  // active slots, table order
+    bool tables_valid = false;
+    int table_bx = 0;  // block width the block prefix was built for
+    int total_blocks = 0, total_ghost_blocks = 0;
+    // tuning and graph
+    int mode = 0;  // 0 batched, 1 per-slot
+    int bx = 64;
+    bool tuned = false;
+    double tuned_ms[4] = {0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128 and per-slot
+    cudaGraphExec_t graph = nullptr;
+    long long graph_replays = 0;
+};
+
+namespace {
+
+fre_status bfail(fre_status s, const char *fmt, const char *detail = "") {
+    char msg[512];
+    snprintf(msg, sizeof(msg), fmt, detail);
+    fre::set_last_error(msg);
+    return s;
+}
+
+#define BCUDA(call)                                                                     \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) return bfail(FRE_ERR_CUDA, #call ": %s", cudaGetErrorString(e_)); \
+    } while (0)
+
+void drop_graph(fre_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+void invalidate(fre_batch *b) {
+    b->tables_valid = false;
+    b->tuned = false;
+    drop_graph(b);
+}
+
+std::vector<int> active(const fre_batch *b) {
+    std::vector<int> a;
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (b->slots[i]) a.push_back(i);
+    return a;
+}
+
+// launch descriptor of a context after one more step (buffers swapped)
+fre::Launch next_launch(fre_ctx *c) {
+    c->cur ^= 1;
+    c->pp ^= 1;
+    fre::Launch L = fre::ctx_launch(c);
+    c->cur ^= 1;
+    c->pp ^= 1;
+    L.pull = 1;
+    return L;
+}
+
+fre_status build_tables(fre_batch *b) {
+    b->order = active(b);
+    const int n = (int)b->order.size();
+    if (n > b->cap) {
+        for (auto &p : b->d_cases) {
+            if (p) cudaFree(p);
+            p = nullptr;
+        }
+        if (b->d_bstart) cudaFree(b->d_bstart);
+        if (b->d_gstart) cudaFree(b->d_gstart);
+        b->d_bstart = b->d_gstart = nullptr;
+        const int cap = std::max(64, n * 2);
+        BCUDA(cudaMalloc(&b->d_cases[0], sizeof(fre::Launch) * cap));
+        BCUDA(cudaMalloc(&b->d_cases[1], sizeof(fre::Launch) * cap));
+        BCUDA(cudaMalloc(&b->d_bstart, sizeof(int) * (cap + 1)));
+        BCUDA(cudaMalloc(&b->d_gstart, sizeof(int) * (cap + 1)));
+        b->cap = cap;
+    }
+    std::vector<fre::Launch> A(n), B(n);
+    std::vector<int> gs(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        fre_ctx *c = b->slots[b->order[k]];
+        A[k] = fre::ctx_launch(c);
+        A[k].pull = c->local ? 0 : 1;
+        B[k] = next_launch(c);
+        gs[k + 1] = gs[k] + (c->n_ghost + 255) / 256;
+    }
+    b->total_ghost_blocks = gs[n];
+    b->table_bx = 0;  // the block prefix follows the slot order
+    BCUDA(cudaMemcpyAsync(b->d_cases[0], A.data(), sizeof(fre::Launch) * n, cudaMemcpyHostToDevice, b->stream));
+    BCUDA(cudaMemcpyAsync(b->d_cases[1], B.data(), sizeof(fre::Launch) * n, cudaMemcpyHostToDevice, b->stream));
+    BCUDA(cudaMemcpyAsync(b->d_gstart, gs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->stream));
+    BCUDA(cudaStreamSynchronize(b->stream));
+    b->tables_valid = true;
+    return FRE_OK;
+}
+
+// block prefix of the batched kernels for block width bx
+fre_status upload_blocks(fre_batch *b, int bx) {
+    const int n = (int)b->order.size();
+    const int by = 256 / bx;
+    std::vector<int> bs(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        const fre_ctx *c = b->slots[b->order[k]];
+        const long long nb = (long long)((c->p.nx + bx - 1) / bx) * ((c->p.ny + by - 1) / by) * c->p.nz;
+        if (bs[k] + nb > (1LL << 31) - 1) return bfail(FRE_ERR_ARG, "fre_batch: too many blocks%s");
+        bs[k + 1] = bs[k] + (int)nb;
+    }
+    b->total_blocks = bs[n];
+    BCUDA(cudaMemcpyAsync(b->d_bstart, bs.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->stream));
+    BCUDA(cudaStreamSynchronize(b->stream));
+    b->table_bx = bx;
+    return FRE_OK;
+}
+
+fre::BatchLaunch batch_launch(fre_batch *b, int which) {
+    fre::BatchLaunch B{};
+    B.cases = b->d_cases[which];
+    B.block_start = b->d_bstart;
+    B.ghost_start = b->d_gstart;
+    B.nslots = (int)b->order.size();
+    B.total_blocks = b->total_blocks;
+    B.total_ghost_blocks = b->total_ghost_blocks;
+    B.stream = b->stream;
+    return B;
+}
+
+// kernels of one step of every slot in batched mode, descriptors `which`
+void launch_batched(fre_batch *b, int which) {
+    const fre::BatchLaunch B = batch_launch(b, which);
+    b->bk->phi(B, b->bx);
+    if (B.total_ghost_blocks) b->bk->ghost(B, 0);
+    b->bk->mu(B, b->bx);
+    if (B.total_ghost_blocks) b->bk->ghost(B, 1);
+    b->bk->update(B, b->bx);
+}
+
+// advance the host state of every slot by one step (after batched kernels)
+void advance_state(fre_batch *b) {
+    for (int s : b->order) {
+        fre_ctx *c = b->slots[s];
+        c->cur ^= 1;
+        c->pp ^= 1;
+        c->local = false;
+        c->step++;
+    }
+}
+
+// one step outside any graph
+fre_status single_step(fre_batch *b) {
+    if (b->mode == 0) {
+        if (!b->tables_valid) {
+            fre_status s = build_tables(b);
+            if (s != FRE_OK) return s;
+            b->table_bx = 0;
+        }
+        if (b->table_bx != b->bx) {
+            fre_status s = upload_blocks(b, b->bx);
+            if (s != FRE_OK) return s;
+        }
+        launch_batched(b, 0);
+        const bool had_local = [&] {
+            for (int s : b->order)
+                if (b->slots[s]->local) return true;
+            return false;
+        }();
+        advance_state(b);
+        // descriptors A and B swap roles; a slot that streamed in place
+        // changes its pull flag, which needs a rebuild
+        if (had_local) {
+            b->tables_valid = false;
+        } else {
+            std::swap(b->d_cases[0], b->d_cases[1]);
+        }
+        drop_graph(b);
+    } else {
+        b->order = active(b);
+        for (int s : b->order) fre::ctx_launch_step(b->slots[s]);
+        b->tables_valid = false;  // buffer parities changed
+        drop_graph(b);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(FRE_ERR_CUDA, "fre_batch_step: %s", cudaGetErrorString(e));
+    return FRE_OK;
+}
+
+// capture the two-step graph of the current mode
+fre_status capture(fre_batch *b) {
+    drop_graph(b);
+    if (b->mode == 0) {
+        if (!b->tables_valid) {
+            fre_status s = build_tables(b);
+            if (s != FRE_OK) return s;
+            b->table_bx = 0;
+        }
+        if (b->table_bx != b->bx) {
+            fre_status s = upload_blocks(b, b->bx);
+            if (s != FRE_OK) return s;
+        }
+    } else {
+        b->order = active(b);
+    }
+    BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    if (b->mode == 0) {
+        launch_batched(b, 0);
+        launch_batched(b, 1);
+    } else {
+        for (int s : b->order) fre::ctx_launch_step(b->slots[s]);
+        for (int s : b->order) fre::ctx_launch_step(b->slots[s]);
+        for (int s : b->order) b->slots[s]->step -= 2;  // captured, not run
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(FRE_ERR_CUDA, "fre_batch: graph capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return bfail(FRE_ERR_CUDA, "fre_batch: graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return FRE_OK;
+}
+
+fre_status replay(fre_batch *b, long long pairs) {
+    for (long long k = 0; k < pairs; ++k) BCUDA(cudaGraphLaunch(b->graph, b->stream));
+    for (int s : b->order) b->slots[s]->step += 2 * pairs;
+    b->graph_replays += pairs;
+    return FRE_OK;
+}
+
+bool any_local(const fre_batch *b) {
+    for (auto *c : b->slots)
+        if (c && c->local) return true;
+    return false;
+}
+
+// Time the candidates on the live slot set: each takes one plain step (so
+// every kernel it uses has run once outside a capture), is captured, and
+// runs 3 graph replays, the last 2 timed -- 7 real steps per candidate.
+constexpr int kTuneSteps = 28;
+fre_status autotune(fre_batch *b, long long *taken) {
+    const int modes[4] = {0, 0, 0, 1};
+    const int bxs[4] = {32, 64, 128, 64};
+    double best = 1e300;
+    int best_k = 1;
+    cudaEvent_t e0, e1;
+    BCUDA(cudaEventCreate(&e0));
+    BCUDA(cudaEventCreate(&e1));
+    for (int k = 0; k < 4; ++k) {
+        b->mode = modes[k];
+        b->bx = bxs[k];
+        fre_status s = single_step(b);
+        if (s != FRE_OK) return s;
+        *taken += 1;
+        s = capture(b);
+        if (s != FRE_OK) return s;
+        s = replay(b, 1);  // warm-up
+        if (s != FRE_OK) return s;
+        cudaEventRecord(e0, b->stream);
+        s = replay(b, 2);
+        if (s != FRE_OK) return s;
+        cudaEventRecord(e1, b->stream);
+        BCUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        b->tuned_ms[k] = ms / 4.0;
+        *taken += 6;
+        if (ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->mode = modes[best_k];
+    b->bx = bxs[best_k];
+    b->tuned = true;
+    return capture(b);
+}
+
+fre_status benter(fre_batch *b) {
+    if (!b) return bfail(FRE_ERR_ARG, "batch is NULL%s");
+    BCUDA(cudaSetDevice(b->device_id));
+    return FRE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fre_status fre_batch_create(int lattice, int precision, void *cuda_stream, size_t budget_bytes, fre_batch **out) {
+    if (!out) return bfail(FRE_ERR_ARG, "fre_batch_create: out is NULL%s");
+    *out = nullptr;
+    if (lattice != FRE_D2Q9 && lattice != FRE_D3Q19) return bfail(FRE_ERR_ARG, "fre_batch_create: unknown lattice%s");
+    if (precision < FRE_FP64 || precision > FRE_BF16DEV)
+        return bfail(FRE_ERR_ARG, "fre_batch_create: unknown precision%s");
+    fre_batch *b = new fre_batch();
+    b->lattice = lattice;
+    b->precision = precision;
+    b->budget = budget_bytes;
+    b->bk = lattice == FRE_D2Q9 ? fre::batch_kernels_d2q9(precision) : fre::batch_kernels_d3q19(precision);
+    if (cudaGetDevice(&b->device_id) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return bfail(FRE_ERR_CUDA, "fre_batch_create: no CUDA device%s");
+    }
+    if (cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return bfail(FRE_ERR_CUDA, "fre_batch_create: cudaStreamCreate failed%s");
+        }
+        b->own_stream = true;
+    }
+    *out = b;
+    return FRE_OK;
+}
+
+fre_status fre_batch_add(fre_batch *b, const fre_params *p, double cx, double cy, double cz, double R, int *slot) {
+    fre_status s = benter(b);
+    if (s != FRE_OK) return s;
+    if (!p || !slot) return bfail(FRE_ERR_ARG, "fre_batch_add: NULL argument%s");
+    if (p->lattice != b->lattice || p->precision != b->precision)
+        return bfail(FRE_ERR_ARG, "fre_batch_add: lattice and precision must match the batch%s");
+    const size_t bytes = fre_device_bytes(p);
+    if (bytes == 0) return bfail(FRE_ERR_ARG, "fre_batch_add: invalid parameters%s");
+    if (b->in_use + bytes > b->budget) return bfail(FRE_ERR_BUDGET, "fre_batch_add: device-memory budget exceeded%s");
+    fre_ctx *c = nullptr;
+    s = fre_create(p, b->stream, &c);
+    if (s != FRE_OK) return s;
+    s = fre_init_droplet(c, cx, cy, cz, R);
+    if (s != FRE_OK) {
+        fre_destroy(c);
+        return s;
+    }
+    int k = 0;
+    while (k < (int)b->slots.size() && b->slots[k]) ++k;
+    if (k == (int)b->slots.size()) {
+        b->slots.push_back(nullptr);
+        b->slot_bytes.push_back(0);
+    }
+    b->slots[k] = c;
+    b->slot_bytes[k] = bytes;
+    b->in_use += bytes;
+    *slot = k;
+    invalidate(b);
+    return FRE_OK;
+}
+
+fre_status fre_batch_remove(fre_batch *b, int slot) {
+    fre_status s = benter(b);
+    if (s != FRE_OK) return s;
+    if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
+        return bfail(FRE_ERR_ARG, "fre_batch_remove: no such slot%s");
+    BCUDA(cudaStreamSynchronize(b->stream));
+    fre_destroy(b->slots[slot]);
+    b->slots[slot] = nullptr;
+    b->in_use -= b->slot_bytes[slot];
+    b->slot_bytes[slot] = 0;
+    invalidate(b);
+    return FRE_OK;
+}
+
+fre_status fre_batch_step(fre_batch *b, int nsteps) {
+    fre_status s = benter(b);
+    if (s != FRE_OK) return s;
+    if (nsteps < 0) return bfail(FRE_ERR_ARG, "fre_batch_step: nsteps < 0%s");
+    if (active(b).empty() || nsteps == 0) return FRE_OK;
+    long long left = nsteps;
+    // slots that still hold in-place populations take one batched step first
+    if (any_local(b)) {
+        const int m = b->mode;
+        b->mode = 0;
+        s = single_step(b);
+        b->mode = m;
+        if (s != FRE_OK) return s;
+        --left;
+    }
+    if (!b->tuned && left >= kTuneSteps + 4) {
+        long long taken = 0;
+        s = autotune(b, &taken);
+        if (s != FRE_OK) return s;
+        left -= taken;
+    }
+    if (left >= 2) {
+        if (!b->graph) {
+            s = capture(b);
+            if (s != FRE_OK) return s;
+        }
+        s = replay(b, left / 2);
+        if (s != FRE_OK) return s;
+        left -= 2 * (left / 2);
+    }
+    if (left == 1) {
+        s = single_step(b);
+        if (s != FRE_OK) return s;
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(FRE_ERR_CUDA, "fre_batch_step: %s", cudaGetErrorString(e));
+    return FRE_OK;
+}
+
+fre_status fre_batch_observables(fre_batch *b, int slot, fre_obs *out) {
+    fre_status s = benter(b);
+    if (s != FRE_OK) return s;
+    if (slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
+        return bfail(FRE_ERR_ARG, "fre_batch_observables: no such slot%s");
+    return fre_observables(b->slots[slot], out);
+}
+
+fre_ctx *fre_batch_context(fre_batch *b, int slot) {
+    if (!b || slot < 0 || slot >= (int)b->slots.size()) return nullptr;
+    return b->slots[slot];
+}
+
+int fre_batch_slots(const fre_batch *b, int *slots, int max_slots) {
+    if (!b) return -1;
+    int n = 0;
+    for (int i = 0; i < (int)b->slots.size(); ++i)
+        if (b->slots[i]) {
+            if (slots && n < max_slots) slots[n] = i;
+            ++n;
+        }
+    return n;
+}
+
+size_t fre_batch_bytes_in_use(const fre_batch *b) { return b ? b->in_use : 0; }
+
+fre_status fre_batch_tuning(const fre_batch *b, int *mode, int *bx, double *ms_per_step) {
+    if (!b) return bfail(FRE_ERR_ARG, "batch is NULL%s");
+    if (mode) *mode = b->mode;
+    if (bx) *bx = b->bx;
+    if (ms_per_step)
+        for (int k = 0; k < 4; ++k) ms_per_step[k] = b->tuned_ms[k];
+    return b->tuned ? FRE_OK : FRE_ERR_STATE;
+}
+
+fre_status fre_batch_synchronize(fre_batch *b) {
+    fre_status s = benter(b);
+    if (s != FRE_OK) return s;
+    BCUDA(cudaStreamSynchronize(b->stream));
+    return FRE_OK;
+}
+
+void fre_batch_destroy(fre_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device_id);
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (auto *c : b->slots)
+        if (c) fre_destroy(c);
+    for (auto *p : b->d_cases)
+        if (p) cudaFree(p);
+    if (b->d_bstart) cudaFree(b->d_bstart);
+    if (b->d_gstart) cudaFree(b->d_gstart);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // extern "C"

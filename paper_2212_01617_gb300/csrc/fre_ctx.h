@@ -1,0 +1,46 @@
+// Internal: the context behind the opaque fre_ctx handle of the C ABI, and
+// the pieces of the runtime that the batch runtime reuses.
+#pragma once
+
+#include <vector>
+
+#include "fre_internal.h"
+
+struct fre_ctx {
+    fre_params p;
+    int q = 0;
+    int device_id = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    const fre::KernelSet *ks = nullptr;
+    fre::Geo G{};
+    fre::Phys P{};
+    fre::Buf buf[2]{};
+    void *phi[2]{};
+    void *mu = nullptr;
+    unsigned char *solid = nullptr;
+    int *ghost = nullptr;
+    int n_ghost = 0;
+    double *red = nullptr;
+    int red_blocks = 0;
+    fre_obs *obs_dev = nullptr;
+    fre_obs *obs_host = nullptr;
+    int *err_dev = nullptr;  // set by a kernel whose bounded wait timed out
+    double *staging = nullptr;
+    std::vector<void *> allocs;
+    int cur = 0;        // buffer holding the state
+    int pp = 1;         // phi buffer holding phi of the previous step
+    bool local = true;  // state is pre-collision (no streaming pending)
+    bool initialised = false;
+    bool rows = false;  // the row kernels run the hot path
+    int row_w = 0;      // their chunk width
+    bool fullrow = false;  // the update runs on the full-row kernel
+    long long step = 0;
+};
+
+namespace fre {
+// launch descriptor of the context's current state
+Launch ctx_launch(fre_ctx *c);
+// the kernels of one time step on the context stream; advances the state
+void ctx_launch_step(fre_ctx *c);
+}  // namespace fre

@@ -49,6 +49,7 @@ struct Launch {
     int red_blocks;
     fre_obs *obs;          // device observables
     int W;                 // chunk width of the row kernels
+    int pull;              // batched kernels: stream from the post-collision buffer
     int *err;              // device error word (pipeline wait timed out)
     double *staging;       // FP64 staging of host I/O (n doubles per field)
     cudaStream_t stream;
@@ -80,6 +81,29 @@ struct KernelSet {
     void (*phi_fullrow)(const Launch &, bool pull);
     void (*mu_fullrow)(const Launch &);
 };
+
+// Many contexts of one lattice and storage format advanced by one launch
+// per kernel: per-slot launch descriptors and block tables on the device.
+struct BatchLaunch {
+    const Launch *cases;     // [nslots]
+    const int *block_start;  // [nslots + 1], exclusive prefix of lattice blocks
+    const int *ghost_start;  // [nslots + 1], exclusive prefix of ghost blocks
+    int nslots;
+    int total_blocks;
+    int total_ghost_blocks;
+    cudaStream_t stream;
+};
+
+// Batched per-node kernels, templated on the block width BX (BY = 256/BX).
+struct BatchKernels {
+    void (*phi)(const BatchLaunch &, int bx);
+    void (*mu)(const BatchLaunch &, int bx);
+    void (*ghost)(const BatchLaunch &, int field);  // field 0: phi, 1: mu
+    void (*update)(const BatchLaunch &, int bx);
+};
+
+const BatchKernels *batch_kernels_d2q9(int precision);
+const BatchKernels *batch_kernels_d3q19(int precision);
 
 const KernelSet *kernels_d2q9(int precision);
 const KernelSet *kernels_d3q19(int precision);

@@ -310,11 +310,10 @@ static_assert(kBX * kBY == kBlock, "block shape");
     if (x_ >= (L).G.nx || y_ >= (L).G.ny) return;                      \
     const Site s = make_site((L).G, x_, y_, z_)
 
+// phi = sum of the pulled g at one node
 template <int Q, int FMT, bool PULL>
-__global__ void __launch_bounds__(kBlock) k_phi(Launch L) {
+__device__ __forceinline__ void node_phi(const Launch &L, const Site &s) {
     using T = typename Fmt<FMT>::T;
-    FRE_SITE_OR_RETURN(L, s);
-    if (is_solid(L.G, s.n)) return;
     T g[Q];
     gather<Q, FMT, PULL, false>(L, s, nullptr, g);
     T ph = T(0);
@@ -323,11 +322,16 @@ __global__ void __launch_bounds__(kBlock) k_phi(Launch L) {
     static_cast<T *>(L.phi)[s.n] = ph;
 }
 
-// Stencil values at roller solids: w-weighted mean over fluid neighbours.
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_phi(Launch L) {
+    FRE_SITE_OR_RETURN(L, s);
+    if (is_solid(L.G, s.n)) return;
+    node_phi<Q, FMT, PULL>(L, s);
+}
+
+// Stencil value at roller solid ghost[t]: w-weighted mean over fluid neighbours.
 template <int Q, typename T>
-__global__ void __launch_bounds__(kBlock) k_ghost(Launch L, T *field) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L.n_ghost) return;
+__device__ __forceinline__ void node_ghost(const Launch &L, T *field, int t) {
     int x, y, z;
     decode(L.G, L.ghost[t], x, y, z);
     const Site s = make_site(L.G, x, y, z);
@@ -342,11 +346,16 @@ __global__ void __launch_bounds__(kBlock) k_ghost(Launch L, T *field) {
     field[s.n] = den > T(0) ? num / den : T(0);
 }
 
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlock) k_ghost(Launch L, T *field) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.n_ghost) return;
+    node_ghost<Q, T>(L, field, t);
+}
+
 // mu = A (phi^3 - phi) - kappa lap(phi), lap = (2/cs^2) sum w_i (phi(x+c_i) - phi(x))
 template <int Q, typename T>
-__global__ void __launch_bounds__(kBlock) k_mu(Launch L) {
-    FRE_SITE_OR_RETURN(L, s);
-    if (is_solid(L.G, s.n)) return;
+__device__ __forceinline__ void node_mu(const Launch &L, const Site &s) {
     const T *__restrict__ phi = static_cast<const T *>(L.phi);
     const T p0 = phi[s.n];
     T lap = T(0);
@@ -356,13 +365,18 @@ __global__ void __launch_bounds__(kBlock) k_mu(Launch L) {
     static_cast<T *>(L.mu)[s.n] = T(L.P.A) * (p0 * p0 * p0 - p0) - T(L.P.kappa) * lap;
 }
 
-// Fused pull + collide of f and g for one node (Algorithm 1).
-template <int Q, int FMT, bool PULL>
-__global__ void __launch_bounds__(kBlock) k_update(Launch L) {
-    using T = typename Fmt<FMT>::T;
-    using P = Pop<Q, FMT>;
+template <int Q, typename T>
+__global__ void __launch_bounds__(kBlock) k_mu(Launch L) {
     FRE_SITE_OR_RETURN(L, s);
     if (is_solid(L.G, s.n)) return;
+    node_mu<Q, T>(L, s);
+}
+
+// Fused pull + collide of f and g for one node (Algorithm 1).
+template <int Q, int FMT, bool PULL>
+__device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
     const int n = s.n;
     T f[Q], g[Q];
     gather<Q, FMT, PULL, true>(L, s, f, g);
@@ -395,6 +409,13 @@ __global__ void __launch_bounds__(kBlock) k_update(Launch L) {
     // rest populations close the collision invariants: sum f* = rho, sum g* = phi
     P::stf(L.dst, L.G.np, 0, n, m.rho - fsum, T(L.P.rho0));
     P::stg(L.dst, L.G.np, 0, n, m.phi - gsum);
+}
+
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_update(Launch L) {
+    FRE_SITE_OR_RETURN(L, s);
+    if (is_solid(L.G, s.n)) return;
+    node_update<Q, FMT, PULL>(L, s);
 }
 
 // Macroscopic fields -> staging (FP64): rho, ux, uy, uz, phi, mu.

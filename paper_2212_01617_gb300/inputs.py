@@ -35,3 +35,43 @@ def random_fields(shape, seed: int = SEED, u_amp: float = 0.02, drho: float = 0.
     ux, uy, uz = (u_amp * r.uniform(-1, 1, shape) for _ in range(3))
     phi = np.tanh(3.0 * r.uniform(-1, 1, shape))
     return rho, ux, uy, uz, phi
+
+
+def batch_cases(n: int = 64, seed: int = SEED + 3):
+    """Draws of a D2Q9 batch of `n` uneven cases: alternating parallel-band
+    shear and four-roller devices, Nx even and uniform in [64, 512], capillary
+    number Ca ~ U(0.05, 0.5) and droplet size ratio R/H ~ U(0.1, 0.3).
+
+    Returns a list of dicts (device, nx, ca, r_over_h); the lattice height and
+    the wall speed that realises Ca are the caller's."""
+    r = rng(seed)
+    out = []
+    for k in range(n):
+        out.append({"device": "shear" if k % 2 == 0 else "four_roller",
+                    "nx": 2 * int(r.integers(32, 257)),
+                    "ca": float(r.uniform(0.05, 0.5)),
+                    "r_over_h": float(r.uniform(0.1, 0.3))})
+    return out
+
+
+SERVE_SIZES = ((64, 64, 64), (96, 96, 96), (128, 64, 64), (192, 96, 96))
+
+
+def serving_trace(n: int = 400, rate: float = 20.0, seed: int = SEED + 4):
+    """A finite Poisson request trace: exponential inter-arrival gaps of mean
+    1/rate seconds, lattice size uniform over SERVE_SIZES, device shear or
+    four-roller with equal odds, Ca ~ U(0.05, 0.45), R/H ~ U(0.1, 0.3).
+
+    Returns a list of dicts (t_arrival, shape, device, ca, r_over_h) in
+    arrival order."""
+    r = rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += float(r.exponential(1.0 / rate))
+        out.append({"t_arrival": t,
+                    "shape": SERVE_SIZES[int(r.integers(0, len(SERVE_SIZES)))],
+                    "device": "shear" if r.uniform() < 0.5 else "four_roller",
+                    "ca": float(r.uniform(0.05, 0.45)),
+                    "r_over_h": float(r.uniform(0.1, 0.3))})
+    return out
