@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -410,6 +412,103 @@ def _batch_workload(args, fre, cases, nodes, stream):
     return 0
 
 
+# D3Q19 serving requests: A = kappa = 0.01 (xi = 1), tau_f = 1.5 (dynamic
+# viscosity 1/3), tau_g = 1, Gamma = 1
+SERVE_PHYS = dict(tau_f=1.5, tau_g=1.0, A=0.01, kappa=0.01, gamma_mob=1.0, rho0=1.0)
+
+
+def serve_case_params(c):
+    """Lattice, droplet and wall speed of one request.  Shear: H = Ny, rate
+    G = 2 u_w / H.  Four-roller: H = Nx/2, rate G = u_w / (Nx/4).  R = (R/H) H
+    and Ca = mu G R / sigma, so u_w = Ca sigma / (2 mu (R/H)) for both."""
+    nx, ny, nz = c["shape"]
+    H = ny if c["device"] == "shear" else nx / 2
+    sigma = (8.0 * SERVE_PHYS["kappa"] * SERVE_PHYS["A"] / 9.0) ** 0.5
+    mu_visc = SERVE_PHYS["rho0"] * (SERVE_PHYS["tau_f"] - 0.5) / 3.0
+    u_w = c["ca"] * sigma / (2.0 * mu_visc * c["r_over_h"])
+    params = dict(SERVE_PHYS, lattice="d3q19", device=c["device"], nx=nx, ny=ny, nz=nz, u_wall=u_w)
+    drop = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, c["r_over_h"] * H)
+    return params, drop
+
+
+def drive_server(srv, trace, cases):
+    """Submit each request when its arrival time comes (server clock) and
+    advance the server until every request has a result."""
+    start = srv.clock()
+    n = len(trace)
+    i, by_id, results = 0, {}, {}
+    while len(results) < n:
+        now = srv.clock() - start
+        while i < n and trace[i]["t_arrival"] <= now:
+            p, d = cases[i]
+            by_id[srv.submit(*d, **p)] = i
+            i += 1
+        running = srv.advance()
+        for r in srv.results():
+            k = by_id[r["id"]]
+            r["latency"] = r["t_done"] - (start + trace[k]["t_arrival"])
+            r["nodes"] = int(np.prod(trace[k]["shape"]))
+            results[k] = r
+        if running == 0 and srv.stats()["queued"] == 0 and i < n:
+            wait = trace[i]["t_arrival"] - (srv.clock() - start)
+            if wait > 0:
+                time.sleep(wait)
+    end = max(r["t_done"] for r in results.values())
+    return results, end - start
+
+
+def run_serve_workload(args):
+    """Poisson-arriving D3Q19 droplet-deformation requests: the serving loop
+    (FP16 deviation store, continuous batching under a 150 GB budget)
+    against the same requests served one at a time in plain FP32."""
+    import torch
+    import paper_2212_01617_gb300 as fre
+    from paper_2212_01617_gb300 import inputs
+    trace = inputs.serving_trace(args.serve_requests)
+    cases = [serve_case_params(c) for c in trace]
+    stream = torch.cuda.Stream()
+    out = {}
+    with torch.cuda.stream(stream):
+        arms = [("batched_fp16dev", dict(precision="fp16dev", target_nodes=args.serve_target_nodes,
+                                         chunk_steps=250)),
+                ("sequential_fp32", dict(precision="fp32", max_running=1, chunk_steps=1000))]
+        for name, kw in arms:
+            prec = kw["precision"]
+            srv = fre.Server("d3q19", budget_bytes=150 << 30, check_every=1000, tol_D=1e-4,
+                             max_steps=args.serve_max_steps, stream=stream.cuda_stream, **kw)
+            cs = [(dict(p, precision=prec), d) for p, d in cases]
+            res, wall = drive_server(srv, trace, cs)
+            st = srv.stats()
+            srv.close()
+            lat = np.array([res[k]["latency"] for k in range(len(trace))])
+            upd = sum(res[k]["steps"] * res[k]["nodes"] for k in range(len(trace)))
+            outcomes = {}
+            for r in res.values():
+                outcomes[r["outcome"]] = outcomes.get(r["outcome"], 0) + 1
+            out[name] = {"aggregate_mlups": upd / wall / 1e6, "wall_s": wall,
+                         "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                         "mean_s": float(lat.mean()), "node_updates": upd, "outcomes": outcomes,
+                         "mean_steps": float(np.mean([r["steps"] for r in res.values()])),
+                         "contexts_created": st["contexts_created"], "contexts_reused": st["contexts_reused"]}
+            log(f"{name}: {json.dumps(out[name])}")
+    b, s_ = out["batched_fp16dev"], out["sequential_fp32"]
+    line = {"metric": "serving D3Q19 FRE-LBM: aggregate MLUPS and p50/p99 time-to-result",
+            "value": b["aggregate_mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16-store/f32",
+            "data": "synthetic",
+            "config": {"workload": f"{len(trace)} Poisson requests (20/s), D3Q19 sizes 64^3, 96^3, 128x64x64, "
+                                   "192x96x96, shear or four-roller, Ca U(0.05,0.45), R/H U(0.1,0.3), run until "
+                                   "|dD| < 1e-4 per 1000 steps or breakup, 150 GB budget",
+                       "max_steps": args.serve_max_steps, "target_nodes": args.serve_target_nodes},
+            "p50_s": b["p50_s"], "p99_s": b["p99_s"],
+            "sequential_fp32": s_,
+            "batched_fp16dev": b,
+            "speedup_p50": s_["p50_s"] / b["p50_s"], "speedup_p99": s_["p99_s"] / b["p99_s"],
+            "throughput_ratio": b["aggregate_mlups"] / s_["aggregate_mlups"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,11 +522,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-case", default=None,
                     help="NXxNYxNZ: run a few steps of a small case (ncu captures) and exit")
-    ap.add_argument("--workload", choices=["lattice", "batch"], default="lattice",
-                    help="lattice: the 512x256x256 D3Q19 lattice (default); batch: 64 uneven D2Q9 cases")
+    ap.add_argument("--workload", choices=["lattice", "batch", "serve"], default="lattice",
+                    help="lattice: the 512x256x256 D3Q19 lattice (default); batch: 64 uneven D2Q9 cases; "
+                         "serve: Poisson-arriving D3Q19 requests through the serving loop")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-target-nodes", type=int, default=8_000_000)
+    ap.add_argument("--serve-max-steps", type=int, default=30000)
     args = ap.parse_args()
     if args.workload == "batch":
         return run_batch_workload(args)
+    if args.workload == "serve":
+        return run_serve_workload(args)
     if args.profile_case:
         return profile_case(args.profile_case, [p for p in args.precisions.split(",") if p])
     if args.warmup < 3:

@@ -266,8 +266,9 @@ size_t fre_batch_bytes_in_use(const fre_batch *b);
 
 /* Autotuner result: mode (0 one launch per kernel for all slots, 1 each
  * slot's own kernels), block width, and ms per step measured for the four
- * candidates (batched width 32, 64, 128; per-slot).  FRE_ERR_STATE if the
- * current slot set has not been tuned yet. */
+ * candidates (batched width 32, 64, 128; per-slot).  FRE_ERR_STATE if no
+ * tuning is in force: none ran yet, or the slot count has since changed by
+ * more than a factor 2 (smaller changes keep the tuned mode). */
 fre_status fre_batch_tuning(const fre_batch *b, int *mode, int *bx, double *ms_per_step);
 
 /* Wait for the batch's queued work. */
@@ -275,6 +276,92 @@ fre_status fre_batch_synchronize(fre_batch *b);
 
 /* Destroy the batch and every slot; NULL-safe. */
 void fre_batch_destroy(fre_batch *b);
+
+/* ---------------------------------------------------------------- serving
+ *
+ * A serving loop over a batch: droplet-deformation requests are queued,
+ * admitted first come first served under a device-memory budget, advanced
+ * together, checked every check_every of their own steps and retired when a
+ * stopping rule holds (Sec. 3 measures the deformation D of the droplet):
+ *   FRE_SERVE_CONVERGED  |D - D_prev| < tol_D between consecutive checks;
+ *   FRE_SERVE_BREAKUP    no node with phi > 0 left, or the Laplace pressure
+ *                        dp at the centroid below breakup_frac (d - 1)
+ *                        sigma / R0, sigma = sqrt(8 kappa A / 9): the
+ *                        centroid left the liquid, the drop split;
+ *   FRE_SERVE_UNSTABLE   non-finite values or |u| > 0.3;
+ *   FRE_SERVE_MAX_STEPS  max_steps reached.
+ * Retired contexts stay allocated in a pool and serve later requests of the
+ * same geometry (lattice, precision, device, sizes) without allocation; the
+ * pool is trimmed when a new geometry needs the budget. */
+typedef struct fre_server fre_server;
+
+typedef enum {
+    FRE_SERVE_RUNNING = 0,
+    FRE_SERVE_CONVERGED = 1,
+    FRE_SERVE_BREAKUP = 2,
+    FRE_SERVE_MAX_STEPS = 3,
+    FRE_SERVE_UNSTABLE = 4,
+    FRE_SERVE_REJECTED = 5, /* invalid, or larger than the whole budget */
+    FRE_SERVE_FAILED = 6    /* could not be started (e.g. allocation failed) */
+} fre_serve_outcome;
+
+typedef struct {
+    size_t budget_bytes;     /* device memory of running + pooled contexts */
+    long long target_nodes;  /* admit while running nodes stay <= this (0: no limit) */
+    int max_running;         /* at most this many running requests (0: no limit) */
+    int chunk_steps;         /* steps per fre_server_advance (at most) */
+    int check_every;         /* steps of a request between two checks */
+    double tol_D;            /* convergence threshold on |D - D_prev| */
+    long long max_steps;     /* step cap of a request */
+    double breakup_frac;     /* breakup threshold on dp, fraction of (d-1) sigma / R0 */
+} fre_serve_config;
+
+typedef struct {
+    long long id;
+    int outcome;        /* fre_serve_outcome */
+    long long steps;    /* steps the request ran */
+    double t_submit;    /* seconds on the server clock */
+    double t_admit;     /* -1 if never admitted */
+    double t_done;
+    fre_obs obs;        /* observables at the final check (zero if none) */
+} fre_serve_result;
+
+typedef struct {
+    int running, queued;
+    size_t bytes_running, bytes_pooled;
+    long long running_nodes;
+    long long node_updates;     /* sum over advances of running nodes x steps */
+    long long steps_advanced;   /* batch steps issued */
+    long long contexts_created, contexts_reused;
+} fre_serve_stats;
+
+/* Create a server for one lattice and storage format; cuda_stream as in
+ * fre_create.  chunk_steps and check_every must be >= 1. */
+fre_status fre_server_create(int lattice, int precision, const fre_serve_config *cfg, void *cuda_stream,
+                             fre_server **out);
+
+/* Queue a request (parameters, droplet centre and radius); *id receives its
+ * id.  A request that can never fit is finished at once as REJECTED (its
+ * result is returned by fre_server_results). */
+fre_status fre_server_submit(fre_server *s, const fre_params *p, double cx, double cy, double cz, double R,
+                             long long *id);
+
+/* Admit what fits, advance every running request by up to chunk_steps
+ * steps (stopping early at the next due check), run the due checks and
+ * retire finished requests.  *running (nullable) receives the number of
+ * requests still running.  Synchronises at each check. */
+fre_status fre_server_advance(fre_server *s, int *running);
+
+/* Pop up to max finished results (completion order); returns the count. */
+int fre_server_results(fre_server *s, fre_serve_result *out, int max);
+
+fre_status fre_server_stats(const fre_server *s, fre_serve_stats *out);
+
+/* Seconds since fre_server_create (the clock of the result timestamps). */
+double fre_server_clock(const fre_server *s);
+
+/* Destroy the server, its batch and its pool; NULL-safe. */
+void fre_server_destroy(fre_server *s);
 
 /* Destroy a context and free its device memory; NULL-safe. */
 void fre_destroy(fre_ctx *c);

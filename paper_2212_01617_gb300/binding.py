@@ -35,6 +35,8 @@ EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_field
            "fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
            "fre_batch_observables", "fre_batch_context", "fre_batch_slots", "fre_batch_bytes_in_use",
            "fre_batch_tuning", "fre_batch_synchronize", "fre_batch_destroy",
+           "fre_server_create", "fre_server_submit", "fre_server_advance", "fre_server_results",
+           "fre_server_stats", "fre_server_clock", "fre_server_destroy",
            "fre_destroy", "fre_last_error"]
 FRE_FLAG_GENERIC_KERNELS = 1
 
@@ -67,6 +69,33 @@ class fre_obs(C.Structure):
             v = getattr(self, name)
             out[name] = list(v) if hasattr(v, "__len__") else v
         return out
+
+
+SERVE_OUTCOMES = {0: "running", 1: "converged", 2: "breakup", 3: "max_steps", 4: "unstable", 5: "rejected",
+                  6: "failed"}
+
+
+class fre_serve_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("target_nodes", C.c_longlong), ("max_running", C.c_int),
+                ("chunk_steps", C.c_int), ("check_every", C.c_int), ("tol_D", C.c_double),
+                ("max_steps", C.c_longlong), ("breakup_frac", C.c_double)]
+
+
+class fre_serve_result(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("outcome", C.c_int), ("steps", C.c_longlong), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_done", C.c_double), ("obs", fre_obs)]
+
+    def as_dict(self) -> dict:
+        return {"id": self.id, "outcome": SERVE_OUTCOMES.get(self.outcome, str(self.outcome)),
+                "steps": self.steps, "t_submit": self.t_submit, "t_admit": self.t_admit, "t_done": self.t_done,
+                "obs": self.obs.as_dict()}
+
+
+class fre_serve_stats(C.Structure):
+    _fields_ = [("running", C.c_int), ("queued", C.c_int), ("bytes_running", C.c_size_t),
+                ("bytes_pooled", C.c_size_t), ("running_nodes", C.c_longlong), ("node_updates", C.c_longlong),
+                ("steps_advanced", C.c_longlong), ("contexts_created", C.c_longlong),
+                ("contexts_reused", C.c_longlong)]
 
 
 _lock = threading.Lock()
@@ -122,6 +151,19 @@ def load_library(path: str = LIB_PATH):
         L.fre_batch_synchronize.argtypes = [vp]
         L.fre_batch_destroy.argtypes = [vp]
         L.fre_batch_destroy.restype = None
+        L.fre_server_create.argtypes = [C.c_int, C.c_int, C.POINTER(fre_serve_config), vp, C.POINTER(vp)]
+        L.fre_server_submit.argtypes = [vp, C.POINTER(fre_params), C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.POINTER(C.c_longlong)]
+        L.fre_server_advance.argtypes = [vp, C.POINTER(C.c_int)]
+        L.fre_server_results.restype = C.c_int
+        L.fre_server_results.argtypes = [vp, C.POINTER(fre_serve_result), C.c_int]
+        L.fre_server_stats.argtypes = [vp, C.POINTER(fre_serve_stats)]
+        L.fre_server_clock.restype = C.c_double
+        L.fre_server_clock.argtypes = [vp]
+        L.fre_server_destroy.restype = None
+        L.fre_server_destroy.argtypes = [vp]
+        for name in ("fre_server_create", "fre_server_submit", "fre_server_advance", "fre_server_stats"):
+            getattr(L, name).restype = C.c_int
         for name in ("fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
                      "fre_batch_observables", "fre_batch_tuning", "fre_batch_synchronize"):
             getattr(L, name).restype = C.c_int
@@ -418,3 +460,65 @@ class Batch:
 
     def synchronize(self):
         _check(load_library().fre_batch_synchronize(self.h), "fre_batch_synchronize")
+
+
+class Server:
+    """Serving loop over a batch (C ABI fre_server_*): submit requests,
+    call advance() until they finish, collect results()."""
+
+    def __init__(self, lattice="d3q19", precision="fp16dev", budget_bytes=150 << 30, target_nodes=0,
+                 max_running=0, chunk_steps=250, check_every=1000, tol_D=1e-4, max_steps=100000,
+                 breakup_frac=0.25, stream=None):
+        self.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg = fre_serve_config(int(budget_bytes), int(target_nodes), int(max_running), int(chunk_steps),
+                               int(check_every), float(tol_D), int(max_steps), float(breakup_frac))
+        h = C.c_void_p()
+        st = stream if stream is not None else current_stream_handle()
+        _check(load_library().fre_server_create(self.lattice, self.precision, C.byref(cfg),
+                                                C.c_void_p(st) if st else None, C.byref(h)), "fre_server_create")
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().fre_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, cx, cy, cz, R, **params) -> int:
+        params.setdefault("lattice", self.lattice)
+        params.setdefault("precision", self.precision)
+        p = make_params(**params)
+        rid = C.c_longlong(0)
+        _check(load_library().fre_server_submit(self.h, C.byref(p), cx, cy, cz, R, C.byref(rid)),
+               "fre_server_submit")
+        return rid.value
+
+    def advance(self) -> int:
+        n = C.c_int(0)
+        _check(load_library().fre_server_advance(self.h, C.byref(n)), "fre_server_advance")
+        return n.value
+
+    def results(self, max_results: int = 256):
+        buf = (fre_serve_result * max_results)()
+        n = load_library().fre_server_results(self.h, buf, max_results)
+        return [buf[i].as_dict() for i in range(max(n, 0))]
+
+    def stats(self) -> dict:
+        st = fre_serve_stats()
+        _check(load_library().fre_server_stats(self.h, C.byref(st)), "fre_server_stats")
+        return {name: getattr(st, name) for name, _ in st._fields_}
+
+    def clock(self) -> float:
+        return float(load_library().fre_server_clock(self.h))

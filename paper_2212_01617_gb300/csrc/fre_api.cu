@@ -204,6 +204,24 @@ void fre::ctx_launch_step(fre_ctx *c) {
     c->step++;
 }
 
+bool fre::same_geometry(const fre_params *p, const fre_params *q) {
+    return p->lattice == q->lattice && p->precision == q->precision && p->device == q->device && p->nx == q->nx &&
+           p->ny == q->ny && p->nz == q->nz && p->flags == q->flags;
+}
+
+fre_status fre::ctx_reparam(fre_ctx *c, const fre_params *p) {
+    if (!c || !p) return fail(FRE_ERR_ARG, "ctx_reparam: NULL argument");
+    if (!same_geometry(&c->p, p)) return fail(FRE_ERR_ARG, "ctx_reparam: geometry differs");
+    Sizes s;
+    std::string why;
+    if (!sizes_of(p, s, &why)) return fail(FRE_ERR_ARG, "ctx_reparam: %s", why.c_str());
+    c->p = *p;
+    c->G.uwall = p->u_wall;
+    c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0};
+    c->initialised = false;
+    return FRE_OK;
+}
+
 namespace {
 
 fre::Launch launch_of(fre_ctx *c) { return fre::ctx_launch(c); }

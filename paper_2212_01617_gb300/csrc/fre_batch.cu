@@ -39,6 +39,7 @@ struct fre_batch {
     int mode = 0;  // 0 batched, 1 per-slot
     int bx = 64;
     bool tuned = false;
+    int tuned_nslots = 0;  // slot count the tuning was measured on
     double tuned_ms[4] = {0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128 and per-slot
     cudaGraphExec_t graph = nullptr;
     long long graph_replays = 0;
@@ -64,17 +65,22 @@ void drop_graph(fre_batch *b) {
     b->graph = nullptr;
 }
 
-void invalidate(fre_batch *b) {
-    b->tables_valid = false;
-    b->tuned = false;
-    drop_graph(b);
-}
-
 std::vector<int> active(const fre_batch *b) {
     std::vector<int> a;
     for (int i = 0; i < (int)b->slots.size(); ++i)
         if (b->slots[i]) a.push_back(i);
     return a;
+}
+
+// The slot set changed: tables and graph are rebuilt; the tuned launch mode
+// is kept while the slot count stays within a factor 2 of the tuned one.
+void invalidate(fre_batch *b) {
+    b->tables_valid = false;
+    drop_graph(b);
+    if (b->tuned) {
+        const int n = (int)active(b).size();
+        if (2 * n < b->tuned_nslots || n > 2 * b->tuned_nslots) b->tuned = false;
+    }
 }
 
 // launch descriptor of a context after one more step (buffers swapped)
@@ -308,6 +314,7 @@ fre_status autotune(fre_batch *b, long long *taken) {
     b->mode = modes[best_k];
     b->bx = bxs[best_k];
     b->tuned = true;
+    b->tuned_nslots = (int)active(b).size();
     return capture(b);
 }
 
@@ -318,6 +325,38 @@ fre_status benter(fre_batch *b) {
 }
 
 }  // namespace
+
+fre_status fre::batch_attach(fre_batch *b, fre_ctx *c, size_t bytes, int *slot) {
+    if (!b || !c || !slot) return bfail(FRE_ERR_ARG, "batch_attach: NULL argument%s");
+    if (c->p.lattice != b->lattice || c->p.precision != b->precision || c->stream != b->stream)
+        return bfail(FRE_ERR_ARG, "batch_attach: lattice, precision and stream must match the batch%s");
+    if (!c->initialised) return bfail(FRE_ERR_STATE, "batch_attach: context not initialised%s");
+    if (b->in_use + bytes > b->budget) return bfail(FRE_ERR_BUDGET, "batch_attach: device-memory budget exceeded%s");
+    int k = 0;
+    while (k < (int)b->slots.size() && b->slots[k]) ++k;
+    if (k == (int)b->slots.size()) {
+        b->slots.push_back(nullptr);
+        b->slot_bytes.push_back(0);
+    }
+    b->slots[k] = c;
+    b->slot_bytes[k] = bytes;
+    b->in_use += bytes;
+    *slot = k;
+    invalidate(b);
+    return FRE_OK;
+}
+
+fre_ctx *fre::batch_detach(fre_batch *b, int slot) {
+    if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot]) return nullptr;
+    fre_ctx *c = b->slots[slot];
+    b->slots[slot] = nullptr;
+    b->in_use -= b->slot_bytes[slot];
+    b->slot_bytes[slot] = 0;
+    invalidate(b);
+    return c;
+}
+
+cudaStream_t fre::batch_stream(const fre_batch *b) { return b ? b->stream : nullptr; }
 
 extern "C" {
 

@@ -43,4 +43,22 @@ namespace fre {
 Launch ctx_launch(fre_ctx *c);
 // the kernels of one time step on the context stream; advances the state
 void ctx_launch_step(fre_ctx *c);
+// give a context new physical parameters of the same geometry (lattice,
+// precision, device, sizes and flags equal); the state must be
+// re-initialised before the next step
+fre_status ctx_reparam(fre_ctx *c, const fre_params *p);
+// true when a context made for *p could serve *q after ctx_reparam
+bool same_geometry(const fre_params *p, const fre_params *q);
+}  // namespace fre
+
+struct fre_batch;
+namespace fre {
+// hand an existing context (created on the batch stream, initialised) to a
+// batch as a new slot; `bytes` is charged to the batch budget
+fre_status batch_attach(fre_batch *b, fre_ctx *c, size_t bytes, int *slot);
+// take a slot's context out of a batch without synchronising or freeing it
+// (work already queued on the stream still uses it)
+fre_ctx *batch_detach(fre_batch *b, int slot);
+// the stream of a batch
+cudaStream_t batch_stream(const fre_batch *b);
 }  // namespace fre
