@@ -27,8 +27,9 @@
  *   6. g_eq (Eq. geq, g_eq_0 = phi - sum_{i!=0} g_eq_i), g*_i = g_i -
  *      (g_i - g_eq_i)/tau_g  (Eq. LBEg)
  *   7. streaming f(x+c_i, t+1) = f*(x, t)  (Sec. 2.3), with half-way
- *      bounce-back and the moving-wall term of the "standard LBM boundary
- *      methods" (Sec. 2.3) where the source node x-c_i is solid:
+ *      bounce-back and the moving-wall term (the usual LBM boundary
+ *      treatment the paper defers to, Sec. 2.3) where the source node x-c_i
+ *      is solid:
  *         f_i(x,t+1) = f*_ibar(x,t) + 2 w_i rho_w (c_i . u_w) / cs^2,
  *         g_i(x,t+1) = g*_ibar(x,t) + 2 w_i phi(x,t) (c_i . u_w) / cs^2,
  *      with rho_w = rho0.
