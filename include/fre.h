@@ -17,7 +17,7 @@
  *   BGK + Guo for f, BGK for g              (Eq. bgk, Eq. feq, Eq. Fi,
  *                                            Eq. geq, Eq. LBEg)
  *   streaming with half-way bounce-back and the moving-wall term at solid
- *   sources (Sec. 2.3, "standard LBM boundary methods").
+ *   sources (the usual LBM wall treatment the paper defers to, Sec. 2.3).
  *
  * Conventions shared by every entry point:
  *   - node index n = (z*ny + y)*nx + x, x fastest; D2Q9 has nz = 1;
