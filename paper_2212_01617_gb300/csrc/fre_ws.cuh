@@ -445,6 +445,51 @@ struct FullRowLayout {
 
 __device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
 
+// Two adjacent nodes per consumer thread: FP32 arithmetic on packed pairs
+// (the paired add / multiply / fused multiply-add of sm_100 and later).
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// acc + c a for a lattice component c in {-1, 0, 1} (folded after unrolling)
+__device__ __forceinline__ float2 acc_c(float2 acc, float2 a, int c) {
+    return c > 0 ? add2(acc, a) : (c < 0 ? sub2(acc, a) : acc);
+}
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+// row[x], row[x + 1] for even x (one aligned vector load)
+__device__ __forceinline__ float2 ld_pair(const float *row, int x) { return *reinterpret_cast<const float2 *>(row + x); }
+__device__ __forceinline__ float2 ld_pair(const __half *row, int x) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(row + x));
+}
+__device__ __forceinline__ float2 ld_pair(const __nv_bfloat16 *row, int x) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(row + x));
+}
+// row[xa], row[xb]
+template <typename S>
+__device__ __forceinline__ float2 ld_two(const S *row, int xa, int xb) {
+    return make_float2(to_f(row[xa]), to_f(row[xb]));
+}
+// the pulled pair of one staged row: x0, x0 + 1 shifted by -cx with wrap
+template <typename S>
+__device__ __forceinline__ float2 ld_shift(const S *row, int x0, int cx, int nx) {
+    if (cx == 0) return ld_pair(row, x0);
+    return ld_two(row, wrap_x(x0 - cx, nx), wrap_x(x0 + 1 - cx, nx));
+}
+__device__ __forceinline__ void st_pair(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ float2 st_pair(__half *p, float2 v) {
+    const __half2 h = __float22half2_rn(v);
+    *reinterpret_cast<__half2 *>(p) = h;
+    return __half22float2(h);
+}
+__device__ __forceinline__ float2 st_pair(__nv_bfloat16 *p, float2 v) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    *reinterpret_cast<__nv_bfloat162 *>(p) = h;
+    return __bfloat1622float2(h);
+}
+
 template <int Q, int FMT>
 __device__ __forceinline__ float fr_g(const unsigned char *gb, int nx, int i, int xs) {
     using S = typename Fmt<FMT>::S;
@@ -457,24 +502,24 @@ __device__ __forceinline__ float fr_g(const unsigned char *gb, int nx, int i, in
 }
 
 template <int Q, int FMT, int KIND, bool PULL, int NST, int NPT>
-__global__ void __launch_bounds__(544, 1) k_wsrow(Launch L, int nunits) {
+__global__ void __launch_bounds__(512 / NPT + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
     using FL = FullRowLayout<Q, FMT, KIND>;
     constexpr int NS = n_stencil_rows<Q>();
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NST], empty[NST];
     __shared__ unsigned wall_s[NST];
-    __shared__ int cabort;
     const int nx = L.G.nx;
     const int ncons = nx / NPT;
     const bool producer = threadIdx.x >= ncons;
     const unsigned stage_bytes = FL::stage(nx);
+    // a stage is released by each consumer warp on its own once it has read
+    // it, so the consumer warps never wait for one another
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init_count(smem_addr(&full[s]), 1);
-            mbar_init_count(smem_addr(&empty[s]), 1);
+            mbar_init_count(smem_addr(&empty[s]), (unsigned)(ncons / 32));
         }
-        cabort = 0;
         fence_async_smem();
     }
     __syncthreads();
@@ -573,13 +618,13 @@ __global__ void __launch_bounds__(544, 1) k_wsrow(Launch L, int nunits) {
         const int s = k % NST;
         const unsigned char *cur = sm + s * stage_bytes;
         const unsigned char *gb = cur + FL::g_off(nx);
-        const bool ok = mbar_wait_hint(smem_addr(&full[s]), (unsigned)((k / NST) & 1));
+        // a warp whose wait timed out leaves; the producer then times out
+        // on the stage it never releases, and every other wait runs out too
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_hint(smem_addr(&full[s]), (unsigned)((k / NST) & 1)));
         if (!ok) {
-            atomicExch(L.err, 5);
-            cabort = 1;
+            if ((threadIdx.x & 31) == 0) atomicExch(L.err, 5);
+            break;
         }
-        consumer_sync(ncons);
-        if (cabort) break;
         const int y = unit % L.G.ny, z = unit / L.G.ny;
         const unsigned wall = wall_s[s];
         const size_t row = ((size_t)z * L.G.ny + y) * nx;
@@ -603,8 +648,8 @@ __global__ void __launch_bounds__(544, 1) k_wsrow(Launch L, int nunits) {
                 }
                 out[t] = sum;
             }
-            consumer_sync(ncons);
-            if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[s]));
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
             reinterpret_cast<float2 *>(static_cast<float *>(L.phi) + row)[threadIdx.x] = make_float2(out[0], out[1]);
         } else if constexpr (KIND == WS_MU) {
             const float *ph = reinterpret_cast<const float *>(cur);
@@ -623,129 +668,298 @@ __global__ void __launch_bounds__(544, 1) k_wsrow(Launch L, int nunits) {
                 lap *= 6.f;
                 out[t] = float(L.P.A) * (p0 * p0 * p0 - p0) - float(L.P.kappa) * lap;
             }
-            consumer_sync(ncons);
-            if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[s]));
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
             reinterpret_cast<float2 *>(static_cast<float *>(L.mu) + row)[threadIdx.x] = make_float2(out[0], out[1]);
-        } else {
-            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
-            const float kf = float(1.0 - 0.5 / L.P.tau_f);
-            const float g3 = float(3.0 * L.P.Gamma);
+        } else if constexpr (NPT == 2) {
+            // ------------------------------------------------ update, node pairs
+            constexpr bool DEV = Fmt<FMT>::DEV;
             const float *__restrict__ phif = static_cast<const float *>(L.phi);
             const float *__restrict__ muf = static_cast<const float *>(L.mu);
-            float fo[NPT][Q], go[NPT][Q];
-            const int xb = NPT == 1 ? (int)threadIdx.x : x0;
-#pragma unroll
-            for (int t = 0; t < NPT; ++t) {
-                const int x = xb + t;
-                const Site st = make_site(L.G, x, y, z);
-                float f[Q], g[Q];
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    if (PULL && (wall >> i) & 1u) {
-                        const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
-                        const float cu = float(Lat<Q>::cx(i)) * uw;
-                        const float w2 = float(2.0 * Lat<Q>::w(i) * 3.0);
-                        // slot i holds the local row of population opp(i)
-                        const S fv = reinterpret_cast<const S *>(cur)[i * nx + x];
-                        float fl;
-                        if constexpr (Fmt<FMT>::DEV) fl = to_float(fv) + float(Lat<Q>::w(i)) * rho0;
-                        else fl = fv;
-                        f[i] = fl + w2 * rho0 * cu;
-                        g[i] = fr_g<Q, FMT>(gb, nx, i, x) + w2 * php[st.n] * cu;
-                    } else {
-                        const int xs = PULL ? wrap_x(x - Lat<Q>::cx(i), nx) : x;
-                        const S fv = reinterpret_cast<const S *>(cur)[i * nx + xs];
-                        if constexpr (Fmt<FMT>::DEV) f[i] = to_float(fv) + float(Lat<Q>::w(i)) * rho0;
-                        else f[i] = fv;
-                        g[i] = fr_g<Q, FMT>(gb, nx, i, xs);
-                    }
-                }
-                float rho = 0.f, ph = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    rho += f[i];
-                    ph += g[i];
-                    if (Lat<Q>::cx(i)) jx += float(Lat<Q>::cx(i)) * f[i];
-                    if (Lat<Q>::cy(i)) jy += float(Lat<Q>::cy(i)) * f[i];
-                    if (Lat<Q>::cz(i)) jz += float(Lat<Q>::cz(i)) * f[i];
-                }
-                const float *phs = reinterpret_cast<const float *>(cur + FL::f_off(nx));
-                const float *mus = phs + FL::NA * nx;
-                float gpx = 0.f, gpy = 0.f, gpz = 0.f, gqx = 0.f, gqy = 0.f, gqz = 0.f;
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const int a = axial_slot(Lat<Q>::cy(i), Lat<Q>::cz(i));
-                    float pv, mv;
-                    if (a >= 0) {
-                        const int xn = wrap_x(x + Lat<Q>::cx(i), nx);
-                        pv = phs[a * nx + xn];
-                        mv = mus[a * nx + xn];
-                    } else {
-                        const int kn = site_nb<Q>(st, i);
-                        pv = __ldg(phif + kn);
-                        mv = __ldg(muf + kn);
-                    }
-                    const float pm = pv * mv;
-                    const float w = float(Lat<Q>::w(i));
-                    if (Lat<Q>::cx(i)) { gpx += w * float(Lat<Q>::cx(i)) * pv; gqx += w * float(Lat<Q>::cx(i)) * pm; }
-                    if (Lat<Q>::cy(i)) { gpy += w * float(Lat<Q>::cy(i)) * pv; gqy += w * float(Lat<Q>::cy(i)) * pm; }
-                    if (Lat<Q>::cz(i)) { gpz += w * float(Lat<Q>::cz(i)) * pv; gqz += w * float(Lat<Q>::cz(i)) * pm; }
-                }
-                const float mu = mus[x];
-                const float Fx = 3.f * (mu * gpx - gqx), Fy = 3.f * (mu * gpy - gqy), Fz = 3.f * (mu * gpz - gqz);
-                const float inv = 1.f / rho;
-                const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
-                const float usq = ux * ux + uy * uy + uz * uz;
-                const float uF = ux * Fx + uy * Fy + uz * Fz;
-                const float gmu3 = g3 * mu;
-                float fsum = 0.f, gsum = 0.f;
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const float cx = float(Lat<Q>::cx(i)), cy = float(Lat<Q>::cy(i)), cz = float(Lat<Q>::cz(i));
-                    const float w = float(Lat<Q>::w(i));
-                    const float cu = cx * ux + cy * uy + cz * uz;
-                    const float cF = cx * Fx + cy * Fy + cz * Fz;
-                    const float poly = 3.f * cu + 4.5f * cu * cu - 1.5f * usq;
-                    const float feq = w * rho * (1.f + poly);
-                    const float Sg = kf * w * (3.f * (cF - uF) + 9.f * cu * cF);
-                    const float fv = f[i] - (f[i] - feq) * of + Sg;
-                    const float geq = w * (gmu3 + ph * poly);
-                    const float gv = g[i] - (g[i] - geq) * og;
-                    fsum += fv;
-                    gsum += gv;
-                    fo[t][i] = fv;
-                    go[t][i] = gv;
-                }
-                fo[t][0] = rho - fsum;
-                go[t][0] = ph - gsum;
-            }
-            // the stage is free once every consumer has read it
-            consumer_sync(ncons);
-            if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[s]));
-            const size_t off = row + xb;
-            if constexpr (NPT == 1) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    Pop<Q, FMT>::stf(L.dst, np, i, off, fo[0][i], rho0);
-                    Pop<Q, FMT>::stg(L.dst, np, i, off, go[0][i]);
-                }
-            } else
+            const float *phs = reinterpret_cast<const float *>(cur + FL::f_off(nx));
+            const float *mus = phs + FL::NA * nx;
+            const S *frow = reinterpret_cast<const S *>(cur);
+            const S *grow = reinterpret_cast<const S *>(gb);
+            const float *g0row = reinterpret_cast<const float *>(gb + (size_t)(Q - 1) * nx * sizeof(S));
+            const Site st = make_site(L.G, x0, y, z);
+            // ---- read phase: pulled populations (16-bit f as deviations
+            // f_i - w_i rho0), then the stencil values of phi and mu
+            float2 f[Q], g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                S *fp = static_cast<S *>(L.dst.f) + (size_t)i * np + off;
-                if constexpr (Fmt<FMT>::DEV) {
-                    const float wr = float(Lat<Q>::w(i)) * rho0;
-                    store2<S>(fp, fo[0][i] - wr, fo[1][i] - wr);
-                    if (i == 0) {
-                        *reinterpret_cast<float2 *>(L.dst.g0 + off) = make_float2(go[0][0], go[1][0]);
+                const S *fr = frow + i * nx;
+                const bool wl = PULL && ((wall >> i) & 1u);
+                const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
+                // g row of population i in the stage (16-bit formats: g_0
+                // is the FP32 row after the 16-bit ones)
+                float2 gv;
+                if (DEV && i == 0) gv = ld_shift(g0row, x0, cx, nx);
+                else gv = ld_shift(grow + (DEV ? i - 1 : i) * nx, x0, cx, nx);
+                float2 fv = ld_shift(fr, x0, cx, nx);
+                if (wl) {
+                    // slot i holds the local row of population opp(i): add
+                    // the moving-wall term 2 w_i a (c_i . u_w) / cs^2
+                    const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
+                    const float cu = float(Lat<Q>::cx(i)) * uw;
+                    const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * cu;
+                    fv = add2(fv, p2(w2cu * rho0));
+                    gv = fma2(p2(w2cu), ld_pair(php, (int)st.n), gv);
+                }
+                f[i] = fv;
+                g[i] = gv;
+            }
+            float2 gpx = p2(0.f), gpy = p2(0.f), gpz = p2(0.f), gqx = p2(0.f), gqy = p2(0.f), gqz = p2(0.f);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (Lat<Q>::opp(i) < i) continue;
+                float2 pv[2], mv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = h ? Lat<Q>::opp(i) : i;
+                    const int a = axial_slot(Lat<Q>::cy(k), Lat<Q>::cz(k));
+                    if (a >= 0) {
+                        // stencil reads x + c, i.e. a shift by -c
+                        pv[h] = ld_shift(phs + a * nx, x0, -Lat<Q>::cx(k), nx);
+                        mv[h] = ld_shift(mus + a * nx, x0, -Lat<Q>::cx(k), nx);
                     } else {
-                        store2<S>(static_cast<S *>(L.dst.g) + (size_t)(i - 1) * np + off, go[0][i], go[1][i]);
+                        // off-axis rows (c_x = 0): an aligned pair in global memory
+                        const int kn = site_nb<Q>(st, k);
+                        pv[h] = __ldg(reinterpret_cast<const float2 *>(phif + kn));
+                        mv[h] = __ldg(reinterpret_cast<const float2 *>(muf + kn));
                     }
+                }
+                const float2 dp = sub2(pv[0], pv[1]);
+                const float2 dq = sub2(mul2(pv[0], mv[0]), mul2(pv[1], mv[1]));
+                const float w = float(Lat<Q>::w(i));
+                if (Lat<Q>::cx(i)) { gpx = fma2(p2(w * Lat<Q>::cx(i)), dp, gpx); gqx = fma2(p2(w * Lat<Q>::cx(i)), dq, gqx); }
+                if (Lat<Q>::cy(i)) { gpy = fma2(p2(w * Lat<Q>::cy(i)), dp, gpy); gqy = fma2(p2(w * Lat<Q>::cy(i)), dq, gqy); }
+                if (Lat<Q>::cz(i)) { gpz = fma2(p2(w * Lat<Q>::cz(i)), dp, gpz); gqz = fma2(p2(w * Lat<Q>::cz(i)), dq, gqz); }
+            }
+            const float2 mu = ld_pair(mus, x0);
+            // this warp is done with the stage
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
+
+            // ---- moments, force, velocity
+            float2 sf = f[0], ph = g[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                sf = add2(sf, f[i]);
+                ph = add2(ph, g[i]);
+                jx = acc_c(jx, f[i], Lat<Q>::cx(i));
+                jy = acc_c(jy, f[i], Lat<Q>::cy(i));
+                jz = acc_c(jz, f[i], Lat<Q>::cz(i));
+            }
+            const float2 rho = DEV ? add2(sf, p2(rho0)) : sf;
+            const float2 Fx = mul2(p2(3.f), sub2(mul2(mu, gpx), gqx));
+            const float2 Fy = mul2(p2(3.f), sub2(mul2(mu, gpy), gqy));
+            const float2 Fz = mul2(p2(3.f), sub2(mul2(mu, gpz), gqz));
+            const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+            const float2 ux = mul2(fma2(p2(0.5f), Fx, jx), inv);
+            const float2 uy = mul2(fma2(p2(0.5f), Fy, jy), inv);
+            const float2 uz = mul2(fma2(p2(0.5f), Fz, jz), inv);
+            const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+            const float2 uF = fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)));
+            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
+            const float2 omf = p2(1.f - of), omg = p2(1.f - og);
+            const float kf = float(1.0 - 0.5 / L.P.tau_f);
+            const float2 gmu3 = mul2(p2(float(3.0 * L.P.Gamma)), mu);
+            const float2 m15usq = mul2(p2(-1.5f), usq);
+            const float2 m3uF = mul2(p2(-3.f), uF);
+
+            // ---- collision and stores
+            const size_t off = row + x0;
+            S *fp = static_cast<S *>(L.dst.f) + off;
+            S *gp = static_cast<S *>(L.dst.g) + off;
+            {
+                const float w0 = float(Lat<Q>::w(0));
+                // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F
+                const float2 v = fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), mul2(p2(kf * w0), m3uF)));
+                st_pair(fp, v);
+            }
+            float2 gsum = p2(0.f);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (Lat<Q>::opp(i) < i) continue;
+                const int j = Lat<Q>::opp(i);
+                float2 cu = p2(0.f), cF = p2(0.f);
+                cu = acc_c(cu, ux, Lat<Q>::cx(i));
+                cu = acc_c(cu, uy, Lat<Q>::cy(i));
+                cu = acc_c(cu, uz, Lat<Q>::cz(i));
+                cF = acc_c(cF, Fx, Lat<Q>::cx(i));
+                cF = acc_c(cF, Fy, Lat<Q>::cy(i));
+                cF = acc_c(cF, Fz, Lat<Q>::cz(i));
+                const float w = float(Lat<Q>::w(i));
+                const float2 cu3 = mul2(p2(3.f), cu);
+                const float2 E = fma2(mul2(p2(1.5f), cu3), cu, m15usq);  // 4.5 cu^2 - 1.5 u^2
+                const float2 wr = p2(of * w);
+                const float2 Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), fma2(mul2(p2(3.f), cu3), cF, m3uF)));
+                const float2 Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
+                const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
+                const float2 wg = p2(og * w);
+                const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
+                const float2 Bg = mul2(mul2(wg, ph), cu3);
+                const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
+                if constexpr (DEV) {
+                    st_pair(fp + (size_t)i * np, fi);
+                    st_pair(fp + (size_t)j * np, fj);
+                    // the rest population of g closes sum_i g*_i = phi on
+                    // the values as they are stored
+                    gsum = add2(gsum, add2(st_pair(gp + (size_t)(i - 1) * np, gi),
+                                           st_pair(gp + (size_t)(j - 1) * np, gj)));
                 } else {
-                    store2<S>(fp, fo[0][i], fo[1][i]);
-                    store2<S>(static_cast<S *>(L.dst.g) + (size_t)i * np + off, go[0][i], go[1][i]);
+                    st_pair(fp + (size_t)i * np, fi);
+                    st_pair(fp + (size_t)j * np, fj);
+                    st_pair(gp + (size_t)i * np, gi);
+                    st_pair(gp + (size_t)j * np, gj);
+                    gsum = add2(gsum, add2(gi, gj));
                 }
             }
+            if constexpr (DEV) st_pair(L.dst.g0 + off, sub2(ph, gsum));
+            else st_pair(gp, sub2(ph, gsum));
+        } else {
+            static_assert(NPT == 1, "the update runs one or two nodes per consumer thread");
+            constexpr bool DEV = Fmt<FMT>::DEV;
+            const float *__restrict__ phif = static_cast<const float *>(L.phi);
+            const float *__restrict__ muf = static_cast<const float *>(L.mu);
+            const float *phs = reinterpret_cast<const float *>(cur + FL::f_off(nx));
+            const float *mus = phs + FL::NA * nx;
+            const int x = threadIdx.x;
+            const Site st = make_site(L.G, x, y, z);
+            // ---- read phase: everything this node needs from the stage
+            // pulled populations; the 16-bit formats keep f as deviations
+            // f_i - w_i rho0 all the way through the collision
+            float f[Q], g[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (PULL && (wall >> i) & 1u) {
+                    const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
+                    const float cu = float(Lat<Q>::cx(i)) * uw;
+                    const float w2 = float(2.0 * Lat<Q>::w(i) * 3.0);
+                    // slot i holds the local row of population opp(i)
+                    const S fv = reinterpret_cast<const S *>(cur)[i * nx + x];
+                    float fl;
+                    if constexpr (DEV) fl = to_float(fv);
+                    else fl = fv;
+                    f[i] = fl + w2 * rho0 * cu;
+                    g[i] = fr_g<Q, FMT>(gb, nx, i, x) + w2 * php[st.n] * cu;
+                } else {
+                    const int xs = PULL ? wrap_x(x - Lat<Q>::cx(i), nx) : x;
+                    const S fv = reinterpret_cast<const S *>(cur)[i * nx + xs];
+                    if constexpr (DEV) f[i] = to_float(fv);
+                    else f[i] = fv;
+                    g[i] = fr_g<Q, FMT>(gb, nx, i, xs);
+                }
+            }
+            // isotropic gradients of phi and phi mu over opposite pairs:
+            // sum_i w_i c_i a(x + c_i) = sum_pairs w_i c_i (a(x + c_i) - a(x - c_i))
+            float gpx = 0.f, gpy = 0.f, gpz = 0.f, gqx = 0.f, gqy = 0.f, gqz = 0.f;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (Lat<Q>::opp(i) < i) continue;
+                float pv[2], mv[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = h ? Lat<Q>::opp(i) : i;
+                    const int a = axial_slot(Lat<Q>::cy(k), Lat<Q>::cz(k));
+                    if (a >= 0) {
+                        const int xn = wrap_x(x + Lat<Q>::cx(k), nx);
+                        pv[h] = phs[a * nx + xn];
+                        mv[h] = mus[a * nx + xn];
+                    } else {
+                        const int kn = site_nb<Q>(st, k);
+                        pv[h] = __ldg(phif + kn);
+                        mv[h] = __ldg(muf + kn);
+                    }
+                }
+                const float dp = pv[0] - pv[1];
+                const float dq = pv[0] * mv[0] - pv[1] * mv[1];
+                const float w = float(Lat<Q>::w(i));
+                if (Lat<Q>::cx(i)) { gpx += w * float(Lat<Q>::cx(i)) * dp; gqx += w * float(Lat<Q>::cx(i)) * dq; }
+                if (Lat<Q>::cy(i)) { gpy += w * float(Lat<Q>::cy(i)) * dp; gqy += w * float(Lat<Q>::cy(i)) * dq; }
+                if (Lat<Q>::cz(i)) { gpz += w * float(Lat<Q>::cz(i)) * dp; gqz += w * float(Lat<Q>::cz(i)) * dq; }
+            }
+            const float mu = mus[x];
+            // this warp is done with the stage; the collision and the stores
+            // below run while the producer refills it
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
+
+            // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
+            float sf = 0.f, ph = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                sf += f[i];
+                ph += g[i];
+                if (Lat<Q>::cx(i)) jx += float(Lat<Q>::cx(i)) * f[i];
+                if (Lat<Q>::cy(i)) jy += float(Lat<Q>::cy(i)) * f[i];
+                if (Lat<Q>::cz(i)) jz += float(Lat<Q>::cz(i)) * f[i];
+            }
+            // sf is rho, or rho - rho0 for deviations: in both cases the
+            // density term of omega (f_eq_i - w_i rho0 [deviations])
+            const float rho = DEV ? sf + rho0 : sf;
+            const float Fx = 3.f * (mu * gpx - gqx), Fy = 3.f * (mu * gpy - gqy), Fz = 3.f * (mu * gpz - gqz);
+            const float inv = 1.f / rho;
+            const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
+            const float usq = ux * ux + uy * uy + uz * uz;
+            const float uF = ux * Fx + uy * Fy + uz * Fz;
+            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
+            const float omf = 1.f - of, omg = 1.f - og;
+            const float kf = float(1.0 - 0.5 / L.P.tau_f);
+            const float gmu3 = float(3.0 * L.P.Gamma) * mu;
+
+            // ---- collision (Eq. bgk, feq, Fi, LBEg, geq) and stores
+            const size_t off = row + x;
+            S *fp = static_cast<S *>(L.dst.f) + off;
+            // rest population of f: (1 - omega) f_0 + omega f_eq_0 + S_0
+            {
+                const float w0 = float(Lat<Q>::w(0));
+                const float v = fmaf(omf, f[0], of * w0 * (sf - 1.5f * rho * usq) - 3.f * kf * w0 * uF);
+                if constexpr (DEV) fp[0] = from_float<S>(v);
+                else fp[0] = v;
+            }
+            // moving populations in opposite pairs (i, opp(i)): the
+            // equilibria and the Guo term split into parts even and odd in
+            // c_i that the pair shares
+            float gsum = 0.f;
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (Lat<Q>::opp(i) < i) continue;
+                const int j = Lat<Q>::opp(i);
+                const float cx = float(Lat<Q>::cx(i)), cy = float(Lat<Q>::cy(i)), cz = float(Lat<Q>::cz(i));
+                const float w = float(Lat<Q>::w(i));
+                const float cu = cx * ux + cy * uy + cz * uz;
+                const float cF = cx * Fx + cy * Fy + cz * Fz;
+                const float E = fmaf(4.5f * cu, cu, -1.5f * usq);
+                const float wr = of * w;
+                const float Af = fmaf(wr, fmaf(rho, E, sf), kf * w * fmaf(9.f * cu, cF, -3.f * uF));
+                const float Bf = fmaf(wr * rho, 3.f * cu, 3.f * kf * w * cF);
+                const float fi = fmaf(omf, f[i], Af + Bf), fj = fmaf(omf, f[j], Af - Bf);
+                const float wg = og * w;
+                const float Ag = wg * fmaf(ph, E, gmu3);
+                const float Bg = wg * ph * 3.f * cu;
+                const float gi = fmaf(omg, g[i], Ag + Bg), gj = fmaf(omg, g[j], Ag - Bg);
+                if constexpr (DEV) {
+                    fp[(size_t)i * np] = from_float<S>(fi);
+                    fp[(size_t)j * np] = from_float<S>(fj);
+                    const S hi = from_float<S>(gi), hj = from_float<S>(gj);
+                    S *gp = static_cast<S *>(L.dst.g) + off;
+                    gp[(size_t)(i - 1) * np] = hi;
+                    gp[(size_t)(j - 1) * np] = hj;
+                    // the rest population of g closes sum_i g*_i = phi on
+                    // the values as they are stored
+                    gsum += to_float(hi) + to_float(hj);
+                } else {
+                    fp[(size_t)i * np] = fi;
+                    fp[(size_t)j * np] = fj;
+                    S *gp = static_cast<S *>(L.dst.g) + off;
+                    gp[(size_t)i * np] = gi;
+                    gp[(size_t)j * np] = gj;
+                    gsum += gi + gj;
+                }
+            }
+            if constexpr (DEV) L.dst.g0[off] = ph - gsum;
+            else static_cast<S *>(L.dst.g)[off] = ph - gsum;
         }
     }
 }
@@ -772,9 +986,9 @@ struct WsRowLaunchers {
     }
     template <int KIND, bool PULL, int NST>
     static void launch(const Launch &L) {
-        // the update keeps one node per consumer thread (more warps in
-        // flight); the phi and mu passes take adjacent node pairs
-        constexpr int NPT = KIND == WS_UPDATE ? 1 : 2;
+        // every pass takes adjacent node pairs per consumer thread (the
+        // update computes them with packed FP32 pair arithmetic)
+        constexpr int NPT = 2;
         const int nx = L.G.nx;
         const int nu = L.G.ny * L.G.nz;
         const size_t smem = (size_t)NST * FullRowLayout<Q, FMT, KIND>::stage(nx);

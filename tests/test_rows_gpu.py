@@ -20,8 +20,10 @@ def fre():
     return fre
 
 
-def errs(a, b):
-    uscale = max(np.abs(b[k]).max() for k in ("ux", "uy", "uz"))
+def errs(a, b, u_floor=0.0):
+    """Relative L-inf per field; u relative to max |u| of b or u_floor,
+    whichever is larger (a resting droplet has only small spurious currents)."""
+    uscale = max(max(np.abs(b[k]).max() for k in ("ux", "uy", "uz")), u_floor)
     out = {}
     for k in ("rho", "ux", "uy", "uz", "phi"):
         scale = uscale if k.startswith("u") else np.abs(b[k]).max()
@@ -47,19 +49,32 @@ def make(fre, lattice, device, nx, ny, nz, precision, flags=0, **kw):
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}")
 @pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
-def test_row_kernels_match_per_node_kernels(fre, case, precision):
+def test_row_kernels_match_per_node_kernels(fre, orc, case, precision):
+    """The row kernels and the per-node kernels compute the same update,
+    arranged differently (the row kernels split the collision into parts
+    even and odd in c_i and keep 16-bit f as deviations), so their rounding
+    differs.  Both are held to the FP64 oracle after 200 steps: FP32 1e-5 on
+    rho and phi and 3e-5 on u against max(|u|, 0.01) (the FP32 bound of the
+    100x50 case), FP16 3e-3, BF16 2e-2 (the 16-bit bounds of the D3Q19
+    test below)."""
     lattice, device, nx, ny, nz, kw = case
     rows = make(fre, lattice, device, nx, ny, nz, precision, **kw)
     gen = make(fre, lattice, device, nx, ny, nz, precision, flags=1, **kw)
     assert rows.row_kernels and not gen.row_kernels
+    a = dict(tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0, rho0=1.0)
+    a.update(kw)
+    o = orc.Oracle({"d2q9": 0, "d3q19": 1}[lattice], {"shear": 0, "periodic": 2}[device], nx, ny, nz,
+                   a["tau_f"], a["tau_g"], a["A"], a["kappa"], a["gamma_mob"], a["u_wall"], a["rho0"])
     c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, min(nx, ny) / 4)
-    for s in (rows, gen):
+    for s in (rows, gen, o):
         s.init_droplet(*c)
         s.step(200)
-    e = errs(rows.fields(), gen.fields())
-    # same arithmetic in both; only the contraction/rounding order may differ
-    tol = 1e-5 if precision == "fp32" else 2e-3
-    assert max(e.values()) < tol, e
+    ref = o.fields()
+    tol = {"fp32": 1e-5, "fp16dev": 3e-3, "bf16dev": 2e-2}[precision]
+    utol = 3e-5 if precision == "fp32" else tol
+    res = {name: errs(sim.fields(), ref, u_floor=0.01) for name, sim in (("rows", rows), ("per-node", gen))}
+    for name, e in res.items():
+        assert all(v < (utol if k.startswith("u") else tol) for k, v in e.items()), (name, res)
     rows.close()
     gen.close()
 
