@@ -22,6 +22,10 @@ namespace fre {
 __device__ __forceinline__ void mbar_init_count(unsigned bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
+// expect `bytes` more transaction bytes in the current phase, without arriving
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -407,39 +411,62 @@ namespace fre {
 //                   values come from global memory (re-read by the nine
 //                   neighbouring rows, they stay in L2)
 
-// Axial stencil slots (cy, cz) with cy == 0 or cz == 0: the only ones whose
-// directions carry an x shift.  D3Q19: (0,0) (1,0) (-1,0) (0,1) (0,-1);
-// D2Q9: (0,0) (1,0) (-1,0).
-template <int Q>
-__host__ __device__ constexpr int n_axial() { return Lat<Q>::D == 2 ? 3 : 5; }
-__host__ __device__ constexpr int axial_slot(int cy, int cz) {
-    return (cy == 0 && cz == 0) ? 0 : (cz == 0 ? (cy > 0 ? 1 : 2) : (cy == 0 ? (cz > 0 ? 3 : 4) : -1));
-}
-__host__ __device__ constexpr int axial_cy(int a) { return a == 1 ? 1 : (a == 2 ? -1 : 0); }
-__host__ __device__ constexpr int axial_cz(int a) { return a == 3 ? 1 : (a == 4 ? -1 : 0); }
-
-template <int Q, int FMT, int KIND>
-struct FullRowLayout {
+// Work unit of the full-row kernels: R consecutive rows y0 .. y0 + R - 1 of
+// one z plane (R = 2 where a row is shorter than 2 KB, so that every bulk
+// copy moves at least 2 KB: the copy engine's rate of operations, not HBM,
+// bounds short copies).  The R rows of a population are contiguous in
+// memory and staged by one copy unless the pull offset wraps or meets a
+// wall; the phi / mu stencil rows of one z plane are one copy of R + 2 rows
+// (y0 - 1 .. y0 + R) unless they wrap or are clamped at a wall.
+template <int Q, int FMT, int KIND, int R>
+struct RowsLayout {
     using S = typename Fmt<FMT>::S;
     static constexpr bool DEV = Fmt<FMT>::DEV;
-    static constexpr int NS = n_stencil_rows<Q>();
-    static constexpr int NA = n_axial<Q>();
+    static constexpr int D = Lat<Q>::D;
+    // field rows: update -- phi and mu each: the cz = 0 group (R + 2 rows,
+    // cy = -1 .. R) and in 3D the cz = +1 and cz = -1 groups (R rows, cy = 0);
+    // mu pass -- phi: one group of R + 2 rows per cz in -1, 0, +1 (3D) or cz = 0
+    static constexpr int NGRP = KIND == WS_UPDATE ? (D == 3 ? 3 : 1) : (KIND == WS_MU ? (D == 3 ? 3 : 1) : 0);
+    static constexpr int NFIELD = KIND == WS_UPDATE ? (R + 2) + (D == 3 ? 2 * R : 0)
+                                                    : (KIND == WS_MU ? NGRP * (R + 2) : 0);
     __host__ __device__ static unsigned rowb(int nx) { return (unsigned)(nx * sizeof(S)); }
-    // start of the g rows
-    __host__ __device__ static unsigned g_off(int nx) { return KIND == WS_UPDATE ? Q * rowb(nx) : 0u; }
-    __host__ __device__ static unsigned g_bytes(int nx) {
-        return DEV ? (Q - 1) * rowb(nx) + (unsigned)nx * 4 : Q * rowb(nx);
+    __host__ __device__ static unsigned fldb(int nx) { return (unsigned)(nx * 4); }
+    // population rows: f slot i row r, then g
+    __host__ __device__ static unsigned f_row(int nx, int i, int r) { return (unsigned)(i * R + r) * rowb(nx); }
+    __host__ __device__ static unsigned g_off(int nx) { return KIND == WS_UPDATE ? Q * R * rowb(nx) : 0u; }
+    __host__ __device__ static unsigned g_row(int nx, int i, int r) {
+        if (DEV && i == 0) return g_off(nx) + (Q - 1) * R * rowb(nx) + (unsigned)r * fldb(nx);
+        return g_off(nx) + (unsigned)((DEV ? i - 1 : i) * R + r) * rowb(nx);
     }
-    // update: axial phi rows then axial mu rows after the populations
-    __host__ __device__ static unsigned f_off(int nx) { return (g_off(nx) + g_bytes(nx) + 15u) / 16u * 16u; }
+    __host__ __device__ static unsigned g_bytes(int nx) {
+        return DEV ? (Q - 1) * R * rowb(nx) + R * fldb(nx) : Q * R * rowb(nx);
+    }
+    __host__ __device__ static unsigned fld_off(int nx) {
+        return KIND == WS_UPDATE ? (g_off(nx) + g_bytes(nx) + 15u) / 16u * 16u : 0u;
+    }
+    // field row k of field `fld` (0 phi, 1 mu; the mu pass stages phi only)
+    __host__ __device__ static unsigned fld_row(int nx, int fld, int k) {
+        return fld_off(nx) + (unsigned)(fld * NFIELD + k) * fldb(nx);
+    }
+    // index k of the field row at (y0 + r + cy, z + cz)
+    __host__ __device__ static constexpr int fk(int cy, int cz, int r) {
+        return KIND == WS_MU ? (D == 3 ? (cz + 1) * (R + 2) : 0) + r + cy + 1
+                             : (cz == 0 ? r + cy + 1 : (R + 2) + (cz > 0 ? 0 : R) + r);
+    }
+    // bytes that arrive per stage, and the stage extent
+    __host__ __device__ static unsigned tx_bytes(int nx) {
+        if (KIND == WS_MU) return NFIELD * fldb(nx);
+        if (KIND == WS_UPDATE) return Q * R * rowb(nx) + g_bytes(nx) + 2 * NFIELD * fldb(nx);
+        return g_bytes(nx);
+    }
     __host__ __device__ static unsigned bytes(int nx) {
-        if (KIND == WS_MU) return NS * (unsigned)nx * 4;
-        if (KIND == WS_UPDATE) return f_off(nx) + 2 * NA * (unsigned)nx * 4;
-        return g_off(nx) + g_bytes(nx);
+        if (KIND == WS_UPDATE) return fld_off(nx) + 2 * NFIELD * fldb(nx);
+        return tx_bytes(nx);
     }
     __host__ __device__ static unsigned stage(int nx) { return (bytes(nx) + 127u) / 128u * 128u; }
-    __host__ __device__ static int nrows() {
-        return KIND == WS_UPDATE ? 2 * Q + 2 * NA : (KIND == WS_PHI ? Q : NS);
+    // copy groups issued by the producer lanes
+    __host__ __device__ static constexpr int ngroups() {
+        return KIND == WS_UPDATE ? 2 * Q + 2 * NGRP : (KIND == WS_PHI ? Q : NGRP);
     }
 };
 
@@ -501,18 +528,32 @@ __device__ __forceinline__ float fr_g(const unsigned char *gb, int nx, int i, in
     }
 }
 
-template <int Q, int FMT, int KIND, bool PULL, int NST, int NPT>
-__global__ void __launch_bounds__(512 / NPT + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
+// populations whose c_y has the sign of sy, as a bit mask
+template <int Q>
+__host__ __device__ constexpr unsigned cy_mask(int sy) {
+    unsigned m = 0;
+    for (int i = 0; i < Q; ++i)
+        if (Lat<Q>::cy(i) * sy > 0) m |= 1u << i;
+    return m;
+}
+
+// NXC: the row length as a compile-time constant (every shared-memory
+// offset then folds into the instruction), or 0 to take it from the launch.
+template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC>
+__global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
-    using FL = FullRowLayout<Q, FMT, KIND>;
-    constexpr int NS = n_stencil_rows<Q>();
+    using FL = RowsLayout<Q, FMT, KIND, R>;
+    constexpr bool DEV = Fmt<FMT>::DEV;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NST], empty[NST];
-    __shared__ unsigned wall_s[NST];
-    const int nx = L.G.nx;
-    const int ncons = nx / NPT;
+    __shared__ unsigned wall_s[NST][R];
+    const int nx = NXC ? NXC : L.G.nx;
+    const int ny = L.G.ny, nz = L.G.nz;
+    const int nyu = ny / R;  // units per z plane
+    const int ncons = nx / 2;  // consumer thread t updates x = 2t, 2t + 1
     const bool producer = threadIdx.x >= ncons;
     const unsigned stage_bytes = FL::stage(nx);
+    const bool shear = L.G.device == FRE_SHEAR;
     // a stage is released by each consumer warp on its own once it has read
     // it, so the consumer warps never wait for one another
     if (threadIdx.x == 0) {
@@ -535,76 +576,86 @@ __global__ void __launch_bounds__(512 / NPT + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) {
                     if (lane == 0) atomicExch(L.err, 4);
-                    break;  // consumers then time out on `full` and leave together
+                    break;  // the consumers then time out on `full` and leave
                 }
             }
-            const int y = unit % L.G.ny, z = unit / L.G.ny;
+            const int y0 = (unit % nyu) * R, z = unit / nyu;
             unsigned char *buf = sm + s * stage_bytes;
             const unsigned bar = smem_addr(&full[s]);
-            unsigned wall = 0;
-            const char *src[2];
-            unsigned dst[2], nb[2];
-            int cnt = 0;
-            for (int r = lane; r < FL::nrows(); r += 32, ++cnt) {
-                if (KIND == WS_UPDATE && r >= 2 * Q) {
-                    const int j = r - 2 * Q, fld = j / FL::NA, a = j - fld * FL::NA;
-                    int yn = y + axial_cy(a);
-                    yn = (L.G.device == FRE_SHEAR) ? (yn < 0 ? 0 : (yn >= L.G.ny ? L.G.ny - 1 : yn))
-                                                   : wrapi(yn, L.G.ny);
-                    const int zn = wrapi(z + axial_cz(a), L.G.nz);
-                    const float *base = static_cast<const float *>(fld ? L.mu : L.phi);
-                    src[cnt] = reinterpret_cast<const char *>(base + ((size_t)zn * L.G.ny + yn) * nx);
-                    dst[cnt] = FL::f_off(nx) + (unsigned)(j * nx * 4);
-                    nb[cnt] = (unsigned)(nx * 4);
-                    continue;
-                }
-                if (KIND == WS_MU) {
-                    const int cy = (Lat<Q>::D == 2 ? r : r % 3) - 1, cz = Lat<Q>::D == 2 ? 0 : r / 3 - 1;
-                    int yn = y + cy;
-                    yn = (L.G.device == FRE_SHEAR) ? (yn < 0 ? 0 : (yn >= L.G.ny ? L.G.ny - 1 : yn))
-                                                   : wrapi(yn, L.G.ny);
-                    const int zn = wrapi(z + cz, L.G.nz);
-                    src[cnt] = reinterpret_cast<const char *>(static_cast<const float *>(L.phi) +
-                                                              ((size_t)zn * L.G.ny + yn) * nx);
-                    dst[cnt] = (unsigned)(r * nx * 4);
-                    nb[cnt] = (unsigned)(nx * 4);
-                    continue;
-                }
-                const int lat = (KIND == WS_PHI) ? 1 : (r >= Q);
-                const int i = (KIND == WS_PHI) ? r : r - lat * Q;
-                int ys, zs, pi = i;
-                if (!src_row<Q>(L.G, y, z, i, PULL, ys, zs)) {
-                    wall |= 1u << i;
-                    ys = y;
-                    zs = z;
-                    pi = Lat<Q>::opp(i);
-                }
-                const size_t row = ((size_t)zs * L.G.ny + ys) * nx;
-                if (!lat) {
-                    src[cnt] = static_cast<const char *>(L.src.f) + ((size_t)pi * L.G.np + row) * sizeof(S);
-                    dst[cnt] = i * FL::rowb(nx);
-                    nb[cnt] = FL::rowb(nx);
-                } else if (!Fmt<FMT>::DEV) {
-                    src[cnt] = static_cast<const char *>(L.src.g) + ((size_t)pi * L.G.np + row) * sizeof(S);
-                    dst[cnt] = FL::g_off(nx) + i * FL::rowb(nx);
-                    nb[cnt] = FL::rowb(nx);
-                } else if (pi == 0) {  // only for i = 0 (opp(i) = 0 iff i = 0)
-                    src[cnt] = reinterpret_cast<const char *>(L.src.g0 + row);
-                    dst[cnt] = FL::g_off(nx) + (Q - 1) * FL::rowb(nx);
-                    nb[cnt] = (unsigned)(nx * 4);
-                } else {
-                    src[cnt] = static_cast<const char *>(L.src.g) + ((size_t)(pi - 1) * L.G.np + row) * sizeof(S);
-                    dst[cnt] = FL::g_off(nx) + (i - 1) * FL::rowb(nx);
-                    nb[cnt] = FL::rowb(nx);
-                }
-            }
-            wall = __reduce_or_sync(0xffffffffu, wall);
+            // wall links of each row of the unit (bit i: population i pulls
+            // from beyond a shear wall: c_y > 0 on row 0, c_y < 0 on row ny - 1),
+            // published before the arrival that completes with the copies
             if (lane == 0) {
-                wall_s[s] = wall;
-                mbar_expect(bar, FL::bytes(nx));
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    wall_s[s][r] = (PULL && shear) ? ((y0 + r == 0 ? cy_mask<Q>(1) : 0u) |
+                                                      (y0 + r == ny - 1 ? cy_mask<Q>(-1) : 0u))
+                                                   : 0u;
+                mbar_expect(bar, FL::tx_bytes(nx));
             }
             __syncwarp();
-            for (int c = 0; c < cnt; ++c) bulk_load(buf + dst[c], src[c], nb[c], bar);
+            for (int gi = lane; gi < FL::ngroups(); gi += 32) {
+                if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q)) {
+                    // ---- phi / mu stencil rows of one z plane
+                    const int j = KIND == WS_MU ? gi : gi - 2 * Q;
+                    const int fld = KIND == WS_MU ? 0 : j / (FL::NGRP > 0 ? FL::NGRP : 1);
+                    const int grp = KIND == WS_MU ? j : j - fld * FL::NGRP;
+                    // mu pass groups: cz = -1, 0, +1 (3D); update: cz = 0, +1, -1
+                    const int cz = KIND == WS_MU ? (Lat<Q>::D == 3 ? grp - 1 : 0) : (grp == 0 ? 0 : (grp == 1 ? 1 : -1));
+                    const bool full_y = KIND == WS_MU || cz == 0;  // R + 2 rows with y shifts
+                    const int zn = wrapi(z + cz, nz);
+                    const float *base = static_cast<const float *>(fld ? L.mu : L.phi) + (size_t)zn * ny * nx;
+                    const int k0 = FL::fk(full_y ? -1 : 0, cz, 0);
+                    unsigned char *dst = buf + FL::fld_row(nx, fld, k0);
+                    if (!full_y) {
+                        bulk_load(dst, base + (size_t)y0 * nx, (unsigned)R * FL::fldb(nx), bar);
+                    } else if (y0 >= 1 && y0 + R <= ny - 1) {
+                        bulk_load(dst, base + (size_t)(y0 - 1) * nx, (unsigned)(R + 2) * FL::fldb(nx), bar);
+                    } else {
+                        for (int q = 0; q < R + 2; ++q) {
+                            int yn = y0 - 1 + q;
+                            yn = shear ? (yn < 0 ? 0 : (yn >= ny ? ny - 1 : yn)) : wrapi(yn, ny);
+                            bulk_load(dst + q * FL::fldb(nx), base + (size_t)yn * nx, FL::fldb(nx), bar);
+                        }
+                    }
+                    continue;
+                }
+                // ---- population rows: lattice lat (0 f, 1 g), direction i
+                const int lat = KIND == WS_PHI ? 1 : (gi >= Q);
+                const int i = KIND == WS_PHI ? gi : gi - lat * Q;
+                const int cy = PULL ? Lat<Q>::cy(i) : 0, cz = PULL ? Lat<Q>::cz(i) : 0;
+                const int zs = wrapi(z - cz, nz);
+                // source plane of population p, its element size, smem row r
+                auto plane = [&](int p) -> const char * {
+                    if (!lat) return static_cast<const char *>(L.src.f) + (size_t)p * L.G.np * sizeof(S);
+                    if (DEV && p == 0) return reinterpret_cast<const char *>(L.src.g0);
+                    return static_cast<const char *>(L.src.g) + (size_t)(DEV ? p - 1 : p) * L.G.np * sizeof(S);
+                };
+                const unsigned esz = (lat && DEV && i == 0) ? 4u : (unsigned)sizeof(S);
+                const unsigned rb = (unsigned)nx * esz;
+                auto smrow = [&](int r) -> unsigned { return lat ? FL::g_row(nx, i, r) : FL::f_row(nx, i, r); };
+                const int ys0 = y0 - cy;
+                const bool inside = ys0 >= 0 && ys0 + R - 1 <= ny - 1;
+                if (inside) {
+                    bulk_load(buf + smrow(0), plane(i) + ((size_t)zs * ny + ys0) * nx * esz, (unsigned)R * rb, bar);
+                } else {
+                    for (int r = 0; r < R; ++r) {
+                        int ys = y0 + r - cy;
+                        int pi = i, zr = zs;
+                        if (ys < 0 || ys >= ny) {
+                            if (shear) {
+                                // wall link: the local row of the opposite population
+                                ys = y0 + r;
+                                zr = z;
+                                pi = Lat<Q>::opp(i);
+                            } else {
+                                ys = wrapi(ys, ny);
+                            }
+                        }
+                        bulk_load(buf + smrow(r), plane(pi) + ((size_t)zr * ny + ys) * nx * esz, rb, bar);
+                    }
+                }
+            }
         }
         return;
     }
@@ -613,11 +664,11 @@ __global__ void __launch_bounds__(512 / NPT + 32, KIND == WS_UPDATE ? 1 : 2) k_w
     const float rho0 = float(L.P.rho0);
     const float *__restrict__ php = static_cast<const float *>(L.phi_prev);
     const long long np = L.G.np;
+    const int x0 = 2 * threadIdx.x;
     int k = 0;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
         const int s = k % NST;
         const unsigned char *cur = sm + s * stage_bytes;
-        const unsigned char *gb = cur + FL::g_off(nx);
         // a warp whose wait timed out leaves; the producer then times out
         // on the stage it never releases, and every other wait runs out too
         const bool ok = __all_sync(0xffffffffu, mbar_wait_hint(smem_addr(&full[s]), (unsigned)((k / NST) & 1)));
@@ -625,341 +676,207 @@ __global__ void __launch_bounds__(512 / NPT + 32, KIND == WS_UPDATE ? 1 : 2) k_w
             if ((threadIdx.x & 31) == 0) atomicExch(L.err, 5);
             break;
         }
-        const int y = unit % L.G.ny, z = unit / L.G.ny;
-        const unsigned wall = wall_s[s];
-        const size_t row = ((size_t)z * L.G.ny + y) * nx;
-        const int x0 = 2 * threadIdx.x;
+        const int y0 = (unit % nyu) * R, z = unit / nyu;
 
         if constexpr (KIND == WS_PHI) {
-            float out[2];
+            float2 out[R];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int x = x0 + t;
-                float sum = 0.f;
+            for (int r = 0; r < R; ++r) {
+                const unsigned wall = wall_s[s][r];
+                const size_t row = ((size_t)z * ny + y0 + r) * nx;
+                float2 sum = p2(0.f);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    if (PULL && (wall >> i) & 1u) {
+                    const bool wl = PULL && ((wall >> i) & 1u);
+                    const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
+                    float2 gv;
+                    if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
+                    else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
+                    if (wl) {
                         const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
-                        sum += fr_g<Q, FMT>(gb, nx, i, x) +
-                               float(2.0 * Lat<Q>::w(i) * 3.0) * php[row + x] * float(Lat<Q>::cx(i)) * uw;
-                    } else {
-                        sum += fr_g<Q, FMT>(gb, nx, i, PULL ? wrap_x(x - Lat<Q>::cx(i), nx) : x);
+                        const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
+                        gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
                     }
+                    sum = add2(sum, gv);
                 }
-                out[t] = sum;
+                out[r] = sum;
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-            reinterpret_cast<float2 *>(static_cast<float *>(L.phi) + row)[threadIdx.x] = make_float2(out[0], out[1]);
-        } else if constexpr (KIND == WS_MU) {
-            const float *ph = reinterpret_cast<const float *>(cur);
-            constexpr int c0 = stencil_slot<Q>(0, 0);
-            float out[2];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int x = x0 + t;
-                const float p0 = ph[c0 * nx + x];
-                float lap = 0.f;
+            for (int r = 0; r < R; ++r)
+                st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
+        } else if constexpr (KIND == WS_MU) {
+            float2 out[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float *c0 = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(0, 0, r)));
+                const float2 p0 = ld_pair(c0, x0);
+                float2 lap = p2(0.f);
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
-                    const int slot = stencil_slot<Q>(Lat<Q>::cy(i), Lat<Q>::cz(i));
-                    lap += float(Lat<Q>::w(i)) * (ph[slot * nx + wrap_x(x + Lat<Q>::cx(i), nx)] - p0);
+                    const float *rw = reinterpret_cast<const float *>(
+                        cur + FL::fld_row(nx, 0, FL::fk(Lat<Q>::cy(i), Lat<Q>::cz(i), r)));
+                    // stencil reads x + c, i.e. a shift by -c
+                    lap = fma2(p2(float(Lat<Q>::w(i))), sub2(ld_shift(rw, x0, -Lat<Q>::cx(i), nx), p0), lap);
                 }
-                lap *= 6.f;
-                out[t] = float(L.P.A) * (p0 * p0 * p0 - p0) - float(L.P.kappa) * lap;
+                lap = mul2(p2(6.f), lap);
+                // A (phi^3 - phi) - kappa lap
+                out[r] = sub2(mul2(p2(float(L.P.A)), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
+                              mul2(p2(float(L.P.kappa)), lap));
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-            reinterpret_cast<float2 *>(static_cast<float *>(L.mu) + row)[threadIdx.x] = make_float2(out[0], out[1]);
-        } else if constexpr (NPT == 2) {
-            // ------------------------------------------------ update, node pairs
-            constexpr bool DEV = Fmt<FMT>::DEV;
-            const float *__restrict__ phif = static_cast<const float *>(L.phi);
-            const float *__restrict__ muf = static_cast<const float *>(L.mu);
-            const float *phs = reinterpret_cast<const float *>(cur + FL::f_off(nx));
-            const float *mus = phs + FL::NA * nx;
-            const S *frow = reinterpret_cast<const S *>(cur);
-            const S *grow = reinterpret_cast<const S *>(gb);
-            const float *g0row = reinterpret_cast<const float *>(gb + (size_t)(Q - 1) * nx * sizeof(S));
-            const Site st = make_site(L.G, x0, y, z);
-            // ---- read phase: pulled populations (16-bit f as deviations
-            // f_i - w_i rho0), then the stencil values of phi and mu
-            float2 f[Q], g[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const S *fr = frow + i * nx;
-                const bool wl = PULL && ((wall >> i) & 1u);
-                const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
-                // g row of population i in the stage (16-bit formats: g_0
-                // is the FP32 row after the 16-bit ones)
-                float2 gv;
-                if (DEV && i == 0) gv = ld_shift(g0row, x0, cx, nx);
-                else gv = ld_shift(grow + (DEV ? i - 1 : i) * nx, x0, cx, nx);
-                float2 fv = ld_shift(fr, x0, cx, nx);
-                if (wl) {
-                    // slot i holds the local row of population opp(i): add
-                    // the moving-wall term 2 w_i a (c_i . u_w) / cs^2
-                    const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
-                    const float cu = float(Lat<Q>::cx(i)) * uw;
-                    const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * cu;
-                    fv = add2(fv, p2(w2cu * rho0));
-                    gv = fma2(p2(w2cu), ld_pair(php, (int)st.n), gv);
-                }
-                f[i] = fv;
-                g[i] = gv;
-            }
-            float2 gpx = p2(0.f), gpy = p2(0.f), gpz = p2(0.f), gqx = p2(0.f), gqy = p2(0.f), gqz = p2(0.f);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                if (Lat<Q>::opp(i) < i) continue;
-                float2 pv[2], mv[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = h ? Lat<Q>::opp(i) : i;
-                    const int a = axial_slot(Lat<Q>::cy(k), Lat<Q>::cz(k));
-                    if (a >= 0) {
-                        // stencil reads x + c, i.e. a shift by -c
-                        pv[h] = ld_shift(phs + a * nx, x0, -Lat<Q>::cx(k), nx);
-                        mv[h] = ld_shift(mus + a * nx, x0, -Lat<Q>::cx(k), nx);
-                    } else {
-                        // off-axis rows (c_x = 0): an aligned pair in global memory
-                        const int kn = site_nb<Q>(st, k);
-                        pv[h] = __ldg(reinterpret_cast<const float2 *>(phif + kn));
-                        mv[h] = __ldg(reinterpret_cast<const float2 *>(muf + kn));
-                    }
-                }
-                const float2 dp = sub2(pv[0], pv[1]);
-                const float2 dq = sub2(mul2(pv[0], mv[0]), mul2(pv[1], mv[1]));
-                const float w = float(Lat<Q>::w(i));
-                if (Lat<Q>::cx(i)) { gpx = fma2(p2(w * Lat<Q>::cx(i)), dp, gpx); gqx = fma2(p2(w * Lat<Q>::cx(i)), dq, gqx); }
-                if (Lat<Q>::cy(i)) { gpy = fma2(p2(w * Lat<Q>::cy(i)), dp, gpy); gqy = fma2(p2(w * Lat<Q>::cy(i)), dq, gqy); }
-                if (Lat<Q>::cz(i)) { gpz = fma2(p2(w * Lat<Q>::cz(i)), dp, gpz); gqz = fma2(p2(w * Lat<Q>::cz(i)), dq, gqz); }
-            }
-            const float2 mu = ld_pair(mus, x0);
-            // this warp is done with the stage
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-
-            // ---- moments, force, velocity
-            float2 sf = f[0], ph = g[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                sf = add2(sf, f[i]);
-                ph = add2(ph, g[i]);
-                jx = acc_c(jx, f[i], Lat<Q>::cx(i));
-                jy = acc_c(jy, f[i], Lat<Q>::cy(i));
-                jz = acc_c(jz, f[i], Lat<Q>::cz(i));
-            }
-            const float2 rho = DEV ? add2(sf, p2(rho0)) : sf;
-            const float2 Fx = mul2(p2(3.f), sub2(mul2(mu, gpx), gqx));
-            const float2 Fy = mul2(p2(3.f), sub2(mul2(mu, gpy), gqy));
-            const float2 Fz = mul2(p2(3.f), sub2(mul2(mu, gpz), gqz));
-            const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
-            const float2 ux = mul2(fma2(p2(0.5f), Fx, jx), inv);
-            const float2 uy = mul2(fma2(p2(0.5f), Fy, jy), inv);
-            const float2 uz = mul2(fma2(p2(0.5f), Fz, jz), inv);
-            const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
-            const float2 uF = fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)));
-            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
-            const float2 omf = p2(1.f - of), omg = p2(1.f - og);
-            const float kf = float(1.0 - 0.5 / L.P.tau_f);
-            const float2 gmu3 = mul2(p2(float(3.0 * L.P.Gamma)), mu);
-            const float2 m15usq = mul2(p2(-1.5f), usq);
-            const float2 m3uF = mul2(p2(-3.f), uF);
-
-            // ---- collision and stores
-            const size_t off = row + x0;
-            S *fp = static_cast<S *>(L.dst.f) + off;
-            S *gp = static_cast<S *>(L.dst.g) + off;
-            {
-                const float w0 = float(Lat<Q>::w(0));
-                // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F
-                const float2 v = fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), mul2(p2(kf * w0), m3uF)));
-                st_pair(fp, v);
-            }
-            float2 gsum = p2(0.f);
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                if (Lat<Q>::opp(i) < i) continue;
-                const int j = Lat<Q>::opp(i);
-                float2 cu = p2(0.f), cF = p2(0.f);
-                cu = acc_c(cu, ux, Lat<Q>::cx(i));
-                cu = acc_c(cu, uy, Lat<Q>::cy(i));
-                cu = acc_c(cu, uz, Lat<Q>::cz(i));
-                cF = acc_c(cF, Fx, Lat<Q>::cx(i));
-                cF = acc_c(cF, Fy, Lat<Q>::cy(i));
-                cF = acc_c(cF, Fz, Lat<Q>::cz(i));
-                const float w = float(Lat<Q>::w(i));
-                const float2 cu3 = mul2(p2(3.f), cu);
-                const float2 E = fma2(mul2(p2(1.5f), cu3), cu, m15usq);  // 4.5 cu^2 - 1.5 u^2
-                const float2 wr = p2(of * w);
-                const float2 Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), fma2(mul2(p2(3.f), cu3), cF, m3uF)));
-                const float2 Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
-                const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
-                const float2 wg = p2(og * w);
-                const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
-                const float2 Bg = mul2(mul2(wg, ph), cu3);
-                const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
-                if constexpr (DEV) {
-                    st_pair(fp + (size_t)i * np, fi);
-                    st_pair(fp + (size_t)j * np, fj);
-                    // the rest population of g closes sum_i g*_i = phi on
-                    // the values as they are stored
-                    gsum = add2(gsum, add2(st_pair(gp + (size_t)(i - 1) * np, gi),
-                                           st_pair(gp + (size_t)(j - 1) * np, gj)));
-                } else {
-                    st_pair(fp + (size_t)i * np, fi);
-                    st_pair(fp + (size_t)j * np, fj);
-                    st_pair(gp + (size_t)i * np, gi);
-                    st_pair(gp + (size_t)j * np, gj);
-                    gsum = add2(gsum, add2(gi, gj));
-                }
-            }
-            if constexpr (DEV) st_pair(L.dst.g0 + off, sub2(ph, gsum));
-            else st_pair(gp, sub2(ph, gsum));
+            for (int r = 0; r < R; ++r)
+                st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
         } else {
-            static_assert(NPT == 1, "the update runs one or two nodes per consumer thread");
-            constexpr bool DEV = Fmt<FMT>::DEV;
+            // ---------------------------------------------------- update
             const float *__restrict__ phif = static_cast<const float *>(L.phi);
             const float *__restrict__ muf = static_cast<const float *>(L.mu);
-            const float *phs = reinterpret_cast<const float *>(cur + FL::f_off(nx));
-            const float *mus = phs + FL::NA * nx;
-            const int x = threadIdx.x;
-            const Site st = make_site(L.G, x, y, z);
-            // ---- read phase: everything this node needs from the stage
-            // pulled populations; the 16-bit formats keep f as deviations
-            // f_i - w_i rho0 all the way through the collision
-            float f[Q], g[Q];
+            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
+            const float kf = float(1.0 - 0.5 / L.P.tau_f);
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+                const unsigned wall = wall_s[s][r];
+                const int y = y0 + r;
+                const size_t row = ((size_t)z * ny + y) * nx;
+                const Site st = make_site(L.G, x0, y, z);
+                // ---- read phase: pulled populations (16-bit f as deviations
+                // f_i - w_i rho0), then the stencil values of phi and mu
+                float2 f[Q], g[Q];
 #pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                if (PULL && (wall >> i) & 1u) {
-                    const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
-                    const float cu = float(Lat<Q>::cx(i)) * uw;
-                    const float w2 = float(2.0 * Lat<Q>::w(i) * 3.0);
-                    // slot i holds the local row of population opp(i)
-                    const S fv = reinterpret_cast<const S *>(cur)[i * nx + x];
-                    float fl;
-                    if constexpr (DEV) fl = to_float(fv);
-                    else fl = fv;
-                    f[i] = fl + w2 * rho0 * cu;
-                    g[i] = fr_g<Q, FMT>(gb, nx, i, x) + w2 * php[st.n] * cu;
-                } else {
-                    const int xs = PULL ? wrap_x(x - Lat<Q>::cx(i), nx) : x;
-                    const S fv = reinterpret_cast<const S *>(cur)[i * nx + xs];
-                    if constexpr (DEV) f[i] = to_float(fv);
-                    else f[i] = fv;
-                    g[i] = fr_g<Q, FMT>(gb, nx, i, xs);
+                for (int i = 0; i < Q; ++i) {
+                    const bool wl = PULL && ((wall >> i) & 1u);
+                    const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
+                    float2 gv;
+                    if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
+                    else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
+                    float2 fv = ld_shift(reinterpret_cast<const S *>(cur + FL::f_row(nx, i, r)), x0, cx, nx);
+                    if (wl) {
+                        // the row of opp(i) at this node: add the moving-wall
+                        // term 2 w_i a (c_i . u_w) / cs^2
+                        const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
+                        const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
+                        fv = add2(fv, p2(w2cu * rho0));
+                        gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
+                    }
+                    f[i] = fv;
+                    g[i] = gv;
                 }
-            }
-            // isotropic gradients of phi and phi mu over opposite pairs:
-            // sum_i w_i c_i a(x + c_i) = sum_pairs w_i c_i (a(x + c_i) - a(x - c_i))
-            float gpx = 0.f, gpy = 0.f, gpz = 0.f, gqx = 0.f, gqy = 0.f, gqz = 0.f;
+                float2 gpx = p2(0.f), gpy = p2(0.f), gpz = p2(0.f), gqx = p2(0.f), gqy = p2(0.f), gqz = p2(0.f);
 #pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                if (Lat<Q>::opp(i) < i) continue;
-                float pv[2], mv[2];
+                for (int i = 1; i < Q; ++i) {
+                    if (Lat<Q>::opp(i) < i) continue;
+                    float2 pv[2], mv[2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int k = h ? Lat<Q>::opp(i) : i;
-                    const int a = axial_slot(Lat<Q>::cy(k), Lat<Q>::cz(k));
-                    if (a >= 0) {
-                        const int xn = wrap_x(x + Lat<Q>::cx(k), nx);
-                        pv[h] = phs[a * nx + xn];
-                        mv[h] = mus[a * nx + xn];
+                    for (int h = 0; h < 2; ++h) {
+                        const int kk = h ? Lat<Q>::opp(i) : i;
+                        const int cyk = Lat<Q>::cy(kk), czk = Lat<Q>::cz(kk);
+                        if (cyk == 0 || czk == 0) {
+                            const float *pr = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(cyk, czk, r)));
+                            const float *mr = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 1, FL::fk(cyk, czk, r)));
+                            pv[h] = ld_shift(pr, x0, -Lat<Q>::cx(kk), nx);
+                            mv[h] = ld_shift(mr, x0, -Lat<Q>::cx(kk), nx);
+                        } else {
+                            // off-axis rows (c_x = 0): an aligned pair in global memory
+                            const int kn = site_nb<Q>(st, kk);
+                            pv[h] = __ldg(reinterpret_cast<const float2 *>(phif + kn));
+                            mv[h] = __ldg(reinterpret_cast<const float2 *>(muf + kn));
+                        }
+                    }
+                    const float2 dp = sub2(pv[0], pv[1]);
+                    const float2 dq = sub2(mul2(pv[0], mv[0]), mul2(pv[1], mv[1]));
+                    const float w = float(Lat<Q>::w(i));
+                    if (Lat<Q>::cx(i)) { gpx = fma2(p2(w * Lat<Q>::cx(i)), dp, gpx); gqx = fma2(p2(w * Lat<Q>::cx(i)), dq, gqx); }
+                    if (Lat<Q>::cy(i)) { gpy = fma2(p2(w * Lat<Q>::cy(i)), dp, gpy); gqy = fma2(p2(w * Lat<Q>::cy(i)), dq, gqy); }
+                    if (Lat<Q>::cz(i)) { gpz = fma2(p2(w * Lat<Q>::cz(i)), dp, gpz); gqz = fma2(p2(w * Lat<Q>::cz(i)), dq, gqz); }
+                }
+                const float2 mu = ld_pair(reinterpret_cast<const float *>(cur + FL::fld_row(nx, 1, FL::fk(0, 0, r))), x0);
+                if (r == R - 1) {
+                    // this warp is done with the stage
+                    __syncwarp();
+                    if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
+                }
+
+                // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
+                float2 sf = f[0], ph = g[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    sf = add2(sf, f[i]);
+                    ph = add2(ph, g[i]);
+                    jx = acc_c(jx, f[i], Lat<Q>::cx(i));
+                    jy = acc_c(jy, f[i], Lat<Q>::cy(i));
+                    jz = acc_c(jz, f[i], Lat<Q>::cz(i));
+                }
+                // sf is rho, or rho - rho0 for deviations: in both cases the
+                // density term of omega (f_eq_i [- w_i rho0])
+                const float2 rho = DEV ? add2(sf, p2(rho0)) : sf;
+                const float2 Fx = mul2(p2(3.f), sub2(mul2(mu, gpx), gqx));
+                const float2 Fy = mul2(p2(3.f), sub2(mul2(mu, gpy), gqy));
+                const float2 Fz = mul2(p2(3.f), sub2(mul2(mu, gpz), gqz));
+                const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+                const float2 ux = mul2(fma2(p2(0.5f), Fx, jx), inv);
+                const float2 uy = mul2(fma2(p2(0.5f), Fy, jy), inv);
+                const float2 uz = mul2(fma2(p2(0.5f), Fz, jz), inv);
+                const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+                const float2 uF = fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)));
+                const float2 omf = p2(1.f - of), omg = p2(1.f - og);
+                const float2 gmu3 = mul2(p2(float(3.0 * L.P.Gamma)), mu);
+                const float2 m15usq = mul2(p2(-1.5f), usq);
+                const float2 m3uF = mul2(p2(-3.f), uF);
+
+                // ---- collision (Eq. bgk, feq, Fi, LBEg, geq) and stores
+                const size_t off = row + x0;
+                S *fp = static_cast<S *>(L.dst.f) + off;
+                S *gp = static_cast<S *>(L.dst.g) + off;
+                {
+                    const float w0 = float(Lat<Q>::w(0));
+                    // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F
+                    st_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), mul2(p2(kf * w0), m3uF))));
+                }
+                // moving populations in opposite pairs (i, opp(i)): the
+                // equilibria and the Guo term split into parts even and odd
+                // in c_i that the pair shares
+                float2 gsum = p2(0.f);
+#pragma unroll
+                for (int i = 1; i < Q; ++i) {
+                    if (Lat<Q>::opp(i) < i) continue;
+                    const int j = Lat<Q>::opp(i);
+                    float2 cu = p2(0.f), cF = p2(0.f);
+                    cu = acc_c(cu, ux, Lat<Q>::cx(i));
+                    cu = acc_c(cu, uy, Lat<Q>::cy(i));
+                    cu = acc_c(cu, uz, Lat<Q>::cz(i));
+                    cF = acc_c(cF, Fx, Lat<Q>::cx(i));
+                    cF = acc_c(cF, Fy, Lat<Q>::cy(i));
+                    cF = acc_c(cF, Fz, Lat<Q>::cz(i));
+                    const float w = float(Lat<Q>::w(i));
+                    const float2 cu3 = mul2(p2(3.f), cu);
+                    const float2 E = fma2(mul2(p2(1.5f), cu3), cu, m15usq);  // 4.5 cu^2 - 1.5 u^2
+                    const float2 wr = p2(of * w);
+                    const float2 Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), fma2(mul2(p2(3.f), cu3), cF, m3uF)));
+                    const float2 Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
+                    const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
+                    const float2 wg = p2(og * w);
+                    const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
+                    const float2 Bg = mul2(mul2(wg, ph), cu3);
+                    const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
+                    st_pair(fp + (size_t)i * np, fi);
+                    st_pair(fp + (size_t)j * np, fj);
+                    if constexpr (DEV) {
+                        // the rest population of g closes sum_i g*_i = phi on
+                        // the values as they are stored
+                        gsum = add2(gsum, add2(st_pair(gp + (size_t)(i - 1) * np, gi),
+                                               st_pair(gp + (size_t)(j - 1) * np, gj)));
                     } else {
-                        const int kn = site_nb<Q>(st, k);
-                        pv[h] = __ldg(phif + kn);
-                        mv[h] = __ldg(muf + kn);
+                        st_pair(gp + (size_t)i * np, gi);
+                        st_pair(gp + (size_t)j * np, gj);
+                        gsum = add2(gsum, add2(gi, gj));
                     }
                 }
-                const float dp = pv[0] - pv[1];
-                const float dq = pv[0] * mv[0] - pv[1] * mv[1];
-                const float w = float(Lat<Q>::w(i));
-                if (Lat<Q>::cx(i)) { gpx += w * float(Lat<Q>::cx(i)) * dp; gqx += w * float(Lat<Q>::cx(i)) * dq; }
-                if (Lat<Q>::cy(i)) { gpy += w * float(Lat<Q>::cy(i)) * dp; gqy += w * float(Lat<Q>::cy(i)) * dq; }
-                if (Lat<Q>::cz(i)) { gpz += w * float(Lat<Q>::cz(i)) * dp; gqz += w * float(Lat<Q>::cz(i)) * dq; }
+                if constexpr (DEV) st_pair(L.dst.g0 + off, sub2(ph, gsum));
+                else st_pair(gp, sub2(ph, gsum));
             }
-            const float mu = mus[x];
-            // this warp is done with the stage; the collision and the stores
-            // below run while the producer refills it
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-
-            // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
-            float sf = 0.f, ph = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                sf += f[i];
-                ph += g[i];
-                if (Lat<Q>::cx(i)) jx += float(Lat<Q>::cx(i)) * f[i];
-                if (Lat<Q>::cy(i)) jy += float(Lat<Q>::cy(i)) * f[i];
-                if (Lat<Q>::cz(i)) jz += float(Lat<Q>::cz(i)) * f[i];
-            }
-            // sf is rho, or rho - rho0 for deviations: in both cases the
-            // density term of omega (f_eq_i - w_i rho0 [deviations])
-            const float rho = DEV ? sf + rho0 : sf;
-            const float Fx = 3.f * (mu * gpx - gqx), Fy = 3.f * (mu * gpy - gqy), Fz = 3.f * (mu * gpz - gqz);
-            const float inv = 1.f / rho;
-            const float ux = (jx + 0.5f * Fx) * inv, uy = (jy + 0.5f * Fy) * inv, uz = (jz + 0.5f * Fz) * inv;
-            const float usq = ux * ux + uy * uy + uz * uz;
-            const float uF = ux * Fx + uy * Fy + uz * Fz;
-            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
-            const float omf = 1.f - of, omg = 1.f - og;
-            const float kf = float(1.0 - 0.5 / L.P.tau_f);
-            const float gmu3 = float(3.0 * L.P.Gamma) * mu;
-
-            // ---- collision (Eq. bgk, feq, Fi, LBEg, geq) and stores
-            const size_t off = row + x;
-            S *fp = static_cast<S *>(L.dst.f) + off;
-            // rest population of f: (1 - omega) f_0 + omega f_eq_0 + S_0
-            {
-                const float w0 = float(Lat<Q>::w(0));
-                const float v = fmaf(omf, f[0], of * w0 * (sf - 1.5f * rho * usq) - 3.f * kf * w0 * uF);
-                if constexpr (DEV) fp[0] = from_float<S>(v);
-                else fp[0] = v;
-            }
-            // moving populations in opposite pairs (i, opp(i)): the
-            // equilibria and the Guo term split into parts even and odd in
-            // c_i that the pair shares
-            float gsum = 0.f;
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                if (Lat<Q>::opp(i) < i) continue;
-                const int j = Lat<Q>::opp(i);
-                const float cx = float(Lat<Q>::cx(i)), cy = float(Lat<Q>::cy(i)), cz = float(Lat<Q>::cz(i));
-                const float w = float(Lat<Q>::w(i));
-                const float cu = cx * ux + cy * uy + cz * uz;
-                const float cF = cx * Fx + cy * Fy + cz * Fz;
-                const float E = fmaf(4.5f * cu, cu, -1.5f * usq);
-                const float wr = of * w;
-                const float Af = fmaf(wr, fmaf(rho, E, sf), kf * w * fmaf(9.f * cu, cF, -3.f * uF));
-                const float Bf = fmaf(wr * rho, 3.f * cu, 3.f * kf * w * cF);
-                const float fi = fmaf(omf, f[i], Af + Bf), fj = fmaf(omf, f[j], Af - Bf);
-                const float wg = og * w;
-                const float Ag = wg * fmaf(ph, E, gmu3);
-                const float Bg = wg * ph * 3.f * cu;
-                const float gi = fmaf(omg, g[i], Ag + Bg), gj = fmaf(omg, g[j], Ag - Bg);
-                if constexpr (DEV) {
-                    fp[(size_t)i * np] = from_float<S>(fi);
-                    fp[(size_t)j * np] = from_float<S>(fj);
-                    const S hi = from_float<S>(gi), hj = from_float<S>(gj);
-                    S *gp = static_cast<S *>(L.dst.g) + off;
-                    gp[(size_t)(i - 1) * np] = hi;
-                    gp[(size_t)(j - 1) * np] = hj;
-                    // the rest population of g closes sum_i g*_i = phi on
-                    // the values as they are stored
-                    gsum += to_float(hi) + to_float(hj);
-                } else {
-                    fp[(size_t)i * np] = fi;
-                    fp[(size_t)j * np] = fj;
-                    S *gp = static_cast<S *>(L.dst.g) + off;
-                    gp[(size_t)i * np] = gi;
-                    gp[(size_t)j * np] = gj;
-                    gsum += gi + gj;
-                }
-            }
-            if constexpr (DEV) L.dst.g0[off] = ph - gsum;
-            else static_cast<S *>(L.dst.g)[off] = ph - gsum;
         }
     }
 }
@@ -967,49 +884,70 @@ __global__ void __launch_bounds__(512 / NPT + 32, KIND == WS_UPDATE ? 1 : 2) k_w
 template <int Q, int FMT>
 struct WsRowLaunchers {
     using S = typename Fmt<FMT>::S;
-    static constexpr int kMaxSmem = 200 * 1024;
+    static constexpr int kMaxSmem = 225 * 1024;
     // stages per block: the update takes as many as fit (one block per SM);
     // the lighter phi and mu passes take two, so that two blocks (two
     // producer warps issuing bulk copies) share an SM
-    template <int KIND>
+    template <int KIND, int R>
     static int nst(int nx) {
-        const unsigned sb = FullRowLayout<Q, FMT, KIND>::stage(nx);
-        const int n = (int)(kMaxSmem / sb);
+        const unsigned sb = RowsLayout<Q, FMT, KIND, R>::stage(nx);
+        const int lim = KIND == WS_UPDATE ? kMaxSmem : kMaxSmem / 2;
+        const int n = (int)(lim / sb);
         if (KIND != WS_UPDATE) return n >= 2 ? 2 : n;
-        return n >= 4 ? 4 : (n >= 3 ? 3 : (n >= 2 ? 2 : n));
+        return n >= 3 ? 3 : (n >= 2 ? 2 : n);
+    }
+    // two rows per unit where a staged row is shorter than 2 KB
+    template <int KIND>
+    static int rows_per_unit(const Geo &G, bool pull) {
+        if (KIND == WS_MU || !pull || G.ny % 2 != 0) return 1;
+        if (RowsLayout<Q, FMT, KIND, 1>::rowb(G.nx) >= 2048) return 1;
+        return nst<KIND, 2>(G.nx) >= 2 ? 2 : 1;
     }
     static bool usable(const Geo &G) {
         if (G.device == FRE_FOUR_ROLLER) return false;
         if ((G.np * sizeof(S)) % 16 != 0 || (G.nx * sizeof(S)) % 16 != 0 || (G.nx * 4) % 16 != 0) return false;
         if (G.nx < 64 || G.nx > 512 || G.nx % 64 != 0) return false;
-        return nst<WS_UPDATE>(G.nx) >= 2;
+        return nst<WS_UPDATE, 1>(G.nx) >= 2 && nst<WS_PHI, 1>(G.nx) >= 1 && nst<WS_MU, 1>(G.nx) >= 1;
     }
-    template <int KIND, bool PULL, int NST>
+    template <int KIND, bool PULL, int NST, int R, int NXC>
     static void launch(const Launch &L) {
-        // every pass takes adjacent node pairs per consumer thread (the
-        // update computes them with packed FP32 pair arithmetic)
-        constexpr int NPT = 2;
         const int nx = L.G.nx;
-        const int nu = L.G.ny * L.G.nz;
-        const size_t smem = (size_t)NST * FullRowLayout<Q, FMT, KIND>::stage(nx);
-        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, NPT>;
-        static bool attr = false;
-        if (!attr) {
-            attr = true;
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        const int nu = (L.G.ny / R) * L.G.nz;
+        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
+        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
+        // opt in to exactly the shared memory this launch needs (a larger
+        // opt-in would shrink the L1 share of the SM's on-chip memory)
+        static size_t attr = 0;
+        if (smem > attr) {
+            attr = smem;
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         }
-        const int threads = nx / NPT + 32;
+        const int threads = nx / 2 + 32;
         const int g = std::min(nu, PipeLaunchers<Q, FMT>::sms() *
                                        PipeLaunchers<Q, FMT>::blocks_per_sm((const void *)fn, threads, smem));
         fn<<<g, threads, smem, L.stream>>>(L, nu);
     }
+    template <int KIND, bool PULL, int R>
+    static void run_r(const Launch &L) {
+        // rows of 512 nodes (the common large-lattice case) take the
+        // compile-time row length
+        if (PULL && L.G.nx == 512) {
+            if (nst<KIND, R>(512) >= 3) launch<KIND, PULL, 3, R, 512>(L);
+            else launch<KIND, PULL, 2, R, 512>(L);
+            return;
+        }
+        if (nst<KIND, R>(L.G.nx) >= 3) launch<KIND, PULL, 3, R, 0>(L);
+        else launch<KIND, PULL, 2, R, 0>(L);
+    }
     template <int KIND, bool PULL>
     static void run(const Launch &L) {
-        switch (nst<KIND>(L.G.nx)) {
-            case 4: launch<KIND, PULL, 4>(L); break;
-            case 3: launch<KIND, PULL, 3>(L); break;
-            default: launch<KIND, PULL, 2>(L); break;
+        if constexpr (PULL && KIND != WS_MU) {
+            if (rows_per_unit<KIND>(L.G, PULL) == 2) {
+                run_r<KIND, PULL, 2>(L);
+                return;
+            }
         }
+        run_r<KIND, PULL, 1>(L);
     }
     static void update(const Launch &L, bool pull) {
         if (pull) run<WS_UPDATE, true>(L);
