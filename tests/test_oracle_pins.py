@@ -371,3 +371,115 @@ def test_neutral_wall_half_droplet(orc):
     assert np.abs(ph - pf).max() < 2e-3
     # not vacuous: the droplet still touches the wall
     assert ph[0, N // 2] > 0.9
+
+
+# ---------------------------------------------------- brute force, one step
+
+def _hermite_basis(c, cs2):
+    """Hermite polynomials up to second order at the lattice velocities:
+    columns 1, c_a, c_a c_b - cs2 delta_ab (a <= b)."""
+    q, d = c.shape
+    cols = [np.ones(q)] + [c[:, a] for a in range(d)]
+    for a in range(d):
+        for b in range(a, d):
+            cols.append(c[:, a] * c[:, b] - (cs2 if a == b else 0.0))
+    return np.stack(cols, axis=1)
+
+
+def _moments(c, v):
+    """Zeroth, first and (upper) second moments of a population vector."""
+    q, d = c.shape
+    out = [v.sum()] + [(c[:, a] * v).sum() for a in range(d)]
+    for a in range(d):
+        for b in range(a, d):
+            out.append((c[:, a] * c[:, b] * v).sum())
+    return np.array(out)
+
+
+def _fit(c, w, target, fixed=None):
+    """The population sum_k w_i x_k H_k(c_i) whose moments equal `target`,
+    found by solving the linear moment system (no closed-form equilibrium).
+    `fixed` pins the coefficient of H_0 and lets the rest population absorb
+    the zeroth moment instead (the structure of Eq. geq)."""
+    H = _hermite_basis(c, CS2)
+    if fixed is None:
+        M = np.stack([_moments(c, w * H[:, k]) for k in range(H.shape[1])], axis=1)
+        x = np.linalg.solve(M, target)
+        return w * (H @ x)
+    # moving populations only carry the expansion; the rest population g_0
+    # is a separate unknown
+    wm = w.copy()
+    wm[0] = 0.0
+    M = np.stack([_moments(c, wm * H[:, k]) for k in range(H.shape[1])], axis=1)
+    rest = np.zeros(len(w))
+    rest[0] = 1.0
+    Mr = np.concatenate([M[:, 1:], _moments(c, rest)[:, None]], axis=1)
+    x = np.linalg.solve(Mr, target - fixed * M[:, 0])
+    return wm * (fixed * H[:, 0] + H[:, 1:] @ x[:-1]) + x[-1] * rest
+
+
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 4, 4)), (1, (4, 4, 4))])
+def test_brute_force_one_step(orc, lattice, shape):
+    """One step on a tiny periodic lattice from random positive populations,
+    recomputed by an independent route: equilibria and the Guo term from
+    their moment conditions by linear solves, the stencils as Fourier
+    multipliers (FFT), streaming by array rolls.  Agreement to 1e-13."""
+    nz, ny, nx = shape
+    c, _ = _lat(orc, lattice)
+    q, d = c.shape[0], (2 if lattice == 0 else 3)
+    # textbook weights by speed class (|c|^2 = 0, 1, 2)
+    w = np.array([{0: 4 / 9, 1: 1 / 9, 2: 1 / 36}[int(v)] if d == 2 else {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}[int(v)]
+                  for v in (c ** 2).sum(1)])
+    cd = c[:, :d]
+    tau_f, tau_g, A, kappa, Gamma = 0.8, 1.3, 0.03, 0.05, 0.7
+    rng = np.random.default_rng(5)
+    f = w[:, None, None, None] * (1.0 + 0.1 * rng.uniform(-1, 1, (q,) + shape))
+    g = w[:, None, None, None] * rng.uniform(-0.9, 0.9, (q,) + shape)
+
+    o = orc.Oracle(lattice, orc.PERIODIC, nx, ny, nz, tau_f, tau_g, A, kappa, Gamma, 0.0, 1.0)
+    o.load_populations(f, g)
+    o.step(1)
+    fo, go = o.populations()
+
+    axes = {0: 2, 1: 1, 2: 0}  # lattice axis a -> array axis of [nz][ny][nx]
+    rho = f.sum(0)
+    phi = g.sum(0)
+    # stencils as Fourier multipliers of the isotropic weighted sums
+    ks = np.meshgrid(*[2 * np.pi * np.fft.fftfreq(n) for n in shape], indexing="ij")  # (kz, ky, kx)
+    kvec = [ks[axes[a]] for a in range(d)]
+    phase = [np.exp(1j * sum(kvec[a] * cd[i, a] for a in range(d))) for i in range(q)]
+    lap_sym = (2 / CS2) * sum(w[i] * (phase[i] - 1) for i in range(q))
+    grad_sym = [(1 / CS2) * sum(w[i] * cd[i, a] * phase[i] for i in range(q)) for a in range(d)]
+    lap = np.fft.ifftn(lap_sym * np.fft.fftn(phi)).real
+    mu = A * (phi ** 3 - phi) - kappa * lap
+    grad = lambda field, a: np.fft.ifftn(grad_sym[a] * np.fft.fftn(field)).real  # noqa: E731
+    F = [mu * grad(phi, a) - grad(phi * mu, a) for a in range(d)]
+    u = [(sum(cd[i, a] * f[i] for i in range(q)) + 0.5 * F[a]) / rho for a in range(d)]
+
+    f_new = np.empty_like(f)
+    g_new = np.empty_like(g)
+    post_f = np.empty_like(f)
+    post_g = np.empty_like(g)
+    for idx in np.ndindex(shape):
+        r, ph, m = rho[idx], phi[idx], mu[idx]
+        uu = np.array([u[a][idx] for a in range(d)])
+        FF = np.array([F[a][idx] for a in range(d)])
+        second = [r * (CS2 * (a == b) + uu[a] * uu[b]) for a in range(d) for b in range(a, d)]
+        feq = _fit(cd, w, np.array([r, *(r * uu), *second]))
+        k = 1 - 0.5 / tau_f
+        sec_s = [k * (uu[a] * FF[b] + FF[a] * uu[b]) for a in range(d) for b in range(a, d)]
+        S = _fit(cd, w, np.array([0.0, *(k * FF), *sec_s]))
+        sec_g = [Gamma * m * (a == b) + ph * uu[a] * uu[b] for a in range(d) for b in range(a, d)]
+        geq = _fit(cd, w, np.array([ph, *(ph * uu), *sec_g]), fixed=Gamma * m / CS2)
+        fi = f[(slice(None),) + idx]
+        gi = g[(slice(None),) + idx]
+        post_f[(slice(None),) + idx] = fi - (fi - feq) / tau_f + S
+        post_g[(slice(None),) + idx] = gi - (gi - geq) / tau_g
+    for i in range(q):
+        shift = [0, 0, 0]
+        for a in range(d):
+            shift[axes[a]] = int(cd[i, a])
+        f_new[i] = np.roll(post_f[i], shift, axis=(0, 1, 2))
+        g_new[i] = np.roll(post_g[i], shift, axis=(0, 1, 2))
+    assert np.abs(fo - f_new).max() < 1e-13
+    assert np.abs(go - g_new).max() < 1e-13
