@@ -1,0 +1,54 @@
+"""Accuracy of the storage formats on the 64^3 twin of the 512x256x256
+benchmark lattice (same A, kappa, tau, Gamma, wall speed; droplet R = 12
+keeps R/H = 48/256): droplet deformation D, droplet volume and Laplace
+pressure of FP32, FP16-deviation and BF16-deviation storage against the
+FP64 oracle on the same lattice after the same number of steps."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+N = 64
+STEPS = 2000
+PAR = dict(tau_f=2.0, tau_g=2.0, A=0.04, kappa=0.04, gamma_mob=0.5, u_wall=0.03, rho0=1.0)
+DROP = ((N - 1) / 2, (N - 1) / 2, (N - 1) / 2, 12.0)
+# relative error bounds (D, volume, dp) after STEPS steps: FP32 rounding;
+# 11 and 8 mantissa bits of the 16-bit stores.  Measured on a GB300: FP32
+# 8e-8 / 5e-6 / 2.5e-5, FP16 3.4e-3 / 4.7e-6 / 3.6e-5, BF16 6.4e-2 / 5.8e-6 /
+# 8.1e-4 (the droplet volume is conserved to FP32 rounding in every format:
+# the FP32 rest population of g closes sum_i g_i on the stored values)
+BOUNDS = {"fp32": (1e-4, 1e-5, 1e-4), "fp16dev": (1e-2, 1e-4, 1e-3), "bf16dev": (1e-1, 1e-4, 1e-2)}
+
+
+@pytest.fixture(scope="module")
+def fre():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_01617_gb300 import build
+    build.build()
+    import paper_2212_01617_gb300 as fre
+    return fre
+
+
+@pytest.fixture(scope="module")
+def reference(orc):
+    o = orc.Oracle(1, 0, N, N, N, PAR["tau_f"], PAR["tau_g"], PAR["A"], PAR["kappa"], PAR["gamma_mob"],
+                   PAR["u_wall"], PAR["rho0"])
+    o.init_droplet(*DROP)
+    o.step(STEPS)
+    return o.observables()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
+def test_twin_accuracy(fre, reference, precision):
+    sim = fre.Simulation(lattice="d3q19", precision=precision, device="shear", nx=N, ny=N, nz=N, **PAR)
+    sim.init_droplet(*DROP)
+    sim.step(STEPS)
+    ob = sim.observables()
+    sim.close()
+    ref = reference
+    err = {k: abs(ob[k] - ref[k]) / abs(ref[k]) for k in ("D", "volume", "dp")}
+    print(f"{precision}: D {ob['D']:.6f} (oracle {ref['D']:.6f}), relative errors {err}")
+    bD, bV, bP = BOUNDS[precision]
+    assert err["D"] < bD and err["volume"] < bV and err["dp"] < bP, err
