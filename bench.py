@@ -489,7 +489,9 @@ def run_serve_workload(args):
                          "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                          "mean_s": float(lat.mean()), "node_updates": upd, "outcomes": outcomes,
                          "mean_steps": float(np.mean([r["steps"] for r in res.values()])),
-                         "contexts_created": st["contexts_created"], "contexts_reused": st["contexts_reused"]}
+                         "contexts_created": st["contexts_created"], "contexts_reused": st["contexts_reused"],
+                         "batch_mode_at_end": {0: "batched", 1: "per-slot"}.get(st["batch_mode"]),
+                         "autotunes": st["tunes"], "graph_captures": st["captures"]}
             log(f"{name}: {json.dumps(out[name])}")
     b, s_ = out["batched_fp16dev"], out["sequential_fp32"]
     line = {"metric": "serving D3Q19 FRE-LBM: aggregate MLUPS and p50/p99 time-to-result",

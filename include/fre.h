@@ -333,6 +333,8 @@ typedef struct {
     long long node_updates;     /* sum over advances of running nodes x steps */
     long long steps_advanced;   /* batch steps issued */
     long long contexts_created, contexts_reused;
+    int batch_mode, batch_bx;   /* launch mode in force (see fre_batch_tuning) */
+    long long tunes, captures;  /* autotuner runs and graph captures so far */
 } fre_serve_stats;
 
 /* Create a server for one lattice and storage format; cuda_stream as in
@@ -346,7 +348,9 @@ fre_status fre_server_create(int lattice, int precision, const fre_serve_config 
 fre_status fre_server_submit(fre_server *s, const fre_params *p, double cx, double cy, double cz, double R,
                              long long *id);
 
-/* Admit what fits, advance every running request by up to chunk_steps
+/* Admit what fits (a request's first step, which collides in place, runs
+ * on admission: a result's step count includes it), advance every running
+ * request by up to chunk_steps
  * steps (stopping early at the next due check), run the due checks and
  * retire finished requests.  *running (nullable) receives the number of
  * requests still running.  Synchronises at each check. */

@@ -95,7 +95,8 @@ class fre_serve_stats(C.Structure):
     _fields_ = [("running", C.c_int), ("queued", C.c_int), ("bytes_running", C.c_size_t),
                 ("bytes_pooled", C.c_size_t), ("running_nodes", C.c_longlong), ("node_updates", C.c_longlong),
                 ("steps_advanced", C.c_longlong), ("contexts_created", C.c_longlong),
-                ("contexts_reused", C.c_longlong)]
+                ("contexts_reused", C.c_longlong), ("batch_mode", C.c_int), ("batch_bx", C.c_int),
+                ("tunes", C.c_longlong), ("captures", C.c_longlong)]
 
 
 _lock = threading.Lock()

@@ -43,6 +43,7 @@ struct fre_batch {
     double tuned_ms[4] = {0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128 and per-slot
     cudaGraphExec_t graph = nullptr;
     long long graph_replays = 0;
+    long long n_tunes = 0, n_captures = 0;
 };
 
 namespace {
@@ -236,6 +237,7 @@ fre_status capture(fre_batch *b) {
     } else {
         b->order = active(b);
     }
+    ++b->n_captures;
     BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     if (b->mode == 0) {
         launch_batched(b, 0);
@@ -278,6 +280,7 @@ bool any_local(const fre_batch *b) {
 // runs 3 graph replays, the last 2 timed -- 7 real steps per candidate.
 constexpr int kTuneSteps = 28;
 fre_status autotune(fre_batch *b, long long *taken) {
+    ++b->n_tunes;
     const int modes[4] = {0, 0, 0, 1};
     const int bxs[4] = {32, 64, 128, 64};
     double best = 1e300;
@@ -357,6 +360,13 @@ fre_ctx *fre::batch_detach(fre_batch *b, int slot) {
 }
 
 cudaStream_t fre::batch_stream(const fre_batch *b) { return b ? b->stream : nullptr; }
+
+void fre::batch_counters(const fre_batch *b, int *mode, int *bx, long long *tunes, long long *captures) {
+    *mode = b->mode;
+    *bx = b->bx;
+    *tunes = b->n_tunes;
+    *captures = b->n_captures;
+}
 
 extern "C" {
 

@@ -61,4 +61,6 @@ fre_status batch_attach(fre_batch *b, fre_ctx *c, size_t bytes, int *slot);
 fre_ctx *batch_detach(fre_batch *b, int slot);
 // the stream of a batch
 cudaStream_t batch_stream(const fre_batch *b);
+// launch mode in force and the counts of autotuner runs and graph captures
+void batch_counters(const fre_batch *b, int *mode, int *bx, long long *tunes, long long *captures);
 }  // namespace fre

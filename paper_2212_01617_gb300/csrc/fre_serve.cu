@@ -92,7 +92,8 @@ void collect(fre_server *s) {
         fre_serve_result r{};
         r.id = id;
         r.outcome = j->outcome;
-        r.steps = j->steps;
+        // plus the first step taken on admission
+        r.steps = j->steps + (j->t_admit >= 0.0 && j->outcome != fre::SERVE_FAILED ? 1 : 0);
         r.t_submit = j->t_submit;
         r.t_admit = j->t_admit;
         r.t_done = j->t_done;
@@ -145,6 +146,12 @@ fre_status start(fre_server *s, long long id) {
         if (st == FRE_OK) ++s->created;
     }
     if (st == FRE_OK) st = fre_init_droplet(c, r.cx, r.cy, r.cz, r.R);
+    // the first step collides in place (no streaming yet); taking it here,
+    // on the batch stream, lets the request join the batch's streaming steps
+    if (st == FRE_OK) {
+        fre::ctx_launch_step(c);
+        if (cudaGetLastError() != cudaSuccess) st = sfail(FRE_ERR_CUDA, "fre_server: first step launch failed");
+    }
     if (st == FRE_OK) st = fre::batch_attach(s->batch, c, bytes, &r.slot);
     if (st != FRE_OK) {
         if (c) fre_destroy(c);
@@ -275,6 +282,7 @@ fre_status fre_server_stats(const fre_server *s, fre_serve_stats *out) {
     out->steps_advanced = s->steps_advanced;
     out->contexts_created = s->created;
     out->contexts_reused = s->reused;
+    fre::batch_counters(s->batch, &out->batch_mode, &out->batch_bx, &out->tunes, &out->captures);
     return FRE_OK;
 }
 
