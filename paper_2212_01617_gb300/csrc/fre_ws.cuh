@@ -539,16 +539,6 @@ __host__ __device__ constexpr unsigned cy_mask(int sy) {
 
 // NXC: the row length as a compile-time constant (every shared-memory
 // offset then folds into the instruction), or 0 to take it from the launch.
-// Four-roller device: the near-solid flags of a node pair (x, x + 1) of a
-// row, low byte x (0 plain fluid, 1 solid, 2 fluid with a solid neighbour);
-// 0 on the other devices.  A pair with any flag set is updated by the
-// per-node code (bounce-back per link on the roller staircase), solid
-// nodes not at all.
-__device__ __forceinline__ unsigned pair_flags(const Geo &G, size_t off) {
-    if (G.device != FRE_FOUR_ROLLER) return 0u;
-    return *reinterpret_cast<const unsigned short *>(G.nearsolid + off);
-}
-
 template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC>
 __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
@@ -714,16 +704,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const size_t off = ((size_t)z * ny + y0 + r) * nx + x0;
-                const unsigned fl = pair_flags(L.G, off);
-                if (fl) {
-                    for (int t = 0; t < 2; ++t)
-                        if (((fl >> (8 * t)) & 0xffu) != 1u) node_phi<Q, FMT, PULL>(L, make_site(L.G, x0 + t, y0 + r, z));
-                    continue;
-                }
-                st_pair(static_cast<float *>(L.phi) + off, out[r]);
-            }
+            for (int r = 0; r < R; ++r)
+                st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
         } else if constexpr (KIND == WS_MU) {
             float2 out[R];
 #pragma unroll
@@ -746,16 +728,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const size_t off = ((size_t)z * ny + y0 + r) * nx + x0;
-                const unsigned fl = pair_flags(L.G, off);
-                if (fl) {
-                    for (int t = 0; t < 2; ++t)
-                        if (((fl >> (8 * t)) & 0xffu) != 1u) node_mu<Q, float>(L, make_site(L.G, x0 + t, y0 + r, z));
-                    continue;
-                }
-                st_pair(static_cast<float *>(L.mu) + off, out[r]);
-            }
+            for (int r = 0; r < R; ++r)
+                st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
         } else {
             // ---------------------------------------------------- update
             const float *__restrict__ phif = static_cast<const float *>(L.phi);
@@ -823,14 +797,6 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                     // this warp is done with the stage
                     __syncwarp();
                     if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-                }
-                {
-                    const unsigned fl = pair_flags(L.G, row + x0);
-                    if (fl) {
-                        for (int t = 0; t < 2; ++t)
-                            if (((fl >> (8 * t)) & 0xffu) != 1u) node_update<Q, FMT, PULL>(L, make_site(L.G, x0 + t, y, z));
-                        continue;
-                    }
                 }
 
                 // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
@@ -938,6 +904,7 @@ struct WsRowLaunchers {
         return nst<KIND, 2>(G.nx) >= 2 ? 2 : 1;
     }
     static bool usable(const Geo &G) {
+        if (G.device == FRE_FOUR_ROLLER) return false;
         if ((G.np * sizeof(S)) % 16 != 0 || (G.nx * sizeof(S)) % 16 != 0 || (G.nx * 4) % 16 != 0) return false;
         if (G.nx < 64 || G.nx > 512 || G.nx % 64 != 0) return false;
         return nst<WS_UPDATE, 1>(G.nx) >= 2 && nst<WS_PHI, 1>(G.nx) >= 1 && nst<WS_MU, 1>(G.nx) >= 1;
