@@ -340,7 +340,8 @@ def batch_case_params(c):
 
 def run_batch_workload(args):
     """64 uneven D2Q9 cases (half shear, half four-roller), FP32: one batch
-    (autotuned batched or per-slot launches, CUDA-graph replays) against one
+    (autotuned batched, per-slot or concurrent per-slot launches, CUDA-graph
+    replays) against one
     context per case stepped on its own (one launch per kernel per case)."""
     import torch
     import paper_2212_01617_gb300 as fre
@@ -392,7 +393,7 @@ def _batch_workload(args, fre, cases, nodes, stream):
     ms_seq = e0.elapsed_time(e1)
     for sim in sims:
         sim.close()
-    mode = {0: "batched", 1: "per-slot"}[tuning["mode"]]
+    mode = {0: "batched", 1: "per-slot", 2: "per-slot concurrent"}[tuning["mode"]]
     line = {"metric": "batched D2Q9 FRE-LBM MLUPS, 64 uneven cases", "value": nodes * args.steps / ms_batch / 1e3,
             "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 40),
             "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -406,7 +407,8 @@ def _batch_workload(args, fre, cases, nodes, stream):
             "speedup_vs_sequential": ms_seq / ms_batch,
             "tuning": {"mode": mode, "bx": tuning["bx"],
                        "ms_per_step_candidates": dict(zip(["batched bx32", "batched bx64", "batched bx128",
-                                                           "per-slot"], tuning["ms_per_step"]))},
+                                                           "per-slot", "per-slot concurrent"],
+                                                          tuning["ms_per_step"]))},
             "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
@@ -490,7 +492,8 @@ def run_serve_workload(args):
                          "mean_s": float(lat.mean()), "node_updates": upd, "outcomes": outcomes,
                          "mean_steps": float(np.mean([r["steps"] for r in res.values()])),
                          "contexts_created": st["contexts_created"], "contexts_reused": st["contexts_reused"],
-                         "batch_mode_at_end": {0: "batched", 1: "per-slot"}.get(st["batch_mode"]),
+                         "batch_mode_at_end": {0: "batched", 1: "per-slot", 2: "per-slot concurrent"}.get(
+                             st["batch_mode"]),
                          "autotunes": st["tunes"], "graph_captures": st["captures"]}
             log(f"{name}: {json.dumps(out[name])}")
     b, s_ = out["batched_fp16dev"], out["sequential_fp32"]

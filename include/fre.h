@@ -265,8 +265,10 @@ int fre_batch_slots(const fre_batch *b, int *slots, int max_slots);
 size_t fre_batch_bytes_in_use(const fre_batch *b);
 
 /* Autotuner result: mode (0 one launch per kernel for all slots, 1 each
- * slot's own kernels), block width, and ms per step measured for the four
- * candidates (batched width 32, 64, 128; per-slot).  FRE_ERR_STATE if no
+ * slot's own kernels one slot after another, 2 each slot's own kernels on
+ * four concurrent graph branches), block width, and ms per step measured
+ * for the five candidates (batched width 32, 64, 128; per-slot; concurrent)
+ * in ms_per_step[0..4].  FRE_ERR_STATE if no
  * tuning is in force: none ran yet, or the slot count has since changed by
  * more than a factor 2 (smaller changes keep the tuned mode). */
 fre_status fre_batch_tuning(const fre_batch *b, int *mode, int *bx, double *ms_per_step);

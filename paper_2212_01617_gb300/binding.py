@@ -455,7 +455,7 @@ class Batch:
 
     def tuning(self):
         mode, bx = C.c_int(0), C.c_int(0)
-        ms = np.zeros(4)
+        ms = np.zeros(5)
         s = load_library().fre_batch_tuning(self.h, C.byref(mode), C.byref(bx), _dptr(ms))
         return {"tuned": s == FRE_OK, "mode": mode.value, "bx": bx.value, "ms_per_step": ms.tolist()}
 

@@ -36,11 +36,15 @@ struct fre_batch {
     int table_bx = 0;  // block width the block prefix was built for
     int total_blocks = 0, total_ghost_blocks = 0;
     // tuning and graph
-    int mode = 0;  // 0 batched, 1 per-slot
+    int mode = 0;  // 0 batched, 1 per-slot, 2 per-slot on concurrent streams
     int bx = 64;
     bool tuned = false;
     int tuned_nslots = 0;  // slot count the tuning was measured on
-    double tuned_ms[4] = {0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128 and per-slot
+    double tuned_ms[5] = {0, 0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128, per-slot, concurrent
+    // streams and events of the concurrent mode (graph branches)
+    static constexpr int kBranches = 4;
+    cudaStream_t aux[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
     cudaGraphExec_t graph = nullptr;
     long long graph_replays = 0;
     long long n_tunes = 0, n_captures = 0;
@@ -211,6 +215,7 @@ fre_status single_step(fre_batch *b) {
         }
         drop_graph(b);
     } else {
+        // per-slot modes: one slot after another outside a graph
         b->order = active(b);
         for (int s : b->order) fre::ctx_launch_step(b->slots[s]);
         b->tables_valid = false;  // buffer parities changed
@@ -238,14 +243,41 @@ fre_status capture(fre_batch *b) {
         b->order = active(b);
     }
     ++b->n_captures;
+    if (b->mode == 2 && !b->fork) {
+        // streams and events of the graph branches, made once
+        BCUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        for (int j = 0; j < fre_batch::kBranches; ++j) {
+            BCUDA(cudaStreamCreateWithFlags(&b->aux[j], cudaStreamNonBlocking));
+            BCUDA(cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming));
+        }
+    }
     BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     if (b->mode == 0) {
         launch_batched(b, 0);
         launch_batched(b, 1);
-    } else {
+    } else if (b->mode == 1) {
         for (int s : b->order) fre::ctx_launch_step(b->slots[s]);
         for (int s : b->order) fre::ctx_launch_step(b->slots[s]);
         for (int s : b->order) b->slots[s]->step -= 2;  // captured, not run
+    } else {
+        // slot k's two steps on branch k mod kBranches: the slots' kernels
+        // may then run side by side
+        cudaEventRecord(b->fork, b->stream);
+        for (int j = 0; j < fre_batch::kBranches; ++j) cudaStreamWaitEvent(b->aux[j], b->fork, 0);
+        int k = 0;
+        for (int s : b->order) {
+            fre_ctx *c = b->slots[s];
+            const cudaStream_t own = c->stream;
+            c->stream = b->aux[k++ % fre_batch::kBranches];
+            fre::ctx_launch_step(c);
+            fre::ctx_launch_step(c);
+            c->stream = own;
+            c->step -= 2;  // captured, not run
+        }
+        for (int j = 0; j < fre_batch::kBranches; ++j) {
+            cudaEventRecord(b->join[j], b->aux[j]);
+            cudaStreamWaitEvent(b->stream, b->join[j], 0);
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
@@ -278,17 +310,17 @@ bool any_local(const fre_batch *b) {
 // Time the candidates on the live slot set: each takes one plain step (so
 // every kernel it uses has run once outside a capture), is captured, and
 // runs 3 graph replays, the last 2 timed -- 7 real steps per candidate.
-constexpr int kTuneSteps = 28;
+constexpr int kTuneSteps = 35;
 fre_status autotune(fre_batch *b, long long *taken) {
     ++b->n_tunes;
-    const int modes[4] = {0, 0, 0, 1};
-    const int bxs[4] = {32, 64, 128, 64};
+    const int modes[5] = {0, 0, 0, 1, 2};
+    const int bxs[5] = {32, 64, 128, 64, 64};
     double best = 1e300;
     int best_k = 1;
     cudaEvent_t e0, e1;
     BCUDA(cudaEventCreate(&e0));
     BCUDA(cudaEventCreate(&e1));
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         b->mode = modes[k];
         b->bx = bxs[k];
         fre_status s = single_step(b);
@@ -515,7 +547,7 @@ fre_status fre_batch_tuning(const fre_batch *b, int *mode, int *bx, double *ms_p
     if (mode) *mode = b->mode;
     if (bx) *bx = b->bx;
     if (ms_per_step)
-        for (int k = 0; k < 4; ++k) ms_per_step[k] = b->tuned_ms[k];
+        for (int k = 0; k < 5; ++k) ms_per_step[k] = b->tuned_ms[k];
     return b->tuned ? FRE_OK : FRE_ERR_STATE;
 }
 
@@ -538,6 +570,13 @@ void fre_batch_destroy(fre_batch *b) {
     if (b->d_bstart) cudaFree(b->d_bstart);
     if (b->d_gstart) cudaFree(b->d_gstart);
     if (b->own_stream) cudaStreamDestroy(b->stream);
+    if (b->fork) {
+        cudaEventDestroy(b->fork);
+        for (int j = 0; j < fre_batch::kBranches; ++j) {
+            cudaStreamDestroy(b->aux[j]);
+            cudaEventDestroy(b->join[j]);
+        }
+    }
     cudaGetLastError();
     delete b;
 }
