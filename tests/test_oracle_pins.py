@@ -483,3 +483,26 @@ def test_brute_force_one_step(orc, lattice, shape):
         g_new[i] = np.roll(post_g[i], shift, axis=(0, 1, 2))
     assert np.abs(fo - f_new).max() < 1e-13
     assert np.abs(go - g_new).max() < 1e-13
+
+
+# ------------------------------------------------- Taylor small deformation
+
+def test_taylor_deformation_golden():
+    """Steady deformation of a droplet in 3D shear at small capillary number,
+    viscosity ratio 1: Taylor's D = (35/32) Ca within 5%, the long axis near
+    45 degrees.  The stored value is the oracle's, written by
+    tests/golden/make_taylor.py (R = 14, R/H = 0.1, Ca = 0.05 with the radius
+    the droplet has at the end)."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_taylor", os.path.join(here, "make_taylor.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    with open(os.path.join(here, "taylor_d3q19.json")) as fh:
+        g = json.load(fh)
+    assert g["case"] == mk.CASE and abs(g["u_wall"] - mk.wall_speed(mk.CASE)) < 1e-15
+    taylor = 35.0 / 32.0 * g["Ca_end"]
+    assert abs(g["D"] - taylor) < 0.05 * taylor, (g["D"], taylor)
+    assert abs(g["theta_deg"] - 45.0) < 3.0
