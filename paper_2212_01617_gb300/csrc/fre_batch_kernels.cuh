@@ -26,12 +26,31 @@ __global__ void __launch_bounds__(256) k_batch(const Launch *__restrict__ cases,
                                                int nslots) {
     using T = typename Fmt<FMT>::T;
     constexpr int BY = 256 / BX;
-    const int slot = batch_slot(start, nslots, blockIdx.x);
-    const Launch &L = cases[slot];
-    const int local = blockIdx.x - __ldg(start + slot);
-    const int nbx = (L.G.nx + BX - 1) / BX, nby = (L.G.ny + BY - 1) / BY;
-    const int bx = local % nbx, t = local / nbx;
-    const int x = bx * BX + (int)(threadIdx.x % BX), y = (t % nby) * BY + (int)(threadIdx.x / BX), z = t / nby;
+    static_assert(sizeof(Launch) % 4 == 0, "descriptor copied in words");
+    // The block's slot, its launch descriptor and the block's corner in that
+    // lattice are found once per block by the first warp and shared: every
+    // thread then reads the descriptor from shared memory and does no
+    // division of its own.
+    __shared__ Launch sL;
+    __shared__ int corner[3];
+    if (threadIdx.x < 32) {
+        const int slot = batch_slot(start, nslots, blockIdx.x);
+        const int *src = reinterpret_cast<const int *>(cases + slot);
+        int *dst = reinterpret_cast<int *>(&sL);
+        for (int k = threadIdx.x; k < (int)(sizeof(Launch) / 4); k += 32) dst[k] = __ldg(src + k);
+        if (threadIdx.x == 0) {
+            const int nx = __ldg(&cases[slot].G.nx), ny = __ldg(&cases[slot].G.ny);
+            const int local = blockIdx.x - __ldg(start + slot);
+            const int nbx = (nx + BX - 1) / BX, nby = (ny + BY - 1) / BY;
+            const int t = local / nbx;
+            corner[0] = (local - t * nbx) * BX;
+            corner[1] = (t % nby) * BY;
+            corner[2] = t / nby;
+        }
+    }
+    __syncthreads();
+    const Launch &L = sL;
+    const int x = corner[0] + (int)(threadIdx.x % BX), y = corner[1] + (int)(threadIdx.x / BX), z = corner[2];
     if (x >= L.G.nx || y >= L.G.ny || z >= L.G.nz) return;
     const Site s = make_site(L.G, x, y, z);
     if (is_solid(L.G, s.n)) return;
