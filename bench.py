@@ -405,6 +405,10 @@ def _batch_workload(args, fre, cases, nodes, stream):
                            "ms_per_step": ms_seq / args.steps,
                            "what": "one context per case, each stepped on its own kernels"},
             "speedup_vs_sequential": ms_seq / ms_batch,
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": measured_peak_gbs()[0],
+                         "achieved": 144.0 * nodes / (ms_batch / args.steps * 1e-3) / 1e9,
+                         "frac": 144.0 * nodes / (ms_batch / args.steps * 1e-3) / 1e9 / measured_peak_gbs()[0],
+                         "what": "whole batch step, algorithmic 144 B per D2Q9 FP32 node update"},
             "tuning": {"mode": mode, "bx": tuning["bx"],
                        "ms_per_step_candidates": dict(zip(["batched bx32", "batched bx64", "batched bx128",
                                                            "per-slot", "per-slot concurrent"],
