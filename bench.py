@@ -137,14 +137,19 @@ class Clocks:
 
 
 def dist_setup():
+    """Ranks of a torchrun launch (one replica per GPU; NCCL on GPUs, gloo
+    for the host-only tests of this logic)."""
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return ws, rank, local
@@ -157,13 +162,21 @@ def barrier(ws):
 
 
 def max_over_ranks(ws, x: float) -> float:
+    """The largest of the ranks' values (the slowest rank's time)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(ws: int, nodes: int, steps: int, ms_max: float) -> float:
+    """Whole-job MLUPS of ws independent replicas of `nodes` nodes each, all
+    done in ms_max (the slowest rank's time)."""
+    return ws * nodes * steps / (ms_max * 1e-3) / 1e6
 
 
 def time_steps(fre, precision, steps, warmup, ws, local):
@@ -569,7 +582,7 @@ def main():
     main_prec = precisions[0]
     r = runs[main_prec]
     n = r["n"]
-    value = ws * n * args.steps / (r["ms"] * 1e-3) / 1e6
+    value = weak_scaling_value(ws, n, args.steps, r["ms"])
     peak, peak_src = measured_peak_gbs()
     t_upd = r["ms_update"] / args.steps * 1e-3
     achieved = ALG_BYTES[main_prec] * n / t_upd / 1e9
