@@ -60,7 +60,7 @@ def compare_fields(sim, o, tol, fields=FIELDS):
     return errs
 
 
-@pytest.mark.parametrize("steps", [0, 1, 500])
+@pytest.mark.parametrize("steps", [0, 1, 500, 2000])
 def test_c0_d2q9_fp64_shear_droplet(fre, orc, steps):
     """D2Q9 FP64, 100x50 shear channel, walls at +-0.01, droplet R = 10."""
     sim, o = pair(fre, orc, "d2q9", "shear", 100, 50, 1, u_wall=0.01)
@@ -148,6 +148,27 @@ def test_fp32_vs_fp64_oracle_d3q19(fre, orc):
                   tau_g=2.0, gamma_mob=0.5)
     sim.init_droplet(19.5, 11.5, 9.5, 6.0)
     o.init_droplet(19.5, 11.5, 9.5, 6.0)
+    sim.step(500)
+    o.step(500)
+    compare_fields(sim, o, 1e-5)
+    sim.close()
+
+
+@pytest.mark.parametrize("ca", [0.1, 0.42])
+def test_c1_d3q19_fp32_vs_fp64_oracle(fre, orc, ca):
+    """The 128x64x64 D3Q19 shear case, droplet R = 16, tau = 2, A = kappa =
+    0.04: u_w = Ca sigma H / (2 mu R) sets the capillary number, Gamma the
+    Peclet number 0.43 (M = rate R xi / (Pe A), Gamma = M / (tau_g - 1/2)).
+    FP32 storage and arithmetic (the row kernels) after 500 steps: 1e-5
+    relative L-inf on rho, u and phi against the FP64 oracle."""
+    sigma = (8 * 0.04 * 0.04 / 9) ** 0.5
+    uw = ca * sigma * 64 / (2 * 0.5 * 16)
+    gamma = (2 * uw / 64) * 16 / (0.43 * 0.04) / 1.5
+    sim, o = pair(fre, orc, "d3q19", "shear", 128, 64, 64, precision="fp32", u_wall=uw, tau_f=2.0,
+                  tau_g=2.0, gamma_mob=gamma)
+    assert sim.row_kernels
+    sim.init_droplet(63.5, 31.5, 31.5, 16.0)
+    o.init_droplet(63.5, 31.5, 31.5, 16.0)
     sim.step(500)
     o.step(500)
     compare_fields(sim, o, 1e-5)
