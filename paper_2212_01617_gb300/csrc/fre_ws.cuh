@@ -800,28 +800,15 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 }
 
                 // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
-                // over opposite pairs: sums f_i + f_opp(i) for the zeroth
-                // moments, differences for the first, in three interleaved
-                // partial sums each (short dependency chains)
-                float2 sfp[3] = {f[0], p2(0.f), p2(0.f)}, php[3] = {g[0], p2(0.f), p2(0.f)};
-                float2 jxp[2] = {p2(0.f), p2(0.f)}, jyp[2] = {p2(0.f), p2(0.f)}, jzp[2] = {p2(0.f), p2(0.f)};
-                {
-                    int kp = 0;
+                float2 sf = f[0], ph = g[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
 #pragma unroll
-                    for (int i = 1; i < Q; ++i) {
-                        if (Lat<Q>::opp(i) < i) continue;
-                        const int j = Lat<Q>::opp(i);
-                        const float2 fs = add2(f[i], f[j]), fd = sub2(f[i], f[j]);
-                        sfp[kp % 3] = add2(sfp[kp % 3], fs);
-                        php[kp % 3] = add2(php[kp % 3], add2(g[i], g[j]));
-                        jxp[kp & 1] = acc_c(jxp[kp & 1], fd, Lat<Q>::cx(i));
-                        jyp[kp & 1] = acc_c(jyp[kp & 1], fd, Lat<Q>::cy(i));
-                        jzp[kp & 1] = acc_c(jzp[kp & 1], fd, Lat<Q>::cz(i));
-                        ++kp;
-                    }
+                for (int i = 1; i < Q; ++i) {
+                    sf = add2(sf, f[i]);
+                    ph = add2(ph, g[i]);
+                    jx = acc_c(jx, f[i], Lat<Q>::cx(i));
+                    jy = acc_c(jy, f[i], Lat<Q>::cy(i));
+                    jz = acc_c(jz, f[i], Lat<Q>::cz(i));
                 }
-                const float2 sf = add2(add2(sfp[0], sfp[1]), sfp[2]), ph = add2(add2(php[0], php[1]), php[2]);
-                const float2 jx = add2(jxp[0], jxp[1]), jy = add2(jyp[0], jyp[1]), jz = add2(jzp[0], jzp[1]);
                 // sf is rho, or rho - rho0 for deviations: in both cases the
                 // density term of omega (f_eq_i [- w_i rho0])
                 const float2 rho = DEV ? add2(sf, p2(rho0)) : sf;
