@@ -77,8 +77,7 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
         s.buf_bytes = (size_t)s.q * plane + (size_t)(s.q - 1) * plane + (size_t)s.np * 4;
     }
     s.field_bytes = (size_t)s.np * s.sz_comp;
-    // roller ids, then the near-solid flags
-    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? 2 * (size_t)(s.np) : 0;
+    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) : 0;
     return true;
 }
 
@@ -104,8 +103,7 @@ fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
 
 // Four-roller geometry: roller id of every node and the solid nodes that
 // have a fluid stencil neighbour.
-void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<unsigned char> &near,
-                   std::vector<int> &ghost) {
+void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<int> &ghost) {
     const fre_params &p = c->p;
     fre::Geo &G = c->G;
     const double cx = 0.5 * (p.nx - 1), cy = 0.5 * (p.ny - 1);
@@ -155,26 +153,6 @@ void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<un
                     }
                 }
             }
-    // near-solid flags: 1 solid, 2 fluid with a solid lattice neighbour
-    near.assign((size_t)G.n, 0);
-    for (int z = 0; z < p.nz; ++z)
-        for (int y = 0; y < p.ny; ++y)
-            for (int x = 0; x < p.nx; ++x) {
-                size_t n = ((size_t)z * p.ny + y) * p.nx + x;
-                if (solid[n]) {
-                    near[n] = 1;
-                    continue;
-                }
-                for (int j = 1; j < q; ++j) {
-                    const int *cj = q == 9 ? c9[j] : c19[j];
-                    size_t m = ((size_t)wrap(z + cj[2], p.nz) * p.ny + wrap(y + cj[1], p.ny)) * p.nx +
-                               wrap(x + cj[0], p.nx);
-                    if (solid[m]) {
-                        near[n] = 2;
-                        break;
-                    }
-                }
-            }
 }
 
 }  // namespace
@@ -207,9 +185,7 @@ void fre::ctx_launch_step(fre_ctx *c) {
     const bool pull = !c->local;
     if (c->fullrow) {
         c->ks->phi_fullrow(L, pull);
-        if (c->n_ghost) c->ks->ghost(L, L.phi);
         c->ks->mu_fullrow(L);
-        if (c->n_ghost) c->ks->ghost(L, L.mu);
         c->ks->update_fullrow(L, pull);
     } else if (c->rows) {
         c->ks->phi_rows(L, pull);
@@ -399,18 +375,15 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
         return bail(fail(FRE_ERR_OOM, "cudaMallocHost failed"));
     }
     if (p->device == FRE_FOUR_ROLLER) {
-        std::vector<unsigned char> solid, near;
+        std::vector<unsigned char> solid;
         std::vector<int> ghost;
-        build_rollers(c, solid, near, ghost);
+        build_rollers(c, solid, ghost);
         void *d;
         fre_status st = dev_alloc(c, &d, s.solid_bytes);
         if (st != FRE_OK) return bail(st);
         c->solid = static_cast<unsigned char *>(d);
-        c->nearsolid = c->solid + s.np;
         if (cudaMemcpyAsync(c->solid, solid.data(), solid.size(), cudaMemcpyHostToDevice, c->stream) !=
-                cudaSuccess ||
-            cudaMemcpyAsync(c->nearsolid, near.data(), near.size(), cudaMemcpyHostToDevice, c->stream) !=
-                cudaSuccess)
+            cudaSuccess)
             return bail(fail(FRE_ERR_CUDA, "upload of the roller mask failed"));
         c->n_ghost = (int)ghost.size();
         if (c->n_ghost) {
@@ -425,14 +398,13 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
             return bail(fail(FRE_ERR_CUDA, "geometry upload: %s", cudaGetErrorString(cudaGetLastError())));
     }
     c->G.solid = c->solid;
-    c->G.nearsolid = c->nearsolid;
     if (!(p->flags & FRE_FLAG_GENERIC_KERNELS) && c->ks->row_width) {
         const unsigned sh = (p->flags >> FRE_FLAG_CHUNK_SHIFT) & 0xffu;
         c->row_w = c->ks->row_width(c->G, sh ? (1 << sh) : 0);
         c->rows = c->row_w > 0;
     }
-    c->fullrow = !(p->flags & FRE_FLAG_GENERIC_KERNELS) && !(p->flags & FRE_FLAG_CHUNKED_UPDATE) &&
-                 c->ks->fullrow_usable && c->ks->fullrow_usable(c->G);
+    c->fullrow = c->rows && !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable &&
+                 c->ks->fullrow_usable(c->G);
     cudaGetLastError();
     *out = c;
     return FRE_OK;
@@ -641,7 +613,7 @@ fre_status fre_observables(fre_ctx *c, fre_obs *out) {
 
 long long fre_step_count(const fre_ctx *c) { return c ? c->step : -1; }
 
-int fre_uses_row_kernels(const fre_ctx *c) { return c && (c->rows || c->fullrow) ? 1 : 0; }
+int fre_uses_row_kernels(const fre_ctx *c) { return c && c->rows ? 1 : 0; }
 
 int fre_kernel_path(const fre_ctx *c) { return !c ? -1 : (c->fullrow ? 2 : (c->rows ? 1 : 0)); }
 

@@ -19,7 +19,6 @@ struct fre_ctx {
     void *phi[2]{};
     void *mu = nullptr;
     unsigned char *solid = nullptr;
-    unsigned char *nearsolid = nullptr;
     int *ghost = nullptr;
     int n_ghost = 0;
     double *red = nullptr;

@@ -17,9 +17,6 @@ struct Geo {
     long long n;              // nodes
     long long np;             // plane stride of the population arrays (elements)
     const unsigned char *solid;  // roller id per node (0 = fluid); four-roller only
-    // four-roller only: 1 on solid nodes, 2 on fluid nodes with a solid
-    // lattice neighbour (links that bounce back), else 0
-    const unsigned char *nearsolid;
     double rcx[5], rcy[5], om[5];  // roller centres and angular velocities (1..4)
     double uwall;             // shear wall speed
 };

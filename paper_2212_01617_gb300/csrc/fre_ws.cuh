@@ -537,91 +537,6 @@ __host__ __device__ constexpr unsigned cy_mask(int sy) {
     return m;
 }
 
-// ---- four-roller device in the row kernels
-// Near-solid flags of the node pair (x, x + 1) starting at node offset off,
-// low byte x: 0 plain fluid, 1 solid, 2 fluid with a solid lattice
-// neighbour; 0 on the other devices.
-__device__ __forceinline__ unsigned pair_flags(const Geo &G, size_t off) {
-    if (G.device != FRE_FOUR_ROLLER) return 0u;
-    return *reinterpret_cast<const unsigned short *>(G.nearsolid + off);
-}
-// bit t set when node x + t of a flagged pair is fluid
-__device__ __forceinline__ unsigned fluid_mask(unsigned fl) {
-    return ((fl & 0xffu) != 1u ? 1u : 0u) | (((fl >> 8) & 0xffu) != 1u ? 2u : 0u);
-}
-// store the nodes of a pair selected by mask m (3: both); returns the
-// values as stored
-__device__ __forceinline__ float2 put_pair(float *p, float2 v, unsigned m) {
-    if (m == 3u) {
-        *reinterpret_cast<float2 *>(p) = v;
-    } else {
-        if (m & 1u) p[0] = v.x;
-        if (m & 2u) p[1] = v.y;
-    }
-    return v;
-}
-__device__ __forceinline__ float2 put_pair(__half *p, float2 v, unsigned m) {
-    const __half2 h = __float22half2_rn(v);
-    if (m == 3u) {
-        *reinterpret_cast<__half2 *>(p) = h;
-    } else {
-        if (m & 1u) p[0] = __low2half(h);
-        if (m & 2u) p[1] = __high2half(h);
-    }
-    return __half22float2(h);
-}
-__device__ __forceinline__ float2 put_pair(__nv_bfloat16 *p, float2 v, unsigned m) {
-    const __nv_bfloat162 h = __float22bfloat162_rn(v);
-    if (m == 3u) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = h;
-    } else {
-        if (m & 1u) p[0] = __low2bfloat16(h);
-        if (m & 2u) p[1] = __high2bfloat16(h);
-    }
-    return __bfloat1622float2(h);
-}
-__device__ __forceinline__ void set_comp(float2 &v, int t, float a) {
-    if (t) v.y = a;
-    else v.x = a;
-}
-__device__ __forceinline__ float get_comp(const float2 &v, int t) { return t ? v.y : v.x; }
-// Post-collision population o at node n of the source buffer, as the row
-// kernels hold it (16-bit f as a deviation from w_o rho0).
-template <int Q, int FMT>
-__device__ __forceinline__ float src_f(const Launch &L, int o, int n) {
-    using S = typename Fmt<FMT>::S;
-    return to_f(static_cast<const S *>(L.src.f)[(size_t)o * L.G.np + n]);
-}
-template <int Q, int FMT>
-__device__ __forceinline__ float src_g(const Launch &L, int o, int n) {
-    using S = typename Fmt<FMT>::S;
-    if constexpr (Fmt<FMT>::DEV) {
-        if (o == 0) return L.src.g0[n];
-        return to_f(static_cast<const S *>(L.src.g)[(size_t)(o - 1) * L.G.np + n]);
-    } else {
-        return static_cast<const S *>(L.src.g)[(size_t)o * L.G.np + n];
-    }
-}
-// Links of a fluid node x + t next to a roller whose source is solid:
-// half-way bounce-back from the node's own opposite population plus the
-// moving-wall term of the roller at the wall point (the per-node rule of
-// pull_source); the pulled values of the other links stay.
-template <int Q, int FMT, bool WANT_F>
-__device__ __forceinline__ void roller_links(const Launch &L, int x, int y, int z, int t, float rho0,
-                                             const float *__restrict__ php, float2 *f, float2 *g) {
-    const Site st = make_site(L.G, x, y, z);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        float uwx = 0.f, uwy = 0.f;
-        if (pull_source<Q, float>(L.G, st, i, uwx, uwy) >= 0) continue;
-        const int o = Lat<Q>::opp(i);
-        const float cu = float(Lat<Q>::cx(i)) * uwx + float(Lat<Q>::cy(i)) * uwy;
-        const float w2 = float(2.0 * Lat<Q>::w(i) * 3.0);
-        if (WANT_F) set_comp(f[i], t, src_f<Q, FMT>(L, o, st.n) + w2 * rho0 * cu);
-        set_comp(g[i], t, src_g<Q, FMT>(L, o, st.n) + w2 * php[st.n] * cu);
-    }
-}
-
 // NXC: the row length as a compile-time constant (every shared-memory
 // offset then folds into the instruction), or 0 to take it from the launch.
 template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC>
@@ -765,12 +680,11 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
 
         if constexpr (KIND == WS_PHI) {
             float2 out[R];
-            unsigned msk[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const unsigned wall = wall_s[s][r];
                 const size_t row = ((size_t)z * ny + y0 + r) * nx;
-                float2 gvs[Q];
+                float2 sum = p2(0.f);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const bool wl = PULL && ((wall >> i) & 1u);
@@ -783,25 +697,15 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                         const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
                         gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
                     }
-                    gvs[i] = gv;
+                    sum = add2(sum, gv);
                 }
-                const unsigned fl = pair_flags(L.G, row + x0);
-                if (PULL && fl) {
-                    for (int t = 0; t < 2; ++t)
-                        if (((fl >> (8 * t)) & 0xffu) == 2u)
-                            roller_links<Q, FMT, false>(L, x0 + t, y0 + r, z, t, rho0, php, nullptr, gvs);
-                }
-                float2 sum = gvs[0];
-#pragma unroll
-                for (int i = 1; i < Q; ++i) sum = add2(sum, gvs[i]);
                 out[r] = sum;
-                msk[r] = fl ? fluid_mask(fl) : 3u;
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                put_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + r) * nx + x0, out[r], msk[r]);
+                st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
         } else if constexpr (KIND == WS_MU) {
             float2 out[R];
 #pragma unroll
@@ -824,11 +728,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const size_t off = ((size_t)z * ny + y0 + r) * nx + x0;
-                const unsigned fl = pair_flags(L.G, off);
-                put_pair(static_cast<float *>(L.mu) + off, out[r], fl ? fluid_mask(fl) : 3u);
-            }
+            for (int r = 0; r < R; ++r)
+                st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
         } else {
             // ---------------------------------------------------- update
             const float *__restrict__ phif = static_cast<const float *>(L.phi);
@@ -862,15 +763,6 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                     }
                     f[i] = fv;
                     g[i] = gv;
-                }
-                // four-roller: links of fluid nodes next to a roller bounce
-                // back; solid nodes of the pair are computed but not stored
-                const unsigned fl = pair_flags(L.G, row + x0);
-                const unsigned msk = fl ? fluid_mask(fl) : 3u;
-                if (PULL && fl) {
-                    for (int t = 0; t < 2; ++t)
-                        if (((fl >> (8 * t)) & 0xffu) == 2u)
-                            roller_links<Q, FMT, true>(L, x0 + t, y, z, t, rho0, php, f, g);
                 }
                 float2 gpx = p2(0.f), gpy = p2(0.f), gpz = p2(0.f), gqx = p2(0.f), gqy = p2(0.f), gqz = p2(0.f);
 #pragma unroll
@@ -941,7 +833,7 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 {
                     const float w0 = float(Lat<Q>::w(0));
                     // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F
-                    put_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), mul2(p2(kf * w0), m3uF))), msk);
+                    st_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), mul2(p2(kf * w0), m3uF))));
                 }
                 // moving populations in opposite pairs (i, opp(i)): the
                 // equilibria and the Guo term split into parts even and odd
@@ -969,21 +861,21 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                     const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
                     const float2 Bg = mul2(mul2(wg, ph), cu3);
                     const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
-                    put_pair(fp + (size_t)i * np, fi, msk);
-                    put_pair(fp + (size_t)j * np, fj, msk);
+                    st_pair(fp + (size_t)i * np, fi);
+                    st_pair(fp + (size_t)j * np, fj);
                     if constexpr (DEV) {
                         // the rest population of g closes sum_i g*_i = phi on
                         // the values as they are stored
-                        gsum = add2(gsum, add2(put_pair(gp + (size_t)(i - 1) * np, gi, msk),
-                                               put_pair(gp + (size_t)(j - 1) * np, gj, msk)));
+                        gsum = add2(gsum, add2(st_pair(gp + (size_t)(i - 1) * np, gi),
+                                               st_pair(gp + (size_t)(j - 1) * np, gj)));
                     } else {
-                        put_pair(gp + (size_t)i * np, gi, msk);
-                        put_pair(gp + (size_t)j * np, gj, msk);
+                        st_pair(gp + (size_t)i * np, gi);
+                        st_pair(gp + (size_t)j * np, gj);
                         gsum = add2(gsum, add2(gi, gj));
                     }
                 }
-                if constexpr (DEV) put_pair(L.dst.g0 + off, sub2(ph, gsum), msk);
-                else put_pair(gp, sub2(ph, gsum), msk);
+                if constexpr (DEV) st_pair(L.dst.g0 + off, sub2(ph, gsum));
+                else st_pair(gp, sub2(ph, gsum));
             }
         }
     }
@@ -1012,6 +904,7 @@ struct WsRowLaunchers {
         return nst<KIND, 2>(G.nx) >= 2 ? 2 : 1;
     }
     static bool usable(const Geo &G) {
+        if (G.device == FRE_FOUR_ROLLER) return false;
         if ((G.np * sizeof(S)) % 16 != 0 || (G.nx * sizeof(S)) % 16 != 0 || (G.nx * 4) % 16 != 0) return false;
         if (G.nx < 64 || G.nx > 512 || G.nx % 64 != 0) return false;
         return nst<WS_UPDATE, 1>(G.nx) >= 2 && nst<WS_PHI, 1>(G.nx) >= 1 && nst<WS_MU, 1>(G.nx) >= 1;

@@ -41,9 +41,6 @@ CASES = [
     ("d3q19", "shear", 512, 6, 4, dict(u_wall=0.02, tau_f=1.2)),
     # odd ny: one row per work unit in every format
     ("d2q9", "shear", 128, 37, 1, dict(u_wall=0.02)),
-    # four rollers: links from roller nodes bounce back inside the row kernels
-    ("d3q19", "four_roller", 64, 64, 6, dict(u_wall=0.02, tau_f=1.2)),
-    ("d2q9", "four_roller", 128, 128, 1, dict(u_wall=0.02)),
 ]
 
 
@@ -71,10 +68,9 @@ def test_row_kernels_match_per_node_kernels(fre, orc, case, precision):
     assert rows.row_kernels and not gen.row_kernels
     a = dict(tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0, rho0=1.0)
     a.update(kw)
-    o = orc.Oracle({"d2q9": 0, "d3q19": 1}[lattice], {"shear": 0, "four_roller": 1, "periodic": 2}[device], nx, ny, nz,
+    o = orc.Oracle({"d2q9": 0, "d3q19": 1}[lattice], {"shear": 0, "periodic": 2}[device], nx, ny, nz,
                    a["tau_f"], a["tau_g"], a["A"], a["kappa"], a["gamma_mob"], a["u_wall"], a["rho0"])
-    # (a droplet clear of the rollers in the four-roller device)
-    c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, min(nx, ny) / (8 if device == "four_roller" else 4))
+    c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, min(nx, ny) / 4)
     for s in (rows, gen, o):
         s.init_droplet(*c)
         s.step(200)
