@@ -899,7 +899,10 @@ struct WsRowLaunchers {
     // two rows per unit where a staged row is shorter than 2 KB
     template <int KIND>
     static int rows_per_unit(const Geo &G, bool pull) {
-        if (KIND == WS_MU || !pull || G.ny % 2 != 0) return 1;
+        // the mu pass stages three copies per unit whatever R: four rows per
+        // unit keep it off the copy engine's rate of operations
+        if (KIND == WS_MU) return G.ny % 4 == 0 ? 4 : (G.ny % 2 == 0 ? 2 : 1);
+        if (!pull || G.ny % 2 != 0) return 1;
         if (RowsLayout<Q, FMT, KIND, 1>::rowb(G.nx) >= 2048) return 1;
         return nst<KIND, 2>(G.nx) >= 2 ? 2 : 1;
     }
@@ -941,7 +944,13 @@ struct WsRowLaunchers {
     }
     template <int KIND, bool PULL>
     static void run(const Launch &L) {
-        if constexpr (PULL && KIND != WS_MU) {
+        if constexpr (KIND == WS_MU) {
+            const int r = rows_per_unit<KIND>(L.G, PULL);
+            if (r == 4) run_r<KIND, PULL, 4>(L);
+            else if (r == 2) run_r<KIND, PULL, 2>(L);
+            else run_r<KIND, PULL, 1>(L);
+            return;
+        } else if constexpr (PULL) {
             if (rows_per_unit<KIND>(L.G, PULL) == 2) {
                 run_r<KIND, PULL, 2>(L);
                 return;
