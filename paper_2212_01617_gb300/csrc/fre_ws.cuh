@@ -370,8 +370,8 @@ struct WsLaunchers {
             attr = true;
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
         }
-        const int g = std::min(nu, PipeLaunchers<Q, FMT>::sms() *
-                                       PipeLaunchers<Q, FMT>::blocks_per_sm((const void *)fn, W + 32, smem));
+        const int g = std::min(nu, LaunchShape::sms() *
+                                       LaunchShape::blocks_per_sm((const void *)fn, W + 32, smem));
         fn<<<g, W + 32, smem, L.stream>>>(L, W, nu);
     }
     template <int KIND, bool PULL>
@@ -926,8 +926,8 @@ struct WsRowLaunchers {
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         }
         const int threads = nx / 2 + 32;
-        const int g = std::min(nu, PipeLaunchers<Q, FMT>::sms() *
-                                       PipeLaunchers<Q, FMT>::blocks_per_sm((const void *)fn, threads, smem));
+        const int g = std::min(nu, LaunchShape::sms() *
+                                       LaunchShape::blocks_per_sm((const void *)fn, threads, smem));
         fn<<<g, threads, smem, L.stream>>>(L, nu);
     }
     template <int KIND, bool PULL, int R>
