@@ -63,18 +63,42 @@ __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
     return __float2bfloat16_rn(v);
 }
 
-// Population access for one buffer in a given storage format.
+// Reference state of the 16-bit f formats.  f is stored as the deviation
+// f_i - fr_i(y) from the second-order equilibrium (Eq. feq) of density rho0
+// and velocity (U(y), 0, 0), where U is the plane Couette profile between
+// the shear device's walls, U(y) = u_w (2 (y + 1/2) / ny - 1), and 0 on every
+// other device.  The stored values then carry the departure from the base
+// flow only: a deviation from w_i rho0 alone would spend the 16-bit
+// mantissa on the 3 w_i rho0 c_ix U part of every moving population.
+template <typename T>
+__device__ __forceinline__ T couette_u(const Geo &G, int y) {
+    return G.device == FRE_SHEAR ? T(G.uwall) * (T(2 * y + 1) / T(G.ny) - T(1)) : T(0);
+}
+// U(y + 1) - U(y)
+template <typename T>
+__device__ __forceinline__ T couette_du(const Geo &G) {
+    return G.device == FRE_SHEAR ? T(2.0 * G.uwall / G.ny) : T(0);
+}
+template <int Q, typename T>
+__device__ __forceinline__ T fref(int i, T rho0, T U) {
+    const T cu = T(Lat<Q>::cx(i)) * U;
+    return T(Lat<Q>::w(i)) * rho0 * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * U * U);
+}
+
+// Population access for one buffer in a given storage format.  ldf / stf
+// take rho0 and U of the row of node k (the reference of the 16-bit f
+// formats; unused by the others).
 template <int Q, int FMT>
 struct Pop {
     using S = typename Fmt<FMT>::S;
     using T = typename Fmt<FMT>::T;
 
-    __device__ __forceinline__ static T ldf(const Buf &b, long long np, int i, long long k, T rho0) {
+    __device__ __forceinline__ static T ldf(const Buf &b, long long np, int i, long long k, T rho0, T U) {
         const S *p = static_cast<const S *>(b.f) + (size_t)i * np + k;
         if constexpr (!Fmt<FMT>::DEV) {
             return __ldg(p);
         } else {
-            return to_float(__ldg(p)) + T(Lat<Q>::w(i)) * rho0;
+            return to_float(__ldg(p)) + fref<Q, T>(i, rho0, U);
         }
     }
     __device__ __forceinline__ static T ldg(const Buf &b, long long np, int i, long long k) {
@@ -85,12 +109,12 @@ struct Pop {
             return to_float(__ldg(static_cast<const S *>(b.g) + (size_t)(i - 1) * np + k));
         }
     }
-    __device__ __forceinline__ static void stf(const Buf &b, long long np, int i, long long k, T v, T rho0) {
+    __device__ __forceinline__ static void stf(const Buf &b, long long np, int i, long long k, T v, T rho0, T U) {
         S *p = static_cast<S *>(b.f) + (size_t)i * np + k;
         if constexpr (!Fmt<FMT>::DEV) {
             *p = v;
         } else {
-            *p = from_float<S>(v - T(Lat<Q>::w(i)) * rho0);
+            *p = from_float<S>(v - fref<Q, T>(i, rho0, U));
         }
     }
     __device__ __forceinline__ static void stg(const Buf &b, long long np, int i, long long k, T v) {
@@ -219,25 +243,28 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
     using T = typename Fmt<FMT>::T;
     using P = Pop<Q, FMT>;
     const T rho0 = T(L.P.rho0);
+    // U of this node's row; a pulled population comes from row y - c_iy
+    const T U = Fmt<FMT>::DEV ? couette_u<T>(L.G, s.y) : T(0);
+    const T dU = Fmt<FMT>::DEV ? couette_du<T>(L.G) : T(0);
     const long long np = L.G.np;
     const int n = s.n;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (!PULL || i == 0) {
-            if (WANT_F) f[i] = P::ldf(L.src, np, i, n, rho0);
+            if (WANT_F) f[i] = P::ldf(L.src, np, i, n, rho0, U);
             g[i] = P::ldg(L.src, np, i, n);
             continue;
         }
         T uwx = T(0), uwy = T(0);
         const int src = pull_source<Q, T>(L.G, s, i, uwx, uwy);
         if (src >= 0) {
-            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0);
+            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0, U - T(Lat<Q>::cy(i)) * dU);
             g[i] = P::ldg(L.src, np, i, src);
         } else {
             const int o = Lat<Q>::opp(i);
             const T cu = T(Lat<Q>::cx(i)) * uwx + T(Lat<Q>::cy(i)) * uwy;
             const T wi2 = T(2.0 * Lat<Q>::w(i) * 3.0);
-            if (WANT_F) f[i] = P::ldf(L.src, np, o, n, rho0) + wi2 * rho0 * cu;
+            if (WANT_F) f[i] = P::ldf(L.src, np, o, n, rho0, U) + wi2 * rho0 * cu;
             const T php = static_cast<const T *>(L.phi_prev)[n];
             g[i] = P::ldg(L.src, np, o, n) + wi2 * php * cu;
         }
@@ -387,6 +414,7 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
     const T gmu3 = T(3.0 * L.P.Gamma) * m.mu;
     const T usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     const T uF = m.ux * m.Fx + m.uy * m.Fy + m.uz * m.Fz;
+    const T U = Fmt<FMT>::DEV ? couette_u<T>(L.G, s.y) : T(0);
     T fsum = T(0), gsum = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -403,11 +431,11 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
         const T gs = g[i] - (g[i] - geq) * og;
         fsum += fs;
         gsum += gs;
-        P::stf(L.dst, L.G.np, i, n, fs, T(L.P.rho0));
+        P::stf(L.dst, L.G.np, i, n, fs, T(L.P.rho0), U);
         P::stg(L.dst, L.G.np, i, n, gs);
     }
     // rest populations close the collision invariants: sum f* = rho, sum g* = phi
-    P::stf(L.dst, L.G.np, 0, n, m.rho - fsum, T(L.P.rho0));
+    P::stf(L.dst, L.G.np, 0, n, m.rho - fsum, T(L.P.rho0), U);
     P::stg(L.dst, L.G.np, 0, n, m.phi - gsum);
 }
 
@@ -471,7 +499,7 @@ __global__ void __launch_bounds__(kBlock) k_load_plane(Launch L, int lat_g, int 
     for (int j = 0; j < Q; ++j) {
         if (j != i) continue;
         if (lat_g) P::stg(L.src, L.G.np, j, n, v);
-        else P::stf(L.src, L.G.np, j, n, v, T(L.P.rho0));
+        else P::stf(L.src, L.G.np, j, n, v, T(L.P.rho0), couette_u<T>(L.G, s.y));
     }
 }
 
@@ -505,10 +533,11 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
     const long long N = L.G.n;
     const int n = s.n;
     const T rho0 = T(L.P.rho0);
+    const T U = couette_u<T>(L.G, s.y);
     if (is_solid(L.G, n)) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            P::stf(L.src, L.G.np, i, n, T(0), rho0);
+            P::stf(L.src, L.G.np, i, n, T(0), rho0, U);
             P::stg(L.src, L.G.np, i, n, T(0));
         }
         return;
@@ -521,7 +550,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
         uz = T(L.staging[3 * N + n]);
     } else {
         rho = rho0;
-        ux = (L.G.device == FRE_SHEAR) ? T(L.G.uwall * (2.0 * (s.y + 0.5) / L.G.ny - 1.0)) : T(0);
+        ux = U;
         uy = T(0);
         uz = T(0);
     }
@@ -534,7 +563,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
         const T cu = T(Lat<Q>::cx(i)) * ux + T(Lat<Q>::cy(i)) * uy + T(Lat<Q>::cz(i)) * uz;
         const T poly = T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq;
         const T w = T(Lat<Q>::w(i));
-        P::stf(L.src, L.G.np, i, n, w * rho * (T(1) + poly), rho0);
+        P::stf(L.src, L.G.np, i, n, w * rho * (T(1) + poly), rho0, U);
         if (i > 0) {
             const T ge = w * (T(3.0 * L.P.Gamma) * mu + phi * poly);
             gsum += ge;

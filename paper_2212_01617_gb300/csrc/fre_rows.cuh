@@ -126,22 +126,14 @@ __device__ __forceinline__ RowDesc field_row(const Launch &L, const float *field
 }
 
 // Staged values at local x (-1 <= xl <= W).  fbase / gbase: start of the
-// f / g rows.
+// f / g rows.  f of slot i (a wall slot holds population opp(i)); `ref` is
+// the reference the 16-bit formats add back (the fr_j of the stored row).
 template <int Q, int FMT>
-__device__ __forceinline__ float row_f(const unsigned char *fbase, int W, int i, int xl, float rho0) {
+__device__ __forceinline__ float row_f(const unsigned char *fbase, int W, int i, int xl, float ref) {
     using S = typename Fmt<FMT>::S;
     using CL = ChunkLayout<Q, FMT>;
     const S v = reinterpret_cast<const S *>(fbase + i * CL::rw_s(W))[CL::HS + xl];
-    if constexpr (Fmt<FMT>::DEV) return to_float(v) + float(Lat<Q>::w(i)) * rho0;
-    else return v;
-}
-// raw staged f of slot i (a wall slot holds population opp(i))
-template <int Q, int FMT>
-__device__ __forceinline__ float row_f_slot(const unsigned char *fbase, int W, int i, int xl, float wr) {
-    using S = typename Fmt<FMT>::S;
-    using CL = ChunkLayout<Q, FMT>;
-    const S v = reinterpret_cast<const S *>(fbase + i * CL::rw_s(W))[CL::HS + xl];
-    if constexpr (Fmt<FMT>::DEV) return to_float(v) + wr;
+    if constexpr (Fmt<FMT>::DEV) return to_float(v) + ref;
     else return v;
 }
 template <int Q, int FMT>

@@ -227,6 +227,9 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
             const float kf = float(1.0 - 0.5 / L.P.tau_f);
             const float g3 = float(3.0 * L.P.Gamma);
             constexpr int c0 = stencil_slot<Q>(0, 0);
+            // U of this row; a pulled f_i was stored in row y - c_iy
+            const float U = Fmt<FMT>::DEV ? couette_u<float>(L.G, u.y) : 0.f;
+            const float dU = Fmt<FMT>::DEV ? couette_du<float>(L.G) : 0.f;
             float f[Q], g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -235,13 +238,14 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
                     const float cu = float(Lat<Q>::cx(i)) * uw;
                     const float w2 = float(2.0 * Lat<Q>::w(i) * 3.0);
                     // slot i holds the local row of population opp(i)
-                    const float fo = row_f_slot<Q, FMT>(cur, W, i, xl, float(Lat<Q>::w(Lat<Q>::opp(i))) * rho0);
+                    const float fo = row_f<Q, FMT>(cur, W, i, xl, fref<Q, float>(Lat<Q>::opp(i), rho0, U));
                     const float go = row_g<Q, FMT>(gb, W, i, xl);
                     f[i] = fo + w2 * rho0 * cu;
                     g[i] = go + w2 * php[u.row + u.x0 + xl] * cu;
                 } else {
                     const int xs = PULL ? xl - Lat<Q>::cx(i) : xl;
-                    f[i] = row_f<Q, FMT>(cur, W, i, xs, rho0);
+                    const float Us = PULL ? U - float(Lat<Q>::cy(i)) * dU : U;
+                    f[i] = row_f<Q, FMT>(cur, W, i, xs, fref<Q, float>(i, rho0, Us));
                     g[i] = row_g<Q, FMT>(gb, W, i, xs);
                 }
             }
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if constexpr (Fmt<FMT>::DEV) {
-                    fo[i * W + xl] = from_float<S>(f[i] - float(Lat<Q>::w(i)) * rho0);
+                    fo[i * W + xl] = from_float<S>(f[i] - fref<Q, float>(i, rho0, U));
                     if (i > 0) fo[(Q + i - 1) * W + xl] = from_float<S>(g[i]);
                 } else {
                     fo[i * W + xl] = f[i];
@@ -517,17 +521,6 @@ __device__ __forceinline__ float2 st_pair(__nv_bfloat16 *p, float2 v) {
     return __bfloat1622float2(h);
 }
 
-template <int Q, int FMT>
-__device__ __forceinline__ float fr_g(const unsigned char *gb, int nx, int i, int xs) {
-    using S = typename Fmt<FMT>::S;
-    if constexpr (Fmt<FMT>::DEV) {
-        if (i == 0) return reinterpret_cast<const float *>(gb + (size_t)(Q - 1) * nx * sizeof(S))[xs];
-        return to_float(reinterpret_cast<const S *>(gb)[(size_t)(i - 1) * nx + xs]);
-    } else {
-        return reinterpret_cast<const S *>(gb)[(size_t)i * nx + xs];
-    }
-}
-
 // populations whose c_y has the sign of sy, as a bit mask
 template <int Q>
 __host__ __device__ constexpr unsigned cy_mask(int sy) {
@@ -535,6 +528,77 @@ __host__ __device__ constexpr unsigned cy_mask(int sy) {
     for (int i = 0; i < Q; ++i)
         if (Lat<Q>::cy(i) * sy > 0) m |= 1u << i;
     return m;
+}
+
+// index of the opposite pair (i, opp(i)), i < opp(i), in the order i = 1, 2, ...
+template <int Q>
+__host__ __device__ constexpr int pair_index(int i) {
+    int p = 0;
+    for (int k = 1; k < i; ++k)
+        if (Lat<Q>::opp(k) > k) ++p;
+    return p;
+}
+
+// Per-row constants of the update for the 16-bit f formats, whose stored
+// f is the deviation from the Couette reference fr_i(y) (Eq. feq at rho0
+// and (U(y), 0, 0)).  The update pulls deviations stored against the
+// reference of their source row y - c_iy (or, on a wall link, the local
+// deviation of opp(i)); d_i = d'_i + o_i is then the deviation from this
+// row's reference, and the BGK step on deviations,
+//   d*_i = (1 - omega) d_i + omega (feq_i - fr_i) + F_i,
+// differs from the one on deviations from w_i rho0 by the constant
+//   s_i = (1 - omega) o_i - omega (fr_i - w_i rho0).
+// With a = 4.5 c_ix^2 - 1.5, b = 3 c_ix, fr_i(U) = w_i rho0 (1 + b U + a U^2):
+//   o_i = w_i rho0 (b e + a (2 U + e) e),   e = U(y - c_iy) - U(y);
+//   o_i = w_i rho0 6 c_ix (u_w,i - U)        on a wall link (the local
+//         opp(i) plus the moving-wall term 2 w_i rho0 (c_i . u_w) / cs^2).
+// Entries, each a pair (v, v): 0 sum_i o_i; 1, 2, 3 the momentum rho0 U e_x
+// + sum_i c_i o_i; 4 s_0; 5 unused; 6 + 2p, 7 + 2p the parts of s_i even
+// and odd in c_i of opposite pair p, (s_i + s_opp(i)) / 2 and
+// (s_i - s_opp(i)) / 2.  Lane l of the calling warp takes population l.
+template <int Q, bool PULL>
+__device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *out, int lane) {
+    const bool shear = L.G.device == FRE_SHEAR;
+    const float rho0 = float(L.P.rho0), om = float(1.0 / L.P.tau_f);
+    const float U = couette_u<float>(L.G, y), dU = couette_du<float>(L.G);
+    const int i = lane < Q ? lane : 0;
+    const int ciy = Lat<Q>::cy(i);
+    const float cx = float(Lat<Q>::cx(i)), cy = float(ciy), cz = float(Lat<Q>::cz(i));
+    const float wr = lane < Q ? float(Lat<Q>::w(i)) * rho0 : 0.f;
+    const float a = 4.5f * cx * cx - 1.5f, b = 3.f * cx;
+    float o = 0.f;
+    if (PULL) {
+        if (shear && ((y == 0 && ciy > 0) || (y == L.G.ny - 1 && ciy < 0))) {
+            const float uwl = ciy > 0 ? float(-L.G.uwall) : float(L.G.uwall);
+            o = wr * 6.f * cx * (uwl - U);
+        } else {
+            const float e = -cy * dU;
+            o = wr * (b * e + a * (2.f * U + e) * e);
+        }
+    }
+    const float si = (1.f - om) * o - om * wr * (b * U + a * U * U);
+    float so = o, sx = cx * o, sy = cy * o, sz = cz * o;
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        so += __shfl_xor_sync(0xffffffffu, so, m);
+        sx += __shfl_xor_sync(0xffffffffu, sx, m);
+        sy += __shfl_xor_sync(0xffffffffu, sy, m);
+        sz += __shfl_xor_sync(0xffffffffu, sz, m);
+    }
+    const float sj = __shfl_sync(0xffffffffu, si, lane < Q ? Lat<Q>::opp(i) : lane);
+    if (lane == 0) {
+        out[0] = make_float2(so, so);
+        out[1] = make_float2(rho0 * U + sx, rho0 * U + sx);
+        out[2] = make_float2(sy, sy);
+        out[3] = make_float2(sz, sz);
+        out[4] = make_float2(si, si);
+        out[5] = make_float2(0.f, 0.f);
+    } else if (lane < Q && Lat<Q>::opp(i) > i) {
+        const int p = pair_index<Q>(i);
+        const float e = 0.5f * (si + sj), d = 0.5f * (si - sj);
+        out[6 + 2 * p] = make_float2(e, e);
+        out[7 + 2 * p] = make_float2(d, d);
+    }
 }
 
 // NXC: the row length as a compile-time constant (every shared-memory
@@ -547,6 +611,13 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NST], empty[NST];
     __shared__ unsigned wall_s[NST][R];
+    // per-row constants of the 16-bit update (couette_consts): a ring of
+    // NST + 1 slots, since a consumer warp still reads those of unit k after
+    // it has released the stage of unit k, until the producer may refill
+    // the stage with unit k + NST
+    constexpr bool CST = DEV && KIND == WS_UPDATE;
+    constexpr int NCST = CST ? 6 + (Q - 1) : 2;
+    __shared__ __align__(16) float2 cst_s[CST ? NST + 1 : 1][R][NCST];
     const int nx = NXC ? NXC : L.G.nx;
     const int ny = L.G.ny, nz = L.G.nz;
     const int nyu = ny / R;  // units per z plane
@@ -591,7 +662,9 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                     wall_s[s][r] = (PULL && shear) ? ((y0 + r == 0 ? cy_mask<Q>(1) : 0u) |
                                                       (y0 + r == ny - 1 ? cy_mask<Q>(-1) : 0u))
                                                    : 0u;
-                mbar_expect(bar, FL::tx_bytes(nx));
+                // the 16-bit update arrives once its row constants are in place
+                if (CST) mbar_expect_tx(bar, FL::tx_bytes(nx));
+                else mbar_expect(bar, FL::tx_bytes(nx));
             }
             __syncwarp();
             for (int gi = lane; gi < FL::ngroups(); gi += 32) {
@@ -655,6 +728,12 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                         bulk_load(buf + smrow(r), plane(pi) + ((size_t)zr * ny + ys) * nx * esz, rb, bar);
                     }
                 }
+            }
+            if constexpr (CST) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) couette_consts<Q, PULL>(L, y0 + r, cst_s[k % (NST + 1)][r], lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar);
             }
         }
         return;
@@ -742,8 +821,9 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 const int y = y0 + r;
                 const size_t row = ((size_t)z * ny + y) * nx;
                 const Site st = make_site(L.G, x0, y, z);
-                // ---- read phase: pulled populations (16-bit f as deviations
-                // f_i - w_i rho0), then the stencil values of phi and mu
+                // ---- read phase: pulled populations (16-bit f: deviations
+                // from the reference of the row they were stored in), then
+                // the stencil values of phi and mu
                 float2 f[Q], g[Q];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
@@ -758,7 +838,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                         // term 2 w_i a (c_i . u_w) / cs^2
                         const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
                         const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
-                        fv = add2(fv, p2(w2cu * rho0));
+                        // (16-bit f: the wall term is part of the row constants)
+                        if constexpr (!DEV) fv = add2(fv, p2(w2cu * rho0));
                         gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
                     }
                     f[i] = fv;
@@ -801,6 +882,15 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
 
                 // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
                 float2 sf = f[0], ph = g[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
+                // 16-bit f: row constants (offsets o_i summed into the moments)
+                const float4 *cst = reinterpret_cast<const float4 *>(cst_s[CST ? k % (NST + 1) : 0][r]);
+                if constexpr (CST) {
+                    const float4 c01 = cst[0], c23 = cst[1];
+                    sf = add2(sf, make_float2(c01.x, c01.y));
+                    jx = make_float2(c01.z, c01.w);
+                    jy = make_float2(c23.x, c23.y);
+                    jz = make_float2(c23.z, c23.w);
+                }
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     sf = add2(sf, f[i]);
@@ -832,8 +922,10 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 S *gp = static_cast<S *>(L.dst.g) + off;
                 {
                     const float w0 = float(Lat<Q>::w(0));
-                    // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F
-                    st_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), mul2(p2(kf * w0), m3uF))));
+                    // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F [+ s_0]
+                    const float2 S0 = CST ? fma2(p2(kf * w0), m3uF, make_float2(cst[2].x, cst[2].y))
+                                          : mul2(p2(kf * w0), m3uF);
+                    st_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), S0)));
                 }
                 // moving populations in opposite pairs (i, opp(i)): the
                 // equilibria and the Guo term split into parts even and odd
@@ -854,8 +946,17 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                     const float2 cu3 = mul2(p2(3.f), cu);
                     const float2 E = fma2(mul2(p2(1.5f), cu3), cu, m15usq);  // 4.5 cu^2 - 1.5 u^2
                     const float2 wr = p2(of * w);
-                    const float2 Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), fma2(mul2(p2(3.f), cu3), cF, m3uF)));
-                    const float2 Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
+                    const float2 GA = fma2(mul2(p2(3.f), cu3), cF, m3uF);
+                    float2 Af, Bf;
+                    if constexpr (CST) {
+                        // even and odd parts of the row constants s_i, s_j
+                        const float4 cab = cst[3 + pair_index<Q>(i)];
+                        Af = fma2(wr, fma2(rho, E, sf), fma2(p2(kf * w), GA, make_float2(cab.x, cab.y)));
+                        Bf = fma2(mul2(wr, rho), cu3, fma2(p2(3.f * kf * w), cF, make_float2(cab.z, cab.w)));
+                    } else {
+                        Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), GA));
+                        Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
+                    }
                     const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
                     const float2 wg = p2(og * w);
                     const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
