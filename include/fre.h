@@ -116,8 +116,8 @@ typedef struct {
     double D;            /* deformation (L - B)/(L + B) of the x-y moment ellipse */
     double theta_deg;    /* inclination of its long axis to x, degrees */
     double p_centre;     /* cs^2 rho + phi mu - (A/4)(phi^2 - 1)^2 at the
-                            node nearest the centroid */
-    double p_far;        /* same at the node half a period away in x (and z) */
+                            centroid (trilinear interpolation of the nodes) */
+    double p_far;        /* same half a period away in x (and z) */
     double dp;           /* p_centre - p_far (Laplace pressure) */
     double max_u;        /* max |u| */
     long long step;      /* time steps taken since the last initialisation */

@@ -611,6 +611,36 @@ static double pressure(const orc_state *s, long long n)
     return CS2 * s->rho[n] + ph * s->mu[n] - psi;
 }
 
+/* Pressure at the point (X, Y, Z) by trilinear interpolation of the nodal
+ * pressure: periodic in x and z, and in y off the shear device (whose y is
+ * clamped to the fluid rows); solid nodes carry no weight.  The Laplace
+ * law (Sec. 3) compares the pressure inside and outside a droplet; read at
+ * the node nearest the centroid, a droplet centred on a cell face would
+ * switch nodes under any rounding of its centroid. */
+static double pressure_interp(const orc_state *s, double X, double Y, double Z)
+{
+    int x0 = (int)floor(X), y0 = (int)floor(Y), z0 = (int)floor(Z);
+    double fx = X - x0, fy = Y - y0, fz = Z - z0;
+    double acc = 0.0, wsum = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        double w = (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy) * (dz ? fz : 1.0 - fz);
+        if (w == 0.0) continue;
+        int x = wrap(x0 + dx, s->p.nx), z = wrap(z0 + dz, s->p.nz), y = y0 + dy;
+        if (s->p.device == ORC_SHEAR) {
+            if (y < 0) y = 0;
+            if (y >= s->p.ny) y = s->p.ny - 1;
+        } else {
+            y = wrap(y, s->p.ny);
+        }
+        long long n = node(s, x, y, z);
+        if (s->solid[n]) continue;
+        acc += w * pressure(s, n);
+        wsum += w;
+    }
+    return wsum > 0.0 ? acc / wsum : 0.0;
+}
+
 int orc_observables(orc_state *s, orc_obs *o)
 {
     if (!s || !o) return -1;
@@ -675,18 +705,10 @@ int orc_observables(orc_state *s, orc_obs *o)
         double s1 = sqrt(l1), s2 = sqrt(l2);
         o->D = (s1 + s2) > 0.0 ? (s1 - s2) / (s1 + s2) : 0.0;
         o->theta_deg = 0.5 * atan2(2.0 * c, a - b) * 180.0 / M_PI;
-        /* Laplace pressure: node nearest the centroid vs the node half a
-         * period away in x (and z) */
-        int cx = wrap((int)lround(X[0]), s->p.nx);
-        int cy = (int)lround(X[1]);
-        if (cy < 0) cy = 0;
-        if (cy >= s->p.ny) cy = s->p.ny - 1;
-        int cz = wrap((int)lround(X[2]), s->p.nz);
-        long long nc = node(s, cx, cy, cz);
-        int fz = s->p.nz > 1 ? wrap(cz + s->p.nz / 2, s->p.nz) : 0;
-        long long nf = node(s, wrap(cx + s->p.nx / 2, s->p.nx), cy, fz);
-        o->p_centre = pressure(s, nc);
-        o->p_far = pressure(s, nf);
+        /* Laplace pressure: the pressure at the centroid vs the pressure
+         * half a period away in x (and z) */
+        o->p_centre = pressure_interp(s, X[0], X[1], X[2]);
+        o->p_far = pressure_interp(s, X[0] + s->p.nx / 2, X[1], s->p.nz > 1 ? X[2] + s->p.nz / 2 : X[2]);
         o->dp = o->p_centre - o->p_far;
     }
     o->status = bad ? 1 : (umax > 0.3 ? 2 : 0);

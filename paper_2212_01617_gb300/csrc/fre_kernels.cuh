@@ -702,6 +702,31 @@ __device__ double pressure_at(const Launch &L, int x, int y, int z) {
     return rho / 3.0 + ph * mu - 0.25 * L.P.A * (ph * ph - 1.0) * (ph * ph - 1.0);
 }
 
+// Pressure at the point (X, Y, Z) by trilinear interpolation of the nodal
+// pressure: periodic in x and z, and in y off the shear device (whose y is
+// clamped to the fluid rows); solid nodes carry no weight.  A droplet
+// centred on a cell face would switch nodes under any rounding of its
+// centroid if the pressure were read at the nearest node.
+template <int Q, int FMT, bool PULL>
+__device__ double pressure_interp(const Launch &L, double X, double Y, double Z) {
+    const Geo &G = L.G;
+    const int x0 = (int)floor(X), y0 = (int)floor(Y), z0 = (int)floor(Z);
+    const double fx = X - x0, fy = Y - y0, fz = Z - z0;
+    double acc = 0.0, wsum = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = (k >> 2) & 1;
+        const double w = (dx ? fx : 1.0 - fx) * (dy ? fy : 1.0 - fy) * (dz ? fz : 1.0 - fz);
+        if (w == 0.0) continue;
+        const int x = wrapi(x0 + dx, G.nx), z = wrapi(z0 + dz, G.nz);
+        int y = y0 + dy;
+        y = G.device == FRE_SHEAR ? (y < 0 ? 0 : (y >= G.ny ? G.ny - 1 : y)) : wrapi(y, G.ny);
+        if (is_solid(G, node_index(G, x, y, z))) continue;
+        acc += w * pressure_at<Q, FMT, PULL>(L, x, y, z);
+        wsum += w;
+    }
+    return wsum > 0.0 ? acc / wsum : 0.0;
+}
+
 template <int Q, int FMT, bool PULL>
 __global__ void k_obs_final(Launch L, const double *t1, const double *t2) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -728,14 +753,11 @@ __global__ void k_obs_final(Launch L, const double *t1, const double *t2) {
         const double s1 = sqrt(l1), s2 = sqrt(l2);
         o->D = (s1 + s2) > 0.0 ? (s1 - s2) / (s1 + s2) : 0.0;
         o->theta_deg = 0.5 * atan2(2.0 * c, a - b) * (180.0 / 3.14159265358979323846);
+        // Laplace pressure (Sec. 3): at the centroid vs half a period away
+        // in x (and z)
         const Geo &G = L.G;
-        int cx = wrapi((int)llround(X[0]), G.nx);
-        int cy = (int)llround(X[1]);
-        cy = cy < 0 ? 0 : (cy >= G.ny ? G.ny - 1 : cy);
-        int cz = wrapi((int)llround(X[2]), G.nz);
-        int fz = G.nz > 1 ? wrapi(cz + G.nz / 2, G.nz) : 0;
-        o->p_centre = pressure_at<Q, FMT, PULL>(L, cx, cy, cz);
-        o->p_far = pressure_at<Q, FMT, PULL>(L, wrapi(cx + G.nx / 2, G.nx), cy, fz);
+        o->p_centre = pressure_interp<Q, FMT, PULL>(L, X[0], X[1], X[2]);
+        o->p_far = pressure_interp<Q, FMT, PULL>(L, X[0] + G.nx / 2, X[1], G.nz > 1 ? X[2] + G.nz / 2 : X[2]);
         o->dp = o->p_centre - o->p_far;
     }
     o->status = bad ? 1 : (o->max_u > 0.3 ? 2 : 0);
