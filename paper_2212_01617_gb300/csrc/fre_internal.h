@@ -26,9 +26,18 @@ struct Phys {
     double tau_f, tau_g, A, kappa, Gamma, rho0;
 };
 
+// FP32 copies of the per-launch constants of the FP32-compute kernels,
+// rounded once on the host: the GPU's FP64 pipe is narrow, so the kernels
+// do no double arithmetic per work unit or node.  u0, du: the plane
+// Couette profile of the shear device, U(y) = u0 + y du (0 elsewhere).
+struct PhysF {
+    float omega_f, omega_g, kf, gamma3, A, kappa, rho0, uwall, u0, du;
+};
+
 // One population buffer (A or B).  FP64/FP32: f, g are [q][np] arrays of
 // the storage type.  16-bit formats: f is [q][np] of deviations
-// f_i - w_i rho0; g holds g_1..g_{q-1} as [q-1][np]; g0 is FP32 [np].
+// f_i - fr_i(y) from the Couette reference of the node's row (fref in
+// fre_kernels.cuh); g holds g_1..g_{q-1} as [q-1][np]; g0 is FP32 [np].
 struct Buf {
     void *f;
     void *g;
@@ -39,6 +48,7 @@ struct Buf {
 struct Launch {
     Geo G;
     Phys P;
+    PhysF F;
     Buf src, dst;
     const void *phi_prev;  // phi at the previous step (moving-wall term of g)
     void *phi;             // phi at the current step

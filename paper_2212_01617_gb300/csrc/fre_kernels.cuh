@@ -70,14 +70,14 @@ __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
 // other device.  The stored values then carry the departure from the base
 // flow only: a deviation from w_i rho0 alone would spend the 16-bit
 // mantissa on the 3 w_i rho0 c_ix U part of every moving population.
+// (FP64 evaluates U in double; FP32 computes take u0 + y du from the host.)
 template <typename T>
-__device__ __forceinline__ T couette_u(const Geo &G, int y) {
-    return G.device == FRE_SHEAR ? T(G.uwall) * (T(2 * y + 1) / T(G.ny) - T(1)) : T(0);
-}
-// U(y + 1) - U(y)
-template <typename T>
-__device__ __forceinline__ T couette_du(const Geo &G) {
-    return G.device == FRE_SHEAR ? T(2.0 * G.uwall / G.ny) : T(0);
+__device__ __forceinline__ T couette_u(const Launch &L, int y) {
+    if constexpr (sizeof(T) == 8) {
+        return L.G.device == FRE_SHEAR ? L.G.uwall * ((2.0 * y + 1.0) / L.G.ny - 1.0) : 0.0;
+    } else {
+        return fmaf(float(y), L.F.du, L.F.u0);
+    }
 }
 template <int Q, typename T>
 __device__ __forceinline__ T fref(int i, T rho0, T U) {
@@ -244,8 +244,7 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
     using P = Pop<Q, FMT>;
     const T rho0 = T(L.P.rho0);
     // U of this node's row; a pulled population comes from row y - c_iy
-    const T U = Fmt<FMT>::DEV ? couette_u<T>(L.G, s.y) : T(0);
-    const T dU = Fmt<FMT>::DEV ? couette_du<T>(L.G) : T(0);
+    const T U = Fmt<FMT>::DEV ? couette_u<T>(L, s.y) : T(0);
     const long long np = L.G.np;
     const int n = s.n;
 #pragma unroll
@@ -258,7 +257,7 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
         T uwx = T(0), uwy = T(0);
         const int src = pull_source<Q, T>(L.G, s, i, uwx, uwy);
         if (src >= 0) {
-            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0, U - T(Lat<Q>::cy(i)) * dU);
+            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0, Fmt<FMT>::DEV ? couette_u<T>(L, s.y - Lat<Q>::cy(i)) : T(0));
             g[i] = P::ldg(L.src, np, i, src);
         } else {
             const int o = Lat<Q>::opp(i);
@@ -389,7 +388,8 @@ __device__ __forceinline__ void node_mu(const Launch &L, const Site &s) {
 #pragma unroll
     for (int i = 1; i < Q; ++i) lap += T(Lat<Q>::w(i)) * (phi[site_nb<Q>(s, i)] - p0);
     lap *= T(6);
-    static_cast<T *>(L.mu)[s.n] = T(L.P.A) * (p0 * p0 * p0 - p0) - T(L.P.kappa) * lap;
+    const T A = sizeof(T) == 4 ? T(L.F.A) : T(L.P.A), kappa = sizeof(T) == 4 ? T(L.F.kappa) : T(L.P.kappa);
+    static_cast<T *>(L.mu)[s.n] = A * (p0 * p0 * p0 - p0) - kappa * lap;
 }
 
 template <int Q, typename T>
@@ -409,12 +409,14 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
     gather<Q, FMT, PULL, true>(L, s, f, g);
     const Macro<T> m = macro_of<Q, FMT>(L, s, f, g);
 
-    const T of = T(1.0 / L.P.tau_f), og = T(1.0 / L.P.tau_g);
-    const T kf = T(1.0 - 0.5 / L.P.tau_f);
-    const T gmu3 = T(3.0 * L.P.Gamma) * m.mu;
+    // FP32 computes take the constants rounded on the host
+    const bool f32 = sizeof(T) == 4;
+    const T of = f32 ? T(L.F.omega_f) : T(1.0 / L.P.tau_f), og = f32 ? T(L.F.omega_g) : T(1.0 / L.P.tau_g);
+    const T kf = f32 ? T(L.F.kf) : T(1.0 - 0.5 / L.P.tau_f);
+    const T gmu3 = (f32 ? T(L.F.gamma3) : T(3.0 * L.P.Gamma)) * m.mu;
     const T usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     const T uF = m.ux * m.Fx + m.uy * m.Fy + m.uz * m.Fz;
-    const T U = Fmt<FMT>::DEV ? couette_u<T>(L.G, s.y) : T(0);
+    const T U = Fmt<FMT>::DEV ? couette_u<T>(L, s.y) : T(0);
     T fsum = T(0), gsum = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(kBlock) k_load_plane(Launch L, int lat_g, int 
     for (int j = 0; j < Q; ++j) {
         if (j != i) continue;
         if (lat_g) P::stg(L.src, L.G.np, j, n, v);
-        else P::stf(L.src, L.G.np, j, n, v, T(L.P.rho0), couette_u<T>(L.G, s.y));
+        else P::stf(L.src, L.G.np, j, n, v, T(L.P.rho0), couette_u<T>(L, s.y));
     }
 }
 
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
     const long long N = L.G.n;
     const int n = s.n;
     const T rho0 = T(L.P.rho0);
-    const T U = couette_u<T>(L.G, s.y);
+    const T U = couette_u<T>(L, s.y);
     if (is_solid(L.G, n)) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {

@@ -15,6 +15,8 @@
 // through a path every thread of a role takes together.
 #pragma once
 
+#include <type_traits>
+
 #include "fre_pipe.cuh"
 
 namespace fre {
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
     // ------------------------------------------------------------ consumers
     const int xl = threadIdx.x;
     const float *php = static_cast<const float *>(L.phi_prev);
-    const float rho0 = float(L.P.rho0);
+    const float rho0 = L.F.rho0;
     int k = 0;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
         const int s = k % NST;
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if (PULL && (wall >> i) & 1u) {
-                    const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
+                    const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
                     sum += row_g<Q, FMT>(cur, W, i, xl) +
                            float(2.0 * Lat<Q>::w(i) * 3.0) * php[u.row + u.x0 + xl] * float(Lat<Q>::cx(i)) * uw;
                 } else {
@@ -217,24 +219,23 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
             consumer_sync(ncons);
             if (xl == 0) mbar_arrive(smem_addr(&empty[s]));
             static_cast<float *>(L.mu)[u.row + u.x0 + xl] =
-                float(L.P.A) * (p0 * p0 * p0 - p0) - float(L.P.kappa) * lap;
+                L.F.A * (p0 * p0 * p0 - p0) - L.F.kappa * lap;
         } else {
             const unsigned foff = CL::field_off(W);
             const unsigned char *gb = cur + CL::g_off(W);
             const unsigned char *phs = cur + foff;
             const unsigned char *mus = cur + foff + NS * CL::rw_f(W);
-            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
-            const float kf = float(1.0 - 0.5 / L.P.tau_f);
-            const float g3 = float(3.0 * L.P.Gamma);
+            const float of = L.F.omega_f, og = L.F.omega_g;
+            const float kf = L.F.kf;
+            const float g3 = L.F.gamma3;
             constexpr int c0 = stencil_slot<Q>(0, 0);
             // U of this row; a pulled f_i was stored in row y - c_iy
-            const float U = Fmt<FMT>::DEV ? couette_u<float>(L.G, u.y) : 0.f;
-            const float dU = Fmt<FMT>::DEV ? couette_du<float>(L.G) : 0.f;
+            const float U = Fmt<FMT>::DEV ? couette_u<float>(L, u.y) : 0.f;
             float f[Q], g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if (PULL && (wall >> i) & 1u) {
-                    const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
+                    const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
                     const float cu = float(Lat<Q>::cx(i)) * uw;
                     const float w2 = float(2.0 * Lat<Q>::w(i) * 3.0);
                     // slot i holds the local row of population opp(i)
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
                     g[i] = go + w2 * php[u.row + u.x0 + xl] * cu;
                 } else {
                     const int xs = PULL ? xl - Lat<Q>::cx(i) : xl;
-                    const float Us = PULL ? U - float(Lat<Q>::cy(i)) * dU : U;
+                    const float Us = PULL ? couette_u<float>(L, u.y - Lat<Q>::cy(i)) : U;
                     f[i] = row_f<Q, FMT>(cur, W, i, xs, fref<Q, float>(i, rho0, Us));
                     g[i] = row_g<Q, FMT>(gb, W, i, xs);
                 }
@@ -474,8 +475,6 @@ struct RowsLayout {
     }
 };
 
-__device__ __forceinline__ int wrap_x(int x, int nx) { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
-
 // Two adjacent nodes per consumer thread: FP32 arithmetic on packed pairs
 // (the paired add / multiply / fused multiply-add of sm_100 and later).
 __device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
@@ -503,11 +502,14 @@ template <typename S>
 __device__ __forceinline__ float2 ld_two(const S *row, int xa, int xb) {
     return make_float2(to_f(row[xa]), to_f(row[xb]));
 }
-// the pulled pair of one staged row: x0, x0 + 1 shifted by -cx with wrap
+// the pulled pair of one staged row: x0, x0 + 1 shifted by -cx (|cx| <= 1)
+// with the periodic wrap; x0 even and 0 <= x0 <= nx - 2, so only x0 - 1 and
+// x0 + 2 can leave the row
 template <typename S>
 __device__ __forceinline__ float2 ld_shift(const S *row, int x0, int cx, int nx) {
     if (cx == 0) return ld_pair(row, x0);
-    return ld_two(row, wrap_x(x0 - cx, nx), wrap_x(x0 + 1 - cx, nx));
+    if (cx > 0) return ld_two(row, x0 == 0 ? nx - 1 : x0 - 1, x0);
+    return ld_two(row, x0 + 1, x0 + 2 == nx ? 0 : x0 + 2);
 }
 __device__ __forceinline__ void st_pair(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 __device__ __forceinline__ float2 st_pair(__half *p, float2 v) {
@@ -559,8 +561,8 @@ __host__ __device__ constexpr int pair_index(int i) {
 template <int Q, bool PULL>
 __device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *out, int lane) {
     const bool shear = L.G.device == FRE_SHEAR;
-    const float rho0 = float(L.P.rho0), om = float(1.0 / L.P.tau_f);
-    const float U = couette_u<float>(L.G, y), dU = couette_du<float>(L.G);
+    const float rho0 = L.F.rho0, om = L.F.omega_f;
+    const float U = couette_u<float>(L, y);
     const int i = lane < Q ? lane : 0;
     const int ciy = Lat<Q>::cy(i);
     const float cx = float(Lat<Q>::cx(i)), cy = float(ciy), cz = float(Lat<Q>::cz(i));
@@ -569,10 +571,10 @@ __device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *o
     float o = 0.f;
     if (PULL) {
         if (shear && ((y == 0 && ciy > 0) || (y == L.G.ny - 1 && ciy < 0))) {
-            const float uwl = ciy > 0 ? float(-L.G.uwall) : float(L.G.uwall);
+            const float uwl = ciy > 0 ? -L.F.uwall : L.F.uwall;
             o = wr * 6.f * cx * (uwl - U);
         } else {
-            const float e = -cy * dU;
+            const float e = couette_u<float>(L, y - ciy) - U;
             o = wr * (b * e + a * (2.f * U + e) * e);
         }
     }
@@ -740,7 +742,7 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
     }
 
     // ------------------------------------------------------------ consumers
-    const float rho0 = float(L.P.rho0);
+    const float rho0 = L.F.rho0;
     const float *__restrict__ php = static_cast<const float *>(L.phi_prev);
     const long long np = L.G.np;
     const int x0 = 2 * threadIdx.x;
@@ -763,22 +765,28 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
             for (int r = 0; r < R; ++r) {
                 const unsigned wall = wall_s[s][r];
                 const size_t row = ((size_t)z * ny + y0 + r) * nx;
-                float2 sum = p2(0.f);
+                // rows without wall links (all but the first and last of the
+                // shear device) take every shift as a compile-time constant
+                auto pull_sum = [&](auto walls) {
+                    constexpr bool WL = decltype(walls)::value;
+                    float2 sum = p2(0.f);
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const bool wl = PULL && ((wall >> i) & 1u);
-                    const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
-                    float2 gv;
-                    if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
-                    else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
-                    if (wl) {
-                        const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
-                        const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
-                        gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
+                    for (int i = 0; i < Q; ++i) {
+                        const bool wl = WL && Lat<Q>::cy(i) != 0 && ((wall >> i) & 1u);
+                        const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
+                        float2 gv;
+                        if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
+                        else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
+                        if (wl) {
+                            const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
+                            const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
+                            gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
+                        }
+                        sum = add2(sum, gv);
                     }
-                    sum = add2(sum, gv);
-                }
-                out[r] = sum;
+                    return sum;
+                };
+                out[r] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -801,8 +809,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 }
                 lap = mul2(p2(6.f), lap);
                 // A (phi^3 - phi) - kappa lap
-                out[r] = sub2(mul2(p2(float(L.P.A)), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
-                              mul2(p2(float(L.P.kappa)), lap));
+                out[r] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
+                              mul2(p2(L.F.kappa), lap));
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -813,8 +821,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
             // ---------------------------------------------------- update
             const float *__restrict__ phif = static_cast<const float *>(L.phi);
             const float *__restrict__ muf = static_cast<const float *>(L.mu);
-            const float of = float(1.0 / L.P.tau_f), og = float(1.0 / L.P.tau_g);
-            const float kf = float(1.0 - 0.5 / L.P.tau_f);
+            const float of = L.F.omega_f, og = L.F.omega_g;
+            const float kf = L.F.kf;
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const unsigned wall = wall_s[s][r];
@@ -825,26 +833,33 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 // from the reference of the row they were stored in), then
                 // the stencil values of phi and mu
                 float2 f[Q], g[Q];
+                // rows without wall links (all but the first and last of the
+                // shear device) take every shift as a compile-time constant
+                auto pull = [&](auto walls) {
+                    constexpr bool WL = decltype(walls)::value;
 #pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    const bool wl = PULL && ((wall >> i) & 1u);
-                    const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
-                    float2 gv;
-                    if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
-                    else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
-                    float2 fv = ld_shift(reinterpret_cast<const S *>(cur + FL::f_row(nx, i, r)), x0, cx, nx);
-                    if (wl) {
-                        // the row of opp(i) at this node: add the moving-wall
-                        // term 2 w_i a (c_i . u_w) / cs^2
-                        const float uw = Lat<Q>::cy(i) > 0 ? float(-L.G.uwall) : float(L.G.uwall);
-                        const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
-                        // (16-bit f: the wall term is part of the row constants)
-                        if constexpr (!DEV) fv = add2(fv, p2(w2cu * rho0));
-                        gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
+                    for (int i = 0; i < Q; ++i) {
+                        const bool wl = WL && Lat<Q>::cy(i) != 0 && ((wall >> i) & 1u);
+                        const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
+                        float2 gv;
+                        if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
+                        else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
+                        float2 fv = ld_shift(reinterpret_cast<const S *>(cur + FL::f_row(nx, i, r)), x0, cx, nx);
+                        if (wl) {
+                            // the row of opp(i) at this node: add the moving-wall
+                            // term 2 w_i a (c_i . u_w) / cs^2
+                            const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
+                            const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
+                            // (16-bit f: the wall term is part of the row constants)
+                            if constexpr (!DEV) fv = add2(fv, p2(w2cu * rho0));
+                            gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
+                        }
+                        f[i] = fv;
+                        g[i] = gv;
                     }
-                    f[i] = fv;
-                    g[i] = gv;
-                }
+                };
+                if (PULL && wall != 0u) pull(std::true_type{});
+                else pull(std::false_type{});
                 float2 gpx = p2(0.f), gpy = p2(0.f), gpz = p2(0.f), gqx = p2(0.f), gqy = p2(0.f), gqz = p2(0.f);
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
@@ -912,7 +927,7 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
                 const float2 uF = fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)));
                 const float2 omf = p2(1.f - of), omg = p2(1.f - og);
-                const float2 gmu3 = mul2(p2(float(3.0 * L.P.Gamma)), mu);
+                const float2 gmu3 = mul2(p2(L.F.gamma3), mu);
                 const float2 m15usq = mul2(p2(-1.5f), usq);
                 const float2 m3uF = mul2(p2(-3.f), uF);
 
