@@ -511,6 +511,8 @@ __device__ __forceinline__ float2 ld_shift(const S *row, int x0, int cx, int nx)
     if (cx > 0) return ld_two(row, x0 == 0 ? nx - 1 : x0 - 1, x0);
     return ld_two(row, x0 + 1, x0 + 2 == nx ? 0 : x0 + 2);
 }
+// start the line holding *p toward L1 (no register waits for it)
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.L1 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void st_pair(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 __device__ __forceinline__ float2 st_pair(__half *p, float2 v) {
     const __half2 h = __float22half2_rn(v);
@@ -829,6 +831,20 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 const int y = y0 + r;
                 const size_t row = ((size_t)z * ny + y) * nx;
                 const Site st = make_site(L.G, x0, y, z);
+                // FP32: start the lines of the off-axis stencil values (c_y and
+                // c_z both nonzero, read from global memory below) toward L1
+                // before the pull phase (measured 2% on the update; the
+                // 16-bit update, latency-bound at 9 warps per SM, gains
+                // nothing from it and loses L1 room)
+                if constexpr (!DEV) {
+#pragma unroll
+                    for (int kk = 1; kk < Q; ++kk) {
+                        if (Lat<Q>::cy(kk) == 0 || Lat<Q>::cz(kk) == 0) continue;
+                        const int kn = site_nb<Q>(st, kk);
+                        prefetch_l1(phif + kn);
+                        prefetch_l1(muf + kn);
+                    }
+                }
                 // ---- read phase: pulled populations (16-bit f: deviations
                 // from the reference of the row they were stored in), then
                 // the stencil values of phi and mu
