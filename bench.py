@@ -40,6 +40,17 @@ DROPLET = (255.5, 127.5, 127.5, 48.0)
 ALG_BYTES = {"fp32": 2 * 2 * 19 * 4, "fp16dev": 2 * (19 * 2 + 18 * 2 + 4),
              "bf16dev": 2 * (19 * 2 + 18 * 2 + 4), "fp64": 2 * 2 * 19 * 8}
 CSRC = os.path.join(ROOT, "paper_2212_01617_gb300", "csrc")
+# a precision name may carry "+couette": the 16-bit f stored against the
+# Couette equilibrium of the shear walls (FRE_FLAG_COUETTE_REFERENCE)
+# instead of the rest equilibrium w_i rho0
+FLAG_COUETTE_REFERENCE = 4
+
+
+def split_prec(name: str):
+    base, _, opt = name.partition("+")
+    if opt not in ("", "couette"):
+        raise SystemExit(f"unknown precision variant {name!r}")
+    return base, (FLAG_COUETTE_REFERENCE if opt == "couette" else 0)
 
 
 def log(*a):
@@ -183,7 +194,8 @@ def time_steps(fre, precision, steps, warmup, ws, local):
     """Kernel-only timing of `steps` time steps with inputs resident in HBM."""
     import torch
     n = WORKLOAD["nx"] * WORKLOAD["ny"] * WORKLOAD["nz"]
-    sim = fre.Simulation(precision=precision, **WORKLOAD)
+    base, flags = split_prec(precision)
+    sim = fre.Simulation(precision=base, flags=flags, **WORKLOAD)
     sim.init_droplet(*DROPLET)
     sim.step(warmup)
     torch.cuda.synchronize()
@@ -228,7 +240,8 @@ def time_e2e(fre, precision, steps, obs_every=100):
     host["uy"][:] = 0.0
     host["uz"][:] = 0.0
     del x, y, z, r
-    sim = fre.Simulation(precision=precision, **WORKLOAD)
+    base, flags = split_prec(precision)
+    sim = fre.Simulation(precision=base, flags=flags, **WORKLOAD)
     # one untimed pass allocates the I/O staging buffer of the context
     sim.init_fields(host["rho"], host["ux"], host["uy"], host["uz"], host["phi"])
     sim.step(2)
@@ -321,7 +334,8 @@ def profile_case(spec: str, precisions, steps: int = 3):
     nx, ny, nz = (int(v) for v in spec.split("x"))
     w = dict(WORKLOAD, nx=nx, ny=ny, nz=nz)
     for prec in precisions:
-        sim = fre.Simulation(precision=prec, **w)
+        base, flags = split_prec(prec)
+        sim = fre.Simulation(precision=base, flags=flags, **w)
         sim.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, min(ny, nz) * 0.375)
         sim.step(steps)
         torch.cuda.synchronize()
@@ -537,7 +551,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precisions", default="fp32,fp16dev,bf16dev")
+    ap.add_argument("--precisions", default="fp32,fp16dev,bf16dev,fp16dev+couette,bf16dev+couette")
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -585,9 +599,9 @@ def main():
     value = weak_scaling_value(ws, n, args.steps, r["ms"])
     peak, peak_src = measured_peak_gbs()
     t_upd = r["ms_update"] / args.steps * 1e-3
-    achieved = ALG_BYTES[main_prec] * n / t_upd / 1e9
-    traffic = ncu_traffic(main_prec)
-    step_achieved = ALG_BYTES[main_prec] * n / (r["ms"] / args.steps * 1e-3) / 1e9
+    achieved = ALG_BYTES[split_prec(main_prec)[0]] * n / t_upd / 1e9
+    traffic = ncu_traffic(split_prec(main_prec)[0])
+    step_achieved = ALG_BYTES[split_prec(main_prec)[0]] * n / (r["ms"] / args.steps * 1e-3) / 1e9
 
     e2e = None
     if not args.no_e2e:
@@ -602,14 +616,15 @@ def main():
         variants = {}
         for prec, rr in runs.items():
             t = rr["ms_update"] / args.steps * 1e-3
+            ab = ALG_BYTES[split_prec(prec)[0]]
             variants[prec] = {
                 "mlups": ws * rr["n"] * args.steps / (rr["ms"] * 1e-3) / 1e6,
                 "ms_per_step": rr["ms"] / args.steps,
                 "update_ms": rr["ms_update"] / args.steps, "phi_ms": rr["ms_phi"] / args.steps,
                 "mu_ms": rr["ms_mu"] / args.steps,
-                "update_alg_gbs": ALG_BYTES[prec] * rr["n"] / t / 1e9,
-                "update_frac_of_measured_hbm": ALG_BYTES[prec] * rr["n"] / t / 1e9 / peak,
-                "step_alg_frac_of_measured_hbm": ALG_BYTES[prec] * rr["n"] / (rr["ms"] / args.steps * 1e-3)
+                "update_alg_gbs": ab * rr["n"] / t / 1e9,
+                "update_frac_of_measured_hbm": ab * rr["n"] / t / 1e9 / peak,
+                "step_alg_frac_of_measured_hbm": ab * rr["n"] / (rr["ms"] / args.steps * 1e-3)
                 / 1e9 / peak,
                 "D_after_run": rr["obs"]["D"], "mass": rr["obs"]["mass"], "kernel_path": rr["path"],
             }
@@ -626,7 +641,7 @@ def main():
                          "kernel": (f"k_wsrow<19,{main_prec},update,pull> (fused pull + collide of f and g; "
                                     "warp-specialised, bulk-copy staged x-rows)" if r["path"] == 2 else
                                     f"update kernel, path {r['path']}"),
-                         "algorithmic_bytes_per_launch": ALG_BYTES[main_prec] * n,
+                         "algorithmic_bytes_per_launch": ALG_BYTES[split_prec(main_prec)[0]] * n,
                          "peak_source": peak_src,
                          "step_achieved": step_achieved, "step_frac": step_achieved / peak},
             "cpu_baseline": cpu,

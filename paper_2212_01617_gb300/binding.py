@@ -39,6 +39,7 @@ EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_field
            "fre_server_stats", "fre_server_clock", "fre_server_destroy",
            "fre_destroy", "fre_last_error"]
 FRE_FLAG_GENERIC_KERNELS = 1
+FRE_FLAG_COUETTE_REFERENCE = 4
 
 
 class FreError(RuntimeError):

@@ -162,7 +162,9 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.G = c->G;
     L.P = c->P;
     const double tf = c->P.tau_f, tg = c->P.tau_g;
-    const bool shear = c->G.device == FRE_SHEAR;
+    // reference profile of the 16-bit f stores (FRE_FLAG_COUETTE_REFERENCE)
+    const bool shear = c->G.device == FRE_SHEAR && (c->p.flags & FRE_FLAG_COUETTE_REFERENCE) &&
+                       (c->p.precision == FRE_FP16DEV || c->p.precision == FRE_BF16DEV);
     L.F = {float(1.0 / tf), float(1.0 / tg), float(1.0 - 0.5 / tf), float(3.0 * c->P.Gamma),
            float(c->P.A), float(c->P.kappa), float(c->P.rho0), float(c->G.uwall),
            shear ? float(c->G.uwall * (1.0 / c->G.ny - 1.0)) : 0.f, shear ? float(2.0 * c->G.uwall / c->G.ny) : 0.f};

@@ -28,16 +28,19 @@ struct Phys {
 
 // FP32 copies of the per-launch constants of the FP32-compute kernels,
 // rounded once on the host: the GPU's FP64 pipe is narrow, so the kernels
-// do no double arithmetic per work unit or node.  u0, du: the plane
-// Couette profile of the shear device, U(y) = u0 + y du (0 elsewhere).
+// do no double arithmetic per work unit or node.  u0, du: the reference
+// profile U(y) = u0 + y du of the 16-bit f stores (fref in fre_kernels.cuh):
+// the plane Couette profile of the shear device under
+// FRE_FLAG_COUETTE_REFERENCE, else 0 (the rest equilibrium).
 struct PhysF {
     float omega_f, omega_g, kf, gamma3, A, kappa, rho0, uwall, u0, du;
 };
 
 // One population buffer (A or B).  FP64/FP32: f, g are [q][np] arrays of
 // the storage type.  16-bit formats: f is [q][np] of deviations
-// f_i - fr_i(y) from the Couette reference of the node's row (fref in
-// fre_kernels.cuh); g holds g_1..g_{q-1} as [q-1][np]; g0 is FP32 [np].
+// f_i - fr_i(y) from the reference of the node's row (fref in
+// fre_kernels.cuh; w_i rho0 unless FRE_FLAG_COUETTE_REFERENCE); g holds
+// g_1..g_{q-1} as [q-1][np]; g0 is FP32 [np].
 struct Buf {
     void *f;
     void *g;

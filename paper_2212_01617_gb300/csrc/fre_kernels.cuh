@@ -65,20 +65,13 @@ __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
 
 // Reference state of the 16-bit f formats.  f is stored as the deviation
 // f_i - fr_i(y) from the second-order equilibrium (Eq. feq) of density rho0
-// and velocity (U(y), 0, 0), where U is the plane Couette profile between
-// the shear device's walls, U(y) = u_w (2 (y + 1/2) / ny - 1), and 0 on every
-// other device.  The stored values then carry the departure from the base
-// flow only: a deviation from w_i rho0 alone would spend the 16-bit
-// mantissa on the 3 w_i rho0 c_ix U part of every moving population.
-// (FP64 evaluates U in double; FP32 computes take u0 + y du from the host.)
-template <typename T>
-__device__ __forceinline__ T couette_u(const Launch &L, int y) {
-    if constexpr (sizeof(T) == 8) {
-        return L.G.device == FRE_SHEAR ? L.G.uwall * ((2.0 * y + 1.0) / L.G.ny - 1.0) : 0.0;
-    } else {
-        return fmaf(float(y), L.F.du, L.F.u0);
-    }
-}
+// and velocity (U(y), 0, 0).  By default U = 0: the rest equilibrium
+// w_i rho0.  Under FRE_FLAG_COUETTE_REFERENCE the shear device takes the
+// plane Couette profile between its walls, U(y) = u_w (2 (y + 1/2) / ny -
+// 1), so the stored values carry the departure from the base flow only
+// instead of spending the 16-bit mantissa on the 3 w_i rho0 c_ix U part of
+// every moving population.  U(y) = u0 + y du with u0, du rounded on the host.
+__device__ __forceinline__ float couette_u(const Launch &L, int y) { return fmaf(float(y), L.F.du, L.F.u0); }
 template <int Q, typename T>
 __device__ __forceinline__ T fref(int i, T rho0, T U) {
     const T cu = T(Lat<Q>::cx(i)) * U;
@@ -244,7 +237,7 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
     using P = Pop<Q, FMT>;
     const T rho0 = T(L.P.rho0);
     // U of this node's row; a pulled population comes from row y - c_iy
-    const T U = Fmt<FMT>::DEV ? couette_u<T>(L, s.y) : T(0);
+    const T U = Fmt<FMT>::DEV ? T(couette_u(L, s.y)) : T(0);
     const long long np = L.G.np;
     const int n = s.n;
 #pragma unroll
@@ -257,7 +250,7 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
         T uwx = T(0), uwy = T(0);
         const int src = pull_source<Q, T>(L.G, s, i, uwx, uwy);
         if (src >= 0) {
-            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0, Fmt<FMT>::DEV ? couette_u<T>(L, s.y - Lat<Q>::cy(i)) : T(0));
+            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0, Fmt<FMT>::DEV ? T(couette_u(L, s.y - Lat<Q>::cy(i))) : T(0));
             g[i] = P::ldg(L.src, np, i, src);
         } else {
             const int o = Lat<Q>::opp(i);
@@ -416,7 +409,7 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
     const T gmu3 = (f32 ? T(L.F.gamma3) : T(3.0 * L.P.Gamma)) * m.mu;
     const T usq = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     const T uF = m.ux * m.Fx + m.uy * m.Fy + m.uz * m.Fz;
-    const T U = Fmt<FMT>::DEV ? couette_u<T>(L, s.y) : T(0);
+    const T U = Fmt<FMT>::DEV ? T(couette_u(L, s.y)) : T(0);
     T fsum = T(0), gsum = T(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -501,7 +494,7 @@ __global__ void __launch_bounds__(kBlock) k_load_plane(Launch L, int lat_g, int 
     for (int j = 0; j < Q; ++j) {
         if (j != i) continue;
         if (lat_g) P::stg(L.src, L.G.np, j, n, v);
-        else P::stf(L.src, L.G.np, j, n, v, T(L.P.rho0), couette_u<T>(L, s.y));
+        else P::stf(L.src, L.G.np, j, n, v, T(L.P.rho0), T(couette_u(L, s.y)));
     }
 }
 
@@ -535,7 +528,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
     const long long N = L.G.n;
     const int n = s.n;
     const T rho0 = T(L.P.rho0);
-    const T U = couette_u<T>(L, s.y);
+    const T U = T(couette_u(L, s.y));
     if (is_solid(L.G, n)) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -552,7 +545,7 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
         uz = T(L.staging[3 * N + n]);
     } else {
         rho = rho0;
-        ux = U;
+        ux = (L.G.device == FRE_SHEAR) ? T(L.G.uwall * (2.0 * (s.y + 0.5) / L.G.ny - 1.0)) : T(0);
         uy = T(0);
         uz = T(0);
     }

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
             const float g3 = L.F.gamma3;
             constexpr int c0 = stencil_slot<Q>(0, 0);
             // U of this row; a pulled f_i was stored in row y - c_iy
-            const float U = Fmt<FMT>::DEV ? couette_u<float>(L, u.y) : 0.f;
+            const float U = Fmt<FMT>::DEV ? couette_u(L, u.y) : 0.f;
             float f[Q], g[Q];
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
                     g[i] = go + w2 * php[u.row + u.x0 + xl] * cu;
                 } else {
                     const int xs = PULL ? xl - Lat<Q>::cx(i) : xl;
-                    const float Us = PULL ? couette_u<float>(L, u.y - Lat<Q>::cy(i)) : U;
+                    const float Us = PULL ? couette_u(L, u.y - Lat<Q>::cy(i)) : U;
                     f[i] = row_f<Q, FMT>(cur, W, i, xs, fref<Q, float>(i, rho0, Us));
                     g[i] = row_g<Q, FMT>(gb, W, i, xs);
                 }
@@ -544,8 +544,9 @@ __host__ __device__ constexpr int pair_index(int i) {
 }
 
 // Per-row constants of the update for the 16-bit f formats, whose stored
-// f is the deviation from the Couette reference fr_i(y) (Eq. feq at rho0
-// and (U(y), 0, 0)).  The update pulls deviations stored against the
+// f is the deviation from the reference fr_i(y) (Eq. feq at rho0 and
+// (U(y), 0, 0): U = 0, the rest equilibrium, or the Couette profile of the
+// shear device under FRE_FLAG_COUETTE_REFERENCE).  The update pulls deviations stored against the
 // reference of their source row y - c_iy (or, on a wall link, the local
 // deviation of opp(i)); d_i = d'_i + o_i is then the deviation from this
 // row's reference, and the BGK step on deviations,
@@ -564,7 +565,7 @@ template <int Q, bool PULL>
 __device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *out, int lane) {
     const bool shear = L.G.device == FRE_SHEAR;
     const float rho0 = L.F.rho0, om = L.F.omega_f;
-    const float U = couette_u<float>(L, y);
+    const float U = couette_u(L, y);
     const int i = lane < Q ? lane : 0;
     const int ciy = Lat<Q>::cy(i);
     const float cx = float(Lat<Q>::cx(i)), cy = float(ciy), cz = float(Lat<Q>::cz(i));
@@ -576,7 +577,7 @@ __device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *o
             const float uwl = ciy > 0 ? -L.F.uwall : L.F.uwall;
             o = wr * 6.f * cx * (uwl - U);
         } else {
-            const float e = couette_u<float>(L, y - ciy) - U;
+            const float e = couette_u(L, y - ciy) - U;
             o = wr * (b * e + a * (2.f * U + e) * e);
         }
     }

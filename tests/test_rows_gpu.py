@@ -51,9 +51,13 @@ def make(fre, lattice, device, nx, ny, nz, precision, flags=0, **kw):
                           flags=flags, **args)
 
 
+COUETTE = 4  # FRE_FLAG_COUETTE_REFERENCE
+
+
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}")
-@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
-def test_row_kernels_match_per_node_kernels(fre, orc, case, precision):
+@pytest.mark.parametrize("precision,ref", [("fp32", 0), ("fp16dev", 0), ("bf16dev", 0), ("fp16dev", COUETTE),
+                                           ("bf16dev", COUETTE)])
+def test_row_kernels_match_per_node_kernels(fre, orc, case, precision, ref):
     """The row kernels and the per-node kernels compute the same update,
     arranged differently (the row kernels split the collision into parts
     even and odd in c_i and keep 16-bit f as deviations), so their rounding
@@ -61,10 +65,13 @@ def test_row_kernels_match_per_node_kernels(fre, orc, case, precision):
     rho and phi and 1e-4 on u against max(|u|, 0.01), i.e. 1e-6 absolute
     (populations up to ~0.5 round to ~3e-8 per step in FP32; 200 steps of
     such errors stay below 1e-6 in the velocity moments), FP16 3e-3, BF16
-    2e-2 (the 16-bit bounds of the D3Q19 test below)."""
+    2e-2 (the 16-bit bounds of the D3Q19 test below), with f stored against
+    the rest equilibrium (ref 0) or the Couette equilibrium of the shear
+    walls (FRE_FLAG_COUETTE_REFERENCE; the periodic device has no walls and
+    keeps the rest equilibrium)."""
     lattice, device, nx, ny, nz, kw = case
-    rows = make(fre, lattice, device, nx, ny, nz, precision, **kw)
-    gen = make(fre, lattice, device, nx, ny, nz, precision, flags=1, **kw)
+    rows = make(fre, lattice, device, nx, ny, nz, precision, flags=ref, **kw)
+    gen = make(fre, lattice, device, nx, ny, nz, precision, flags=1 | ref, **kw)
     assert rows.row_kernels and not gen.row_kernels
     a = dict(tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0, rho0=1.0)
     a.update(kw)
@@ -104,13 +111,15 @@ def test_row_kernels_random_populations_fp32(fre, orc):
         assert np.abs(a[k] - b[k]).max() < 1e-6, k
 
 
-@pytest.mark.parametrize("precision,tol", [("fp16dev", 3e-3), ("bf16dev", 2e-2)])
-def test_16bit_storage_vs_fp64_oracle(fre, orc, precision, tol):
+@pytest.mark.parametrize("precision,ref,tol", [("fp16dev", 0, 3e-3), ("bf16dev", 0, 2e-2),
+                                               ("fp16dev", COUETTE, 3e-4), ("bf16dev", COUETTE, 3e-3)])
+def test_16bit_storage_vs_fp64_oracle(fre, orc, precision, ref, tol):
     """16-bit deviation storage (FP32 arithmetic) vs the FP64 oracle after 500
-    steps of the D3Q19 shear droplet: relative L-inf of rho, u, phi."""
+    steps of the D3Q19 shear droplet: relative L-inf of rho, u, phi, with f
+    stored against the rest equilibrium or the Couette equilibrium."""
     nx, ny, nz = 64, 24, 16
     kw = dict(u_wall=0.03, tau_f=2.0, tau_g=2.0, gamma_mob=0.5)
-    sim = make(fre, "d3q19", "shear", nx, ny, nz, precision, **kw)
+    sim = make(fre, "d3q19", "shear", nx, ny, nz, precision, flags=ref, **kw)
     assert sim.row_kernels
     o = orc.Oracle(1, 0, nx, ny, nz, 2.0, 2.0, 0.04, 0.04, 0.5, 0.03, 1.0)
     c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, 6.0)
@@ -119,5 +128,5 @@ def test_16bit_storage_vs_fp64_oracle(fre, orc, precision, tol):
     sim.step(500)
     o.step(500)
     e = errs(sim.fields(), o.fields())
-    print(precision, e)
+    print(precision, ref, e)
     assert max(e.values()) < tol, e
