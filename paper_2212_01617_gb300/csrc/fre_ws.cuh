@@ -1063,17 +1063,36 @@ struct WsRowLaunchers {
                                        LaunchShape::blocks_per_sm((const void *)fn, threads, smem));
         fn<<<g, threads, smem, L.stream>>>(L, nu);
     }
+    // resident blocks per SM of one launch shape
+    template <int KIND, bool PULL, int NST, int R, int NXC>
+    static int resident(const Launch &L) {
+        const int nx = L.G.nx;
+        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
+        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
+        static size_t attr = 0;
+        if (smem > attr) {
+            attr = smem;
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }
+        return LaunchShape::blocks_per_sm((const void *)fn, nx / 2 + 32, smem);
+    }
+    // a third stage deepens the copy pipeline, but on short rows (few
+    // consumer warps per block) it can cost a resident block: keep it only
+    // where the SM holds as many blocks with it as with two
+    template <int KIND, bool PULL, int R, int NXC>
+    static void run_n(const Launch &L) {
+        if (nst<KIND, R>(L.G.nx) >= 3 &&
+            resident<KIND, PULL, 3, R, NXC>(L) >= resident<KIND, PULL, 2, R, NXC>(L))
+            launch<KIND, PULL, 3, R, NXC>(L);
+        else
+            launch<KIND, PULL, 2, R, NXC>(L);
+    }
     template <int KIND, bool PULL, int R>
     static void run_r(const Launch &L) {
         // rows of 512 nodes (the common large-lattice case) take the
         // compile-time row length
-        if (PULL && L.G.nx == 512) {
-            if (nst<KIND, R>(512) >= 3) launch<KIND, PULL, 3, R, 512>(L);
-            else launch<KIND, PULL, 2, R, 512>(L);
-            return;
-        }
-        if (nst<KIND, R>(L.G.nx) >= 3) launch<KIND, PULL, 3, R, 0>(L);
-        else launch<KIND, PULL, 2, R, 0>(L);
+        if (PULL && L.G.nx == 512) run_n<KIND, PULL, R, 512>(L);
+        else run_n<KIND, PULL, R, 0>(L);
     }
     template <int KIND, bool PULL>
     static void run(const Launch &L) {
