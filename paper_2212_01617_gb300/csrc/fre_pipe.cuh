@@ -49,8 +49,31 @@ __device__ __forceinline__ Unit unit_at(const Geo &G, int W, int b) {
     return u;
 }
 
-// Launch shape of the persistent kernels: SM count and resident blocks.
+// Launch shape of the persistent kernels: SM count, resident blocks and the
+// dynamic shared-memory opt-in.
 struct LaunchShape {
+    // raise a kernel's dynamic shared-memory opt-in to at least `smem`; one
+    // record per kernel, so that no caller lowers what another one raised
+    // (a launch above the opt-in fails with an invalid-argument error)
+    static void opt_in(const void *fn, size_t smem) {
+        static const void *fns[128] = {};
+        static size_t vals[128] = {};
+        static int n = 0;
+        for (int k = 0; k < n; ++k) {
+            if (fns[k] != fn) continue;
+            if (smem > vals[k]) {
+                vals[k] = smem;
+                cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            }
+            return;
+        }
+        if (n < 128) {
+            fns[n] = fn;
+            vals[n] = smem;
+            ++n;
+        }
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
     // resident blocks per SM of a kernel (cached per kernel and block size)
     static int blocks_per_sm(const void *fn, int threads, size_t smem) {
         static const void *last_fn[16] = {};

@@ -370,11 +370,7 @@ struct WsLaunchers {
         const int nu = (int)((size_t)L.G.ny * L.G.nz * (L.G.nx / W));
         const size_t smem = (size_t)NST * WsRows<Q, FMT, KIND>::stage_bytes(W);
         auto fn = k_ws<Q, FMT, KIND, PULL, NST>;
-        static bool attr = false;
-        if (!attr) {
-            attr = true;
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        }
+        LaunchShape::opt_in((const void *)fn, kMaxSmem);
         const int g = std::min(nu, LaunchShape::sms() *
                                        LaunchShape::blocks_per_sm((const void *)fn, W + 32, smem));
         fn<<<g, W + 32, smem, L.stream>>>(L, W, nu);
@@ -1051,13 +1047,7 @@ struct WsRowLaunchers {
         const int nu = (L.G.ny / R) * L.G.nz;
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
-        // opt in to exactly the shared memory this launch needs (a larger
-        // opt-in would shrink the L1 share of the SM's on-chip memory)
-        static size_t attr = 0;
-        if (smem > attr) {
-            attr = smem;
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        }
+        LaunchShape::opt_in((const void *)fn, smem);
         const int threads = nx / 2 + 32;
         const int g = std::min(nu, LaunchShape::sms() *
                                        LaunchShape::blocks_per_sm((const void *)fn, threads, smem));
@@ -1069,11 +1059,7 @@ struct WsRowLaunchers {
         const int nx = L.G.nx;
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
-        static size_t attr = 0;
-        if (smem > attr) {
-            attr = smem;
-            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        }
+        LaunchShape::opt_in((const void *)fn, smem);
         return LaunchShape::blocks_per_sm((const void *)fn, nx / 2 + 32, smem);
     }
     // a third stage deepens the copy pipeline, but on short rows (few
