@@ -557,28 +557,47 @@ __host__ __device__ constexpr int pair_index(int i) {
 // + sum_i c_i o_i; 4 s_0; 5 unused; 6 + 2p, 7 + 2p the parts of s_i even
 // and odd in c_i of opposite pair p, (s_i + s_opp(i)) / 2 and
 // (s_i - s_opp(i)) / 2.  Lane l of the calling warp takes population l.
+// What couette_consts needs of the producer lane's population, computed
+// once per block: the lookups by a run-time direction index (velocity,
+// weight, opposite, pair slot) would otherwise be redone for every row, as
+// the mbarrier waits keep the compiler from hoisting them.
+struct CoLane {
+    float wr, cx, cy, cz, a, b, uwl;
+    int ciy, jl, slot;  // c_iy; lane of opp(i); output entry of its pair (-1: none)
+};
+template <int Q>
+__device__ __forceinline__ CoLane co_lane(const Launch &L, int lane) {
+    CoLane c;
+    const int i = lane < Q ? lane : 0;
+    c.ciy = Lat<Q>::cy(i);
+    c.cx = float(Lat<Q>::cx(i));
+    c.cy = float(c.ciy);
+    c.cz = float(Lat<Q>::cz(i));
+    c.wr = lane < Q ? float(Lat<Q>::w(i)) * L.F.rho0 : 0.f;
+    c.a = 4.5f * c.cx * c.cx - 1.5f;
+    c.b = 3.f * c.cx;
+    c.uwl = c.ciy > 0 ? -L.F.uwall : L.F.uwall;
+    c.jl = lane < Q ? Lat<Q>::opp(i) : lane;
+    c.slot = (lane >= 1 && lane < Q && Lat<Q>::opp(i) > i) ? 6 + 2 * pair_index<Q>(i) : -1;
+    return c;
+}
+
 template <int Q, bool PULL>
-__device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *out, int lane) {
+__device__ __forceinline__ void couette_consts(const Launch &L, const CoLane &c, int y, float2 *out, int lane) {
     const bool shear = L.G.device == FRE_SHEAR;
     const float rho0 = L.F.rho0, om = L.F.omega_f;
     const float U = couette_u(L, y);
-    const int i = lane < Q ? lane : 0;
-    const int ciy = Lat<Q>::cy(i);
-    const float cx = float(Lat<Q>::cx(i)), cy = float(ciy), cz = float(Lat<Q>::cz(i));
-    const float wr = lane < Q ? float(Lat<Q>::w(i)) * rho0 : 0.f;
-    const float a = 4.5f * cx * cx - 1.5f, b = 3.f * cx;
     float o = 0.f;
     if (PULL) {
-        if (shear && ((y == 0 && ciy > 0) || (y == L.G.ny - 1 && ciy < 0))) {
-            const float uwl = ciy > 0 ? -L.F.uwall : L.F.uwall;
-            o = wr * 6.f * cx * (uwl - U);
+        if (shear && ((y == 0 && c.ciy > 0) || (y == L.G.ny - 1 && c.ciy < 0))) {
+            o = c.wr * 6.f * c.cx * (c.uwl - U);
         } else {
-            const float e = couette_u(L, y - ciy) - U;
-            o = wr * (b * e + a * (2.f * U + e) * e);
+            const float e = couette_u(L, y - c.ciy) - U;
+            o = c.wr * (c.b * e + c.a * (2.f * U + e) * e);
         }
     }
-    const float si = (1.f - om) * o - om * wr * (b * U + a * U * U);
-    float so = o, sx = cx * o, sy = cy * o, sz = cz * o;
+    const float si = (1.f - om) * o - om * c.wr * (c.b * U + c.a * U * U);
+    float so = o, sx = c.cx * o, sy = c.cy * o, sz = c.cz * o;
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) {
         so += __shfl_xor_sync(0xffffffffu, so, m);
@@ -586,7 +605,7 @@ __device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *o
         sy += __shfl_xor_sync(0xffffffffu, sy, m);
         sz += __shfl_xor_sync(0xffffffffu, sz, m);
     }
-    const float sj = __shfl_sync(0xffffffffu, si, lane < Q ? Lat<Q>::opp(i) : lane);
+    const float sj = __shfl_sync(0xffffffffu, si, c.jl);
     if (lane == 0) {
         out[0] = make_float2(so, so);
         out[1] = make_float2(rho0 * U + sx, rho0 * U + sx);
@@ -594,11 +613,10 @@ __device__ __forceinline__ void couette_consts(const Launch &L, int y, float2 *o
         out[3] = make_float2(sz, sz);
         out[4] = make_float2(si, si);
         out[5] = make_float2(0.f, 0.f);
-    } else if (lane < Q && Lat<Q>::opp(i) > i) {
-        const int p = pair_index<Q>(i);
+    } else if (c.slot >= 0) {
         const float e = 0.5f * (si + sj), d = 0.5f * (si - sj);
-        out[6 + 2 * p] = make_float2(e, e);
-        out[7 + 2 * p] = make_float2(d, d);
+        out[c.slot] = make_float2(e, e);
+        out[c.slot + 1] = make_float2(d, d);
     }
 }
 
@@ -639,6 +657,7 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
 
     if (producer) {
         const int lane = threadIdx.x - ncons;
+        const CoLane col = co_lane<Q>(L, lane);
         int k = 0;
         for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
             const int s = k % NST;
@@ -732,7 +751,7 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
             }
             if constexpr (CST) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) couette_consts<Q, PULL>(L, y0 + r, cst_s[k % (NST + 1)][r], lane);
+                for (int r = 0; r < R; ++r) couette_consts<Q, PULL>(L, col, y0 + r, cst_s[k % (NST + 1)][r], lane);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar);
             }
