@@ -620,10 +620,18 @@ __device__ __forceinline__ void couette_consts(const Launch &L, const CoLane &c,
     }
 }
 
+// Rows of a work unit the update runs side by side (one consumer group of
+// nx/2 threads each); the phi and mu passes loop over the rows of a unit.
+template <int KIND, int R>
+struct RowsPar {
+    static constexpr int V = KIND == WS_UPDATE ? R : 1;
+};
+
 // NXC: the row length as a compile-time constant (every shared-memory
 // offset then folds into the instruction), or 0 to take it from the launch.
 template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC>
-__global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
+__global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPDATE ? 1 : 2)
+    k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
     using FL = RowsLayout<Q, FMT, KIND, R>;
     constexpr bool DEV = Fmt<FMT>::DEV;
@@ -640,7 +648,10 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
     const int nx = NXC ? NXC : L.G.nx;
     const int ny = L.G.ny, nz = L.G.nz;
     const int nyu = ny / R;  // units per z plane
-    const int ncons = nx / 2;  // consumer thread t updates x = 2t, 2t + 1
+    // the update takes the R rows of a unit side by side, one group of nx/2
+    // consumer threads per row; thread t of a group updates x = 2t, 2t + 1
+    constexpr int RP = RowsPar<KIND, R>::V;
+    const int ncons = RP * (nx / 2);
     const bool producer = threadIdx.x >= ncons;
     const unsigned stage_bytes = FL::stage(nx);
     const bool shear = L.G.device == FRE_SHEAR;
@@ -763,7 +774,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
     const float rho0 = L.F.rho0;
     const float *__restrict__ php = static_cast<const float *>(L.phi_prev);
     const long long np = L.G.np;
-    const int x0 = 2 * threadIdx.x;
+    const int x0 = 2 * (threadIdx.x % (nx / 2));
+    const int rg = RP > 1 ? threadIdx.x / (nx / 2) : 0;  // this group's row of the unit
     int k = 0;
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
         const int s = k % NST;
@@ -842,7 +854,7 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
             const float of = L.F.omega_f, og = L.F.omega_g;
             const float kf = L.F.kf;
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) {
+            for (int r = rg; r < R; r += RP) {
                 const unsigned wall = wall_s[s][r];
                 const int y = y0 + r;
                 const size_t row = ((size_t)z * ny + y) * nx;
@@ -861,14 +873,45 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                         prefetch_l1(muf + kn);
                     }
                 }
-                // ---- read phase: pulled populations (16-bit f: deviations
-                // from the reference of the row they were stored in), then
-                // the stencil values of phi and mu
-                float2 f[Q], g[Q];
-                // rows without wall links (all but the first and last of the
-                // shear device) take every shift as a compile-time constant
-                auto pull = [&](auto walls) {
-                    constexpr bool WL = decltype(walls)::value;
+                // With the rows of a unit side by side (RP > 1, 17 warps and
+                // 96 registers per thread) the update runs in two phases, so
+                // that the f and g populations are never held in registers
+                // together: f (pull, moments, force, velocity, collision,
+                // stores), then g (pull, phi, collision, stores).  With one
+                // consumer group (168 registers) both pulls come first and the
+                // stage is released before any collision.  Rows without wall
+                // links (all but the first and last of the shear device) take
+                // every x shift as a compile-time constant.
+                constexpr bool TWO = RP > 1;
+                const bool walls = PULL && wall != 0u;
+                // ---- f: pulled populations (16-bit: deviations from the
+                // reference of the row they were stored in)
+                float2 f[Q];
+                auto pull_f = [&](auto wl_t) {
+                    constexpr bool WL = decltype(wl_t)::value;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        const bool wl = WL && Lat<Q>::cy(i) != 0 && ((wall >> i) & 1u);
+                        const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
+                        float2 fv = ld_shift(reinterpret_cast<const S *>(cur + FL::f_row(nx, i, r)), x0, cx, nx);
+                        if constexpr (!DEV) {
+                            if (wl) {
+                                // the row of opp(i) at this node plus the
+                                // moving-wall term 2 w_i rho0 (c_i . u_w) / cs^2
+                                // (16-bit f: part of the row constants)
+                                const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
+                                fv = add2(fv, p2(float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw * rho0));
+                            }
+                        }
+                        f[i] = fv;
+                    }
+                };
+                if (walls) pull_f(std::true_type{});
+                else pull_f(std::false_type{});
+                // ---- g: pulled populations (now, or after the f collision)
+                float2 g[Q];
+                auto pull_g = [&](auto wl_t) {
+                    constexpr bool WL = decltype(wl_t)::value;
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
                         const bool wl = WL && Lat<Q>::cy(i) != 0 && ((wall >> i) & 1u);
@@ -876,22 +919,21 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                         float2 gv;
                         if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
                         else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
-                        float2 fv = ld_shift(reinterpret_cast<const S *>(cur + FL::f_row(nx, i, r)), x0, cx, nx);
                         if (wl) {
-                            // the row of opp(i) at this node: add the moving-wall
-                            // term 2 w_i a (c_i . u_w) / cs^2
+                            // the row of opp(i) at this node plus the
+                            // moving-wall term 2 w_i phi(t-1) (c_i . u_w) / cs^2
                             const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
                             const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
-                            // (16-bit f: the wall term is part of the row constants)
-                            if constexpr (!DEV) fv = add2(fv, p2(w2cu * rho0));
                             gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
                         }
-                        f[i] = fv;
                         g[i] = gv;
                     }
                 };
-                if (PULL && wall != 0u) pull(std::true_type{});
-                else pull(std::false_type{});
+                if constexpr (!TWO) {
+                    if (walls) pull_g(std::true_type{});
+                    else pull_g(std::false_type{});
+                }
+                // stencil values of phi and mu: F = mu grad(phi) - grad(phi mu)
                 float2 gpx = p2(0.f), gpy = p2(0.f), gpz = p2(0.f), gqx = p2(0.f), gqy = p2(0.f), gqz = p2(0.f);
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
@@ -921,14 +963,15 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                     if (Lat<Q>::cz(i)) { gpz = fma2(p2(w * Lat<Q>::cz(i)), dp, gpz); gqz = fma2(p2(w * Lat<Q>::cz(i)), dq, gqz); }
                 }
                 const float2 mu = ld_pair(reinterpret_cast<const float *>(cur + FL::fld_row(nx, 1, FL::fk(0, 0, r))), x0);
-                if (r == R - 1) {
+                if (!TWO && r + RP >= R) {
                     // this warp is done with the stage
                     __syncwarp();
                     if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
                 }
 
                 // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
-                float2 sf = f[0], ph = g[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
+                float2 sf = f[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
+                float2 ph = TWO ? p2(0.f) : g[0];
                 // 16-bit f: row constants (offsets o_i summed into the moments)
                 const float4 *cst = reinterpret_cast<const float4 *>(cst_s[CST ? k % (NST + 1) : 0][r]);
                 if constexpr (CST) {
@@ -941,7 +984,7 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     sf = add2(sf, f[i]);
-                    ph = add2(ph, g[i]);
+                    if constexpr (!TWO) ph = add2(ph, g[i]);
                     jx = acc_c(jx, f[i], Lat<Q>::cx(i));
                     jy = acc_c(jy, f[i], Lat<Q>::cy(i));
                     jz = acc_c(jz, f[i], Lat<Q>::cz(i));
@@ -959,14 +1002,33 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                 const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
                 const float2 uF = fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz)));
                 const float2 omf = p2(1.f - of), omg = p2(1.f - og);
-                const float2 gmu3 = mul2(p2(L.F.gamma3), mu);
                 const float2 m15usq = mul2(p2(-1.5f), usq);
                 const float2 m3uF = mul2(p2(-3.f), uF);
+                const float2 gmu3 = mul2(p2(L.F.gamma3), mu);
+                // collision of the g pair (i, opp(i)) (Eq. LBEg, geq) and its
+                // stores; cu3 = 3 c_i.u, E = 4.5 (c_i.u)^2 - 1.5 u^2
+                float2 gsum = p2(0.f);
+                S *gp = static_cast<S *>(L.dst.g) + row + x0;
+                auto collide_g = [&](int i, int j, float w, float2 cu3, float2 E) {
+                    const float2 wg = p2(og * w);
+                    const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
+                    const float2 Bg = mul2(mul2(wg, ph), cu3);
+                    const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
+                    if constexpr (DEV) {
+                        // the rest population of g closes sum_i g*_i = phi on
+                        // the values as they are stored
+                        gsum = add2(gsum, add2(st_pair(gp + (size_t)(i - 1) * np, gi),
+                                               st_pair(gp + (size_t)(j - 1) * np, gj)));
+                    } else {
+                        st_pair(gp + (size_t)i * np, gi);
+                        st_pair(gp + (size_t)j * np, gj);
+                        gsum = add2(gsum, add2(gi, gj));
+                    }
+                };
 
-                // ---- collision (Eq. bgk, feq, Fi, LBEg, geq) and stores
+                // ---- collision of f (Eq. bgk, feq, Fi) and stores
                 const size_t off = row + x0;
                 S *fp = static_cast<S *>(L.dst.f) + off;
-                S *gp = static_cast<S *>(L.dst.g) + off;
                 {
                     const float w0 = float(Lat<Q>::w(0));
                     // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F [+ s_0]
@@ -975,9 +1037,8 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                     st_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), S0)));
                 }
                 // moving populations in opposite pairs (i, opp(i)): the
-                // equilibria and the Guo term split into parts even and odd
+                // equilibrium and the Guo term split into parts even and odd
                 // in c_i that the pair shares
-                float2 gsum = p2(0.f);
 #pragma unroll
                 for (int i = 1; i < Q; ++i) {
                     if (Lat<Q>::opp(i) < i) continue;
@@ -1004,22 +1065,32 @@ __global__ void __launch_bounds__(256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(L
                         Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), GA));
                         Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
                     }
-                    const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
-                    const float2 wg = p2(og * w);
-                    const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
-                    const float2 Bg = mul2(mul2(wg, ph), cu3);
-                    const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
-                    st_pair(fp + (size_t)i * np, fi);
-                    st_pair(fp + (size_t)j * np, fj);
-                    if constexpr (DEV) {
-                        // the rest population of g closes sum_i g*_i = phi on
-                        // the values as they are stored
-                        gsum = add2(gsum, add2(st_pair(gp + (size_t)(i - 1) * np, gi),
-                                               st_pair(gp + (size_t)(j - 1) * np, gj)));
-                    } else {
-                        st_pair(gp + (size_t)i * np, gi);
-                        st_pair(gp + (size_t)j * np, gj);
-                        gsum = add2(gsum, add2(gi, gj));
+                    st_pair(fp + (size_t)i * np, fma2(omf, f[i], add2(Af, Bf)));
+                    st_pair(fp + (size_t)j * np, fma2(omf, f[j], sub2(Af, Bf)));
+                    if constexpr (!TWO) collide_g(i, j, w, cu3, E);
+                }
+
+                if constexpr (TWO) {
+                    if (walls) pull_g(std::true_type{});
+                    else pull_g(std::false_type{});
+                    if (r + RP >= R) {
+                        // this warp is done with the stage
+                        __syncwarp();
+                        if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
+                    }
+                    // ---- phi (Eq. ordeMoment) and the collision of g
+                    ph = g[0];
+#pragma unroll
+                    for (int i = 1; i < Q; ++i) ph = add2(ph, g[i]);
+#pragma unroll
+                    for (int i = 1; i < Q; ++i) {
+                        if (Lat<Q>::opp(i) < i) continue;
+                        float2 cu = p2(0.f);
+                        cu = acc_c(cu, ux, Lat<Q>::cx(i));
+                        cu = acc_c(cu, uy, Lat<Q>::cy(i));
+                        cu = acc_c(cu, uz, Lat<Q>::cz(i));
+                        const float2 cu3 = mul2(p2(3.f), cu);
+                        collide_g(i, Lat<Q>::opp(i), float(Lat<Q>::w(i)), cu3, fma2(mul2(p2(1.5f), cu3), cu, m15usq));
                     }
                 }
                 if constexpr (DEV) st_pair(L.dst.g0 + off, sub2(ph, gsum));
@@ -1067,7 +1138,7 @@ struct WsRowLaunchers {
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
         LaunchShape::opt_in((const void *)fn, smem);
-        const int threads = nx / 2 + 32;
+        const int threads = RowsPar<KIND, R>::V * (nx / 2) + 32;
         const int g = std::min(nu, LaunchShape::sms() *
                                        LaunchShape::blocks_per_sm((const void *)fn, threads, smem));
         fn<<<g, threads, smem, L.stream>>>(L, nu);
@@ -1079,7 +1150,7 @@ struct WsRowLaunchers {
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
         LaunchShape::opt_in((const void *)fn, smem);
-        return LaunchShape::blocks_per_sm((const void *)fn, nx / 2 + 32, smem);
+        return LaunchShape::blocks_per_sm((const void *)fn, RowsPar<KIND, R>::V * (nx / 2) + 32, smem);
     }
     // a third stage deepens the copy pipeline, but on short rows (few
     // consumer warps per block) it can cost a resident block: keep it only
