@@ -404,8 +404,9 @@ namespace fre {
 // Full-row variants: one work unit = one whole x-row (y, z), so every staged
 // row is a single large bulk copy (nx * element bytes) -- few, large TMA
 // operations keep HBM busy where many small ones do not.  The periodic x
-// shift is a modular index into the staged row.  Consumer thread t updates
-// the adjacent nodes x = 2t, 2t + 1 and stores 2-wide vectors.
+// shift is a modular index into the staged row.  Consumer thread t of a
+// row's group updates the adjacent nodes x = 2t, 2t + 1 and stores 2-wide
+// vectors (the update gives each row of a unit its own group).
 //   KIND WS_PHI   : stages the q pulled g rows, writes phi
 //   KIND WS_MU    : stages the phi rows of the stencil, writes mu
 //   KIND WS_UPDATE: stages the 2q pulled f and g rows; the phi/mu stencil
@@ -862,8 +863,7 @@ __global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPD
                 // FP32: start the lines of the off-axis stencil values (c_y and
                 // c_z both nonzero, read from global memory below) toward L1
                 // before the pull phase (measured 2% on the update; the
-                // 16-bit update, latency-bound at 9 warps per SM, gains
-                // nothing from it and loses L1 room)
+                // latency-bound 16-bit update gained nothing from it)
                 if constexpr (!DEV) {
 #pragma unroll
                     for (int kk = 1; kk < Q; ++kk) {
@@ -1104,9 +1104,9 @@ template <int Q, int FMT>
 struct WsRowLaunchers {
     using S = typename Fmt<FMT>::S;
     static constexpr int kMaxSmem = 225 * 1024;
-    // stages per block: the update takes as many as fit (one block per SM);
-    // the lighter phi and mu passes take two, so that two blocks (two
-    // producer warps issuing bulk copies) share an SM
+    // stages per block: the update takes up to three of those that fit (one
+    // block per SM on long rows); the lighter phi and mu passes take two, so
+    // that two blocks (two producer warps issuing bulk copies) share an SM
     template <int KIND, int R>
     static int nst(int nx) {
         const unsigned sb = RowsLayout<Q, FMT, KIND, R>::stage(nx);
