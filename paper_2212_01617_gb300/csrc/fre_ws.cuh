@@ -621,8 +621,12 @@ __device__ __forceinline__ void couette_consts(const Launch &L, const CoLane &c,
     }
 }
 
-// Rows of a work unit the update runs side by side (one consumer group of
-// nx/2 threads each); the phi and mu passes loop over the rows of a unit.
+// Rows of a work unit run side by side, one consumer group of nx/2 threads
+// each (the kernel's RPX): the update takes all R rows of a unit at once;
+// the phi and mu passes loop over them, except on rows whose half length is
+// not a whole number of warps (nx a multiple of 32 but not of 64), where
+// every pass takes two rows side by side so that the consumers fill whole
+// warps.
 template <int KIND, int R>
 struct RowsPar {
     static constexpr int V = KIND == WS_UPDATE ? R : 1;
@@ -630,9 +634,8 @@ struct RowsPar {
 
 // NXC: the row length as a compile-time constant (every shared-memory
 // offset then folds into the instruction), or 0 to take it from the launch.
-template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC>
-__global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPDATE ? 1 : 2)
-    k_wsrow(Launch L, int nunits) {
+template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC, int RPX>
+__global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
     using FL = RowsLayout<Q, FMT, KIND, R>;
     constexpr bool DEV = Fmt<FMT>::DEV;
@@ -651,7 +654,8 @@ __global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPD
     const int nyu = ny / R;  // units per z plane
     // the update takes the R rows of a unit side by side, one group of nx/2
     // consumer threads per row; thread t of a group updates x = 2t, 2t + 1
-    constexpr int RP = RowsPar<KIND, R>::V;
+    constexpr int RP = RPX;
+    static_assert(R % RP == 0, "rows side by side must divide the rows of a unit");
     const int ncons = RP * (nx / 2);
     const bool producer = threadIdx.x >= ncons;
     const unsigned stage_bytes = FL::stage(nx);
@@ -791,9 +795,11 @@ __global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPD
         const int y0 = (unit % nyu) * R, z = unit / nyu;
 
         if constexpr (KIND == WS_PHI) {
-            float2 out[R];
+            constexpr int RT = R / RP;  // rows of this thread's group
+            float2 out[RT];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int q = 0; q < RT; ++q) {
+                const int r = rg + q * RP;
                 const unsigned wall = wall_s[s][r];
                 const size_t row = ((size_t)z * ny + y0 + r) * nx;
                 // rows without wall links (all but the first and last of the
@@ -817,17 +823,19 @@ __global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPD
                     }
                     return sum;
                 };
-                out[r] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
+                out[q] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
+            for (int q = 0; q < RT; ++q)
+                st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
         } else if constexpr (KIND == WS_MU) {
-            float2 out[R];
+            constexpr int RT = R / RP;  // rows of this thread's group
+            float2 out[RT];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int q = 0; q < RT; ++q) {
+                const int r = rg + q * RP;
                 const float *c0 = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(0, 0, r)));
                 const float2 p0 = ld_pair(c0, x0);
                 float2 lap = p2(0.f);
@@ -840,14 +848,14 @@ __global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPD
                 }
                 lap = mul2(p2(6.f), lap);
                 // A (phi^3 - phi) - kappa lap
-                out[r] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
+                out[q] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
                               mul2(p2(L.F.kappa), lap));
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-                st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + r) * nx + x0, out[r]);
+            for (int q = 0; q < RT; ++q)
+                st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
         } else {
             // ---------------------------------------------------- update
             const float *__restrict__ phif = static_cast<const float *>(L.phi);
@@ -1029,13 +1037,19 @@ __global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPD
                 // ---- collision of f (Eq. bgk, feq, Fi) and stores
                 const size_t off = row + x0;
                 S *fp = static_cast<S *>(L.dst.f) + off;
-                {
+                if constexpr (DEV) {
+                    // 16-bit: the rest population by its own BGK formula
+                    // (it is rounded to 16 bits as stored anyway):
+                    // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F + s_0
                     const float w0 = float(Lat<Q>::w(0));
-                    // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F [+ s_0]
                     const float2 S0 = CST ? fma2(p2(kf * w0), m3uF, make_float2(cst[2].x, cst[2].y))
                                           : mul2(p2(kf * w0), m3uF);
                     st_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), S0)));
                 }
+                // FP32: the rest population closes sum_i f*_i = rho below (mass
+                // is a collision invariant; its own formula would drift the
+                // mass by the FP32 rounding of the weights every step)
+                float2 fsum = p2(0.f);
                 // moving populations in opposite pairs (i, opp(i)): the
                 // equilibrium and the Guo term split into parts even and odd
                 // in c_i that the pair shares
@@ -1065,10 +1079,13 @@ __global__ void __launch_bounds__(RowsPar<KIND, R>::V * 256 + 32, KIND == WS_UPD
                         Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), GA));
                         Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
                     }
-                    st_pair(fp + (size_t)i * np, fma2(omf, f[i], add2(Af, Bf)));
-                    st_pair(fp + (size_t)j * np, fma2(omf, f[j], sub2(Af, Bf)));
+                    const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
+                    st_pair(fp + (size_t)i * np, fi);
+                    st_pair(fp + (size_t)j * np, fj);
+                    if constexpr (!DEV) fsum = add2(fsum, add2(fi, fj));
                     if constexpr (!TWO) collide_g(i, j, w, cu3, E);
                 }
+                if constexpr (!DEV) st_pair(fp, sub2(rho, fsum));
 
                 if constexpr (TWO) {
                     if (walls) pull_g(std::true_type{});
@@ -1121,6 +1138,8 @@ struct WsRowLaunchers {
         // the mu pass stages three copies per unit whatever R: four rows per
         // unit keep it off the copy engine's rate of operations
         if (KIND == WS_MU) return G.ny % 4 == 0 ? 4 : (G.ny % 2 == 0 ? 2 : 1);
+        // rows of an odd number of half warps: two rows side by side always
+        if (G.nx % 64 != 0) return 2;
         if (!pull || G.ny % 2 != 0) return 1;
         if (RowsLayout<Q, FMT, KIND, 1>::rowb(G.nx) >= 2048) return 1;
         return nst<KIND, 2>(G.nx) >= 2 ? 2 : 1;
@@ -1128,63 +1147,72 @@ struct WsRowLaunchers {
     static bool usable(const Geo &G) {
         if (G.device == FRE_FOUR_ROLLER) return false;
         if ((G.np * sizeof(S)) % 16 != 0 || (G.nx * sizeof(S)) % 16 != 0 || (G.nx * 4) % 16 != 0) return false;
-        if (G.nx < 64 || G.nx > 512 || G.nx % 64 != 0) return false;
+        // rows of a whole number of warps' pairs (nx a multiple of 64), or of
+        // an odd number of half warps taken two rows at a time (ny even)
+        if (G.nx < 64 || G.nx > 512 || G.nx % 32 != 0) return false;
+        if (G.nx % 64 != 0 && (G.ny % 2 != 0 || nst<WS_UPDATE, 2>(G.nx) < 2 || nst<WS_PHI, 2>(G.nx) < 2 ||
+                               nst<WS_MU, 2>(G.nx) < 2 || nst<WS_MU, 4>(G.nx) < 2))
+            return false;
         return nst<WS_UPDATE, 1>(G.nx) >= 2 && nst<WS_PHI, 1>(G.nx) >= 1 && nst<WS_MU, 1>(G.nx) >= 1;
     }
-    template <int KIND, bool PULL, int NST, int R, int NXC>
+    template <int KIND, bool PULL, int NST, int R, int NXC, int RPX>
     static void launch(const Launch &L) {
         const int nx = L.G.nx;
         const int nu = (L.G.ny / R) * L.G.nz;
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
-        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
+        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX>;
         LaunchShape::opt_in((const void *)fn, smem);
-        const int threads = RowsPar<KIND, R>::V * (nx / 2) + 32;
+        const int threads = RPX * (nx / 2) + 32;
         const int g = std::min(nu, LaunchShape::sms() *
                                        LaunchShape::blocks_per_sm((const void *)fn, threads, smem));
         fn<<<g, threads, smem, L.stream>>>(L, nu);
     }
     // resident blocks per SM of one launch shape
-    template <int KIND, bool PULL, int NST, int R, int NXC>
+    template <int KIND, bool PULL, int NST, int R, int NXC, int RPX>
     static int resident(const Launch &L) {
         const int nx = L.G.nx;
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
-        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC>;
+        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX>;
         LaunchShape::opt_in((const void *)fn, smem);
-        return LaunchShape::blocks_per_sm((const void *)fn, RowsPar<KIND, R>::V * (nx / 2) + 32, smem);
+        return LaunchShape::blocks_per_sm((const void *)fn, RPX * (nx / 2) + 32, smem);
     }
     // a third stage deepens the copy pipeline, but on short rows (few
     // consumer warps per block) it can cost a resident block: keep it only
     // where the SM holds as many blocks with it as with two
-    template <int KIND, bool PULL, int R, int NXC>
+    template <int KIND, bool PULL, int R, int NXC, int RPX>
     static void run_n(const Launch &L) {
         if (nst<KIND, R>(L.G.nx) >= 3 &&
-            resident<KIND, PULL, 3, R, NXC>(L) >= resident<KIND, PULL, 2, R, NXC>(L))
-            launch<KIND, PULL, 3, R, NXC>(L);
+            resident<KIND, PULL, 3, R, NXC, RPX>(L) >= resident<KIND, PULL, 2, R, NXC, RPX>(L))
+            launch<KIND, PULL, 3, R, NXC, RPX>(L);
         else
-            launch<KIND, PULL, 2, R, NXC>(L);
+            launch<KIND, PULL, 2, R, NXC, RPX>(L);
     }
     template <int KIND, bool PULL, int R>
     static void run_r(const Launch &L) {
-        // rows of 512 nodes (the common large-lattice case) take the
-        // compile-time row length
-        if (PULL && L.G.nx == 512) run_n<KIND, PULL, R, 512>(L);
-        else run_n<KIND, PULL, R, 0>(L);
-    }
-    template <int KIND, bool PULL>
-    static void run(const Launch &L) {
-        if constexpr (KIND == WS_MU) {
-            const int r = rows_per_unit<KIND>(L.G, PULL);
-            if (r == 4) run_r<KIND, PULL, 4>(L);
-            else if (r == 2) run_r<KIND, PULL, 2>(L);
-            else run_r<KIND, PULL, 1>(L);
-            return;
-        } else if constexpr (PULL) {
-            if (rows_per_unit<KIND>(L.G, PULL) == 2) {
-                run_r<KIND, PULL, 2>(L);
+        constexpr int RPD = RowsPar<KIND, R>::V;
+        // rows of an odd number of half warps: two rows side by side
+        if constexpr (RPD == 1 && R % 2 == 0) {
+            if (L.G.nx % 64 != 0) {
+                run_n<KIND, PULL, R, 0, 2>(L);
                 return;
             }
         }
-        run_r<KIND, PULL, 1>(L);
+        // rows of 512 nodes (the common large-lattice case) take the
+        // compile-time row length
+        if (PULL && L.G.nx == 512) run_n<KIND, PULL, R, 512, RPD>(L);
+        else run_n<KIND, PULL, R, 0, RPD>(L);
+    }
+    template <int KIND, bool PULL>
+    static void run(const Launch &L) {
+        const int r = rows_per_unit<KIND>(L.G, PULL);
+        if constexpr (KIND == WS_MU) {
+            if (r == 4) {
+                run_r<KIND, PULL, 4>(L);
+                return;
+            }
+        }
+        if (r == 2) run_r<KIND, PULL, 2>(L);
+        else run_r<KIND, PULL, 1>(L);
     }
     static void update(const Launch &L, bool pull) {
         if (pull) run<WS_UPDATE, true>(L);

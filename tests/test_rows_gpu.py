@@ -41,6 +41,10 @@ CASES = [
     ("d3q19", "shear", 512, 6, 4, dict(u_wall=0.02, tau_f=1.2)),
     # odd ny: one row per work unit in every format
     ("d2q9", "shear", 128, 37, 1, dict(u_wall=0.02)),
+    # rows of an odd number of half warps (nx a multiple of 32, not of 64):
+    # two rows side by side in every pass
+    ("d3q19", "shear", 96, 10, 6, dict(u_wall=0.03, tau_f=1.5)),
+    ("d2q9", "shear", 160, 20, 1, dict(u_wall=0.02)),
 ]
 
 
@@ -149,3 +153,15 @@ def test_launch_shapes_in_any_order(fre):
     for s in (wide, narrow):
         assert np.isfinite(s.fields()["rho"]).all()
         s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev"])
+def test_half_warp_rows_take_the_full_row_kernels(fre, precision):
+    """A 96-wide lattice (48 consumer threads per row) runs the full-row
+    kernels with two rows side by side; an odd ny (no row pairs) falls back
+    to the chunked kernels."""
+    a = make(fre, "d3q19", "shear", 96, 10, 6, precision, u_wall=0.02)
+    b = make(fre, "d3q19", "shear", 96, 9, 6, precision, u_wall=0.02)
+    assert a.kernel_path == 2 and b.kernel_path == 1, (a.kernel_path, b.kernel_path)
+    a.close()
+    b.close()
