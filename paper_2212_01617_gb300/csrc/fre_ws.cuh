@@ -1037,18 +1037,10 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 // ---- collision of f (Eq. bgk, feq, Fi) and stores
                 const size_t off = row + x0;
                 S *fp = static_cast<S *>(L.dst.f) + off;
-                if constexpr (DEV) {
-                    // 16-bit: the rest population by its own BGK formula
-                    // (it is rounded to 16 bits as stored anyway):
-                    // (1 - omega) f_0 + omega w_0 (sf - 1.5 rho u^2) - 3 kf w_0 u.F + s_0
-                    const float w0 = float(Lat<Q>::w(0));
-                    const float2 S0 = CST ? fma2(p2(kf * w0), m3uF, make_float2(cst[2].x, cst[2].y))
-                                          : mul2(p2(kf * w0), m3uF);
-                    st_pair(fp, fma2(omf, f[0], fma2(p2(of * w0), fma2(rho, m15usq, sf), S0)));
-                }
-                // FP32: the rest population closes sum_i f*_i = rho below (mass
-                // is a collision invariant; its own formula would drift the
-                // mass by the FP32 rounding of the weights every step)
+                // the rest population closes sum_i f*_i = rho below, on the
+                // values as they are stored (mass is a collision invariant;
+                // its own BGK formula would drift the mass by the FP32
+                // rounding of the weights every step)
                 float2 fsum = p2(0.f);
                 // moving populations in opposite pairs (i, opp(i)): the
                 // equilibrium and the Guo term split into parts even and odd
@@ -1080,12 +1072,18 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                         Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
                     }
                     const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
-                    st_pair(fp + (size_t)i * np, fi);
-                    st_pair(fp + (size_t)j * np, fj);
-                    if constexpr (!DEV) fsum = add2(fsum, add2(fi, fj));
+                    if constexpr (DEV) {
+                        fsum = add2(fsum, add2(st_pair(fp + (size_t)i * np, fi), st_pair(fp + (size_t)j * np, fj)));
+                    } else {
+                        st_pair(fp + (size_t)i * np, fi);
+                        st_pair(fp + (size_t)j * np, fj);
+                        fsum = add2(fsum, add2(fi, fj));
+                    }
                     if constexpr (!TWO) collide_g(i, j, w, cu3, E);
                 }
-                if constexpr (!DEV) st_pair(fp, sub2(rho, fsum));
+                // f*_0: rho - sum, or for deviations (sum_i fr_i = rho0)
+                // (rho - rho0) - sum
+                st_pair(fp, sub2(sf, fsum));
 
                 if constexpr (TWO) {
                     if (walls) pull_g(std::true_type{});

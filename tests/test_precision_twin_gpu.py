@@ -17,9 +17,9 @@ COUETTE = 4  # FRE_FLAG_COUETTE_REFERENCE
 # 11 and 8 mantissa bits of the 16-bit stores, which hold f as deviations
 # from the rest equilibrium w_i rho0 (ref 0, the configured form) or from
 # the Couette equilibrium of the walls (FRE_FLAG_COUETTE_REFERENCE).
-# Measured on a GB300: FP32 8.3e-8 / 4.9e-6 / 6.2e-6; rest reference FP16
-# 3.4e-3 / 4.7e-6 / 8.4e-6, BF16 6.4e-2 / 5.7e-6 / 5.1e-4; Couette reference
-# FP16 3.1e-5 / 5.4e-6 / 8.3e-5, BF16 1.4e-3 / 5.7e-6 / 5.7e-4 (the droplet
+# Measured on a GB300: FP32 2.7e-7 / 4.9e-6 / 2.6e-6; rest reference FP16
+# 3.2e-3 / 4.8e-6 / 2.5e-5, BF16 5.3e-2 / 5.6e-6 / 2.3e-3; Couette reference
+# FP16 4.1e-5 / 5.2e-6 / 1.1e-4, BF16 2.3e-4 / 5.8e-6 / 2.5e-4 (the droplet
 # volume is conserved to FP32 rounding in every format: the FP32 rest
 # population of g closes sum_i g_i on the stored values)
 BOUNDS = {("fp32", 0): (1e-6, 1e-5, 1e-4), ("fp16dev", 0): (1e-2, 1e-4, 1e-3), ("bf16dev", 0): (1e-1, 1e-4, 1e-2),
