@@ -555,7 +555,8 @@ __host__ __device__ constexpr int pair_index(int i) {
 //   o_i = w_i rho0 6 c_ix (u_w,i - U)        on a wall link (the local
 //         opp(i) plus the moving-wall term 2 w_i rho0 (c_i . u_w) / cs^2).
 // Entries, each a pair (v, v): 0 sum_i o_i; 1, 2, 3 the momentum rho0 U e_x
-// + sum_i c_i o_i; 4 s_0; 5 unused; 6 + 2p, 7 + 2p the parts of s_i even
+// + sum_i c_i o_i; 4 s_0 (not read: the update closes f*_0 by the mass);
+// 5 unused; 6 + 2p, 7 + 2p the parts of s_i even
 // and odd in c_i of opposite pair p, (s_i + s_opp(i)) / 2 and
 // (s_i - s_opp(i)) / 2.  Lane l of the calling warp takes population l.
 // What couette_consts needs of the producer lane's population, computed
