@@ -203,6 +203,24 @@ def test_flat_interface_tanh(orc):
     assert np.abs(ph_w - ph_e).max() < 2e-3
 
 
+def test_laplace_pressure_continuous_in_the_centroid(orc):
+    """The Laplace pressure is read at the droplet centroid by trilinear
+    interpolation of the nodal pressure, so it depends continuously on the
+    droplet position: a droplet centred on a cell face (x = 15.5) and the
+    same droplet moved by 1e-6 give the same dp to 1e-6 relative (after 200
+    steps, with the Laplace pressure established).  Read at the node nearest
+    the centroid it would jump by the difference of two node pressures."""
+    A = kappa = 0.04
+    def dp_at(cx):
+        o = orc.Oracle(0, orc.PERIODIC, 32, 32, 1, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
+        o.init_droplet(cx, 15.5, 0.0, 8.0)
+        o.step(200)
+        return o.observables()["dp"]
+    base, tiny = dp_at(15.5), dp_at(15.5 + 1e-6)
+    assert base > 0.0
+    assert abs(tiny - base) <= 1e-6 * abs(base), (base, tiny)
+
+
 def test_laplace_law(orc):
     """Static 2D droplets: dp = sigma / R with sigma = sqrt(8 kappa A / 9);
     the slope of dp against 1/R_eff is sigma within 5%."""
