@@ -206,19 +206,25 @@ def test_flat_interface_tanh(orc):
 def test_laplace_pressure_continuous_in_the_centroid(orc):
     """The Laplace pressure is read at the droplet centroid by trilinear
     interpolation of the nodal pressure, so it depends continuously on the
-    droplet position: a droplet centred on a cell face (x = 15.5) and the
-    same droplet moved by 1e-6 give the same dp to 1e-6 relative (after 200
-    steps, with the Laplace pressure established).  Read at the node nearest
-    the centroid it would jump by the difference of two node pressures."""
+    droplet position.  A sheared D2Q9 droplet centred on a cell face (x =
+    15.5) and moved by -+1e-6 in x: the two centroids lie on either side of
+    the face, where the nearest nodes (15, 16) and (16, 16) of the tilted
+    droplet differ in pressure by ~7e-4 of dp; the interpolated dp agrees to
+    1e-6 relative."""
     A = kappa = 0.04
-    def dp_at(cx):
-        o = orc.Oracle(0, orc.PERIODIC, 32, 32, 1, 1.0, 1.0, A, kappa, 1.0, 0.0, 1.0)
-        o.init_droplet(cx, 15.5, 0.0, 8.0)
-        o.step(200)
-        return o.observables()["dp"]
-    base, tiny = dp_at(15.5), dp_at(15.5 + 1e-6)
-    assert base > 0.0
-    assert abs(tiny - base) <= 1e-6 * abs(base), (base, tiny)
+    def run(cx):
+        o = orc.Oracle(0, orc.SHEAR, 32, 32, 1, 1.0, 1.0, A, kappa, 1.0, 0.02, 1.0)
+        o.init_droplet(cx, 15.5 + 1e-6, 0.0, 8.0)
+        o.step(500)
+        ob, f = o.observables(), o.fields()
+        p = f["rho"] / 3 + f["phi"] * f["mu"] - 0.25 * A * (f["phi"] ** 2 - 1) ** 2
+        return ob, p
+    (lo, p_lo), (hi, _) = run(15.5 - 1e-6), run(15.5 + 1e-6)
+    assert lo["centroid"][0] < 15.5 < hi["centroid"][0]
+    # the two nearest-node readings would differ markedly
+    assert abs(p_lo[0, 16, 15] - p_lo[0, 16, 16]) > 1e-4 * lo["dp"]
+    assert lo["dp"] > 0.0
+    assert abs(hi["dp"] - lo["dp"]) <= 1e-6 * lo["dp"], (lo["dp"], hi["dp"])
 
 
 def test_laplace_law(orc):
