@@ -65,3 +65,28 @@ def test_device_bytes_and_validation(fre):
             fre.fre_create(p, stream=0)
         assert e.value.status == fre.binding.FRE_ERR_ARG
         assert "fre_create" in fre.fre_last_error()
+
+
+def header_constants():
+    """Enumerators (NAME = value) and integer #defines of include/fre.h."""
+    txt = open(os.path.join(ROOT, "include", "fre.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for name, val in re.findall(r"\b(FRE_[A-Z0-9_]+)\s*=\s*(\d+)", txt):
+        out[name] = int(val)
+    for name, val in re.findall(r"#define\s+(FRE_[A-Z0-9_]+)\s+(\d+)u?\b", txt):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Every constant the binding shares with include/fre.h has the header's
+    value (status codes, lattices, storage formats, devices, flags)."""
+    from paper_2212_01617_gb300 import binding
+    hdr = header_constants()
+    shared = {n: v for n, v in hdr.items() if hasattr(binding, n)}
+    for need in ("FRE_OK", "FRE_ERR_BUDGET", "FRE_D3Q19", "FRE_BF16DEV", "FRE_PERIODIC",
+                 "FRE_FLAG_GENERIC_KERNELS", "FRE_FLAG_COUETTE_REFERENCE"):
+        assert need in shared, need
+    wrong = {n: (v, getattr(binding, n)) for n, v in shared.items() if getattr(binding, n) != v}
+    assert not wrong, wrong
