@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -70,13 +71,21 @@ def measured_peak_gbs():
 STEP_SOURCES = ("lattice.cuh", "fre_internal.h", "fre_kernels.cuh", "fre_rows.cuh", "fre_pipe.cuh", "fre_ws.cuh")
 
 
+def strip_comments(src: str) -> str:
+    """C/C++ source without comments and trailing blanks (string literals in
+    these kernel sources hold no comment markers)."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_hash() -> str:
-    """Hash of the time-step kernel sources (the ncu traffic figure is valid
-    for them only)."""
+    """Hash of the code of the time-step kernel sources, comments left out
+    (the ncu traffic figure is valid for that code only)."""
     h = hashlib.sha256()
     for name in STEP_SOURCES:
-        with open(os.path.join(CSRC, name), "rb") as fh:
-            h.update(name.encode() + fh.read())
+        with open(os.path.join(CSRC, name), encoding="utf-8") as fh:
+            h.update(name.encode() + strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

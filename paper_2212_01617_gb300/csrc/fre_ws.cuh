@@ -653,8 +653,8 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
     const int nx = NXC ? NXC : L.G.nx;
     const int ny = L.G.ny, nz = L.G.nz;
     const int nyu = ny / R;  // units per z plane
-    // the update takes the R rows of a unit side by side, one group of nx/2
-    // consumer threads per row; thread t of a group updates x = 2t, 2t + 1
+    // RPX rows of a unit side by side, one group of nx/2 consumer threads
+    // per row (RowsPar); thread t of a group updates x = 2t, 2t + 1
     constexpr int RP = RPX;
     static_assert(R % RP == 0, "rows side by side must divide the rows of a unit");
     const int ncons = RP * (nx / 2);
