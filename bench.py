@@ -41,21 +41,25 @@ DROPLET = (255.5, 127.5, 127.5, 48.0)
 ALG_BYTES = {"fp32": 2 * 2 * 19 * 4, "fp16dev": 2 * (19 * 2 + 18 * 2 + 4),
              "bf16dev": 2 * (19 * 2 + 18 * 2 + 4), "fp64": 2 * 2 * 19 * 8}
 CSRC = os.path.join(ROOT, "paper_2212_01617_gb300", "csrc")
-# a precision name may carry "+couette": the 16-bit f stored against the
-# Couette equilibrium of the shear walls (FRE_FLAG_COUETTE_REFERENCE)
-# instead of the rest equilibrium w_i rho0
-FLAG_COUETTE_REFERENCE = 4
+# a precision name may carry "+rest": the 16-bit f stored against the rest
+# equilibrium w_i rho0 (FRE_FLAG_REST_REFERENCE) instead of the Couette
+# equilibrium of the shear walls (the default of the shear device)
+FLAG_REST_REFERENCE = 8
 
 
 def split_prec(name: str):
     base, _, opt = name.partition("+")
-    if opt not in ("", "couette"):
+    if opt not in ("", "rest"):
         raise SystemExit(f"unknown precision variant {name!r}")
-    return base, (FLAG_COUETTE_REFERENCE if opt == "couette" else 0)
+    return base, (FLAG_REST_REFERENCE if opt == "rest" else 0)
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+# nominal HBM3e bandwidth of a GB300 (the ~8 TB/s the hardware is quoted at)
+NOMINAL_HBM_GBS = 7900.0
 
 
 def measured_peak_gbs():
@@ -274,26 +278,42 @@ def time_e2e(fre, precision, steps, obs_every=100):
                 obs_every=obs_every, seconds=t1 - t0)
 
 
-def cpu_baseline(seconds=15.0):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+def _oracle_rate(threads, seconds):
+    """Node updates per second of the FP64 oracle on the 1/8-scale twin with
+    `threads` OpenMP threads, over about `seconds` of stepping."""
     import oracle
-    oracle.build()
     nx, ny, nz = 64, 32, 32
     scale = nx / WORKLOAD["nx"]
     w = WORKLOAD
+    oracle.set_num_threads(threads)
     o = oracle.Oracle(oracle.D3Q19, oracle.SHEAR, nx, ny, nz, w["tau_f"], w["tau_g"], w["A"], w["kappa"],
                       w["gamma_mob"], w["u_wall"], w["rho0"])
     o.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, DROPLET[3] * scale)
     o.step(2)
     steps, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
-        o.step(10)
-        steps += 10
+        o.step(2)
+        steps += 2
     dt = time.perf_counter() - t0
-    return {"value": nx * ny * nz * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"D3Q19 shear {nx}x{ny}x{nz} (1/8-scale twin, droplet R={DROPLET[3] * scale:g}), "
-                      f"FP64, {steps} steps in {dt:.1f} s"}
+    used = oracle.num_threads()
+    return nx * ny * nz * steps / dt / 1e6, used, steps, dt
+
+
+def cpu_baseline(seconds=15.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the
+    workload: all host cores (the reported value) and one core."""
+    import oracle
+    oracle.build()
+    ncores = os.cpu_count() or 1
+    v_all, used, steps, dt = _oracle_rate(ncores, 0.6 * seconds)
+    v_one, _, steps1, dt1 = _oracle_rate(1, 0.4 * seconds)
+    oracle.set_num_threads(ncores)
+    return {"value": v_all, "unit": "MLUPS", "cores": used, "kind": "oracle",
+            "sample": f"D3Q19 shear 64x32x32 (1/8-scale twin, droplet R={DROPLET[3] * 64 / WORKLOAD['nx']:g}), "
+                      f"FP64, {steps} steps in {dt:.1f} s on {used} threads",
+            "one_core": {"value": v_one, "unit": "MLUPS", "cores": 1,
+                         "sample": f"same twin, {steps1} steps in {dt1:.1f} s on 1 thread"},
+            "parallel_speedup": v_all / v_one if v_one > 0 else None}
 
 
 def base_config(precision):
@@ -377,8 +397,14 @@ def batch_case_params(c):
 def run_batch_workload(args):
     """64 uneven D2Q9 cases (half shear, half four-roller), FP32: one batch
     (autotuned batched, per-slot or concurrent per-slot launches, CUDA-graph
-    replays) against one
-    context per case stepped on its own (one launch per kernel per case)."""
+    replays) against one context per case stepped on its own (one launch per
+    kernel per case)."""
+    line = batch_summary(args.steps, max(args.warmup, 40))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def batch_summary(steps, warmup):
     import torch
     import paper_2212_01617_gb300 as fre
     from paper_2212_01617_gb300 import inputs
@@ -388,23 +414,23 @@ def run_batch_workload(args):
     # bracket all the work and the per-case launches run one after another
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        return _batch_workload(args, fre, cases, nodes, stream)
+        return _batch_workload(steps, warmup, fre, cases, nodes, stream)
 
 
-def _batch_workload(args, fre, cases, nodes, stream):
+def _batch_workload(steps, warmup, fre, cases, nodes, stream):
     import torch
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     b = fre.Batch("d2q9", "fp32")
     for p, d in cases:
         b.add(*d, **p)
-    b.step(max(args.warmup, 40))  # includes the autotuner's timed candidates
+    b.step(warmup)  # includes the autotuner's timed candidates
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()
     e0, e1 = ev(), ev()
     e0.record(stream)
-    b.step(args.steps)
+    b.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -418,40 +444,39 @@ def _batch_workload(args, fre, cases, nodes, stream):
         sim.init_droplet(*d)
         sims.append(sim)
     for sim in sims:
-        sim.step(max(args.warmup, 3))
+        sim.step(3)
     torch.cuda.synchronize()
     e0, e1 = ev(), ev()
     e0.record(stream)
     for sim in sims:
-        sim.step(args.steps)
+        sim.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
     for sim in sims:
         sim.close()
     mode = {0: "batched", 1: "per-slot", 2: "per-slot concurrent"}[tuning["mode"]]
-    line = {"metric": "batched D2Q9 FRE-LBM MLUPS, 64 uneven cases", "value": nodes * args.steps / ms_batch / 1e3,
-            "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 40),
-            "ms_per_step": ms_batch / args.steps, "higher_is_better": True, "scaling": "weak",
+    peak = measured_peak_gbs()[0]
+    achieved = 144.0 * nodes / (ms_batch / steps * 1e-3) / 1e9
+    return {"metric": "batched D2Q9 FRE-LBM MLUPS, 64 uneven cases", "value": nodes * steps / ms_batch / 1e3,
+            "unit": "MLUPS", "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms_batch / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "64 D2Q9 cases, Nx uniform in 64..512 (even), shear Ny=Nx/2, four-roller "
                                    "Ny=Nx, Ca U(0.05,0.5), R/H U(0.1,0.3), FP32", "nodes": nodes,
                        "l2": "state of all cases (~0.4 GB) larger than L2; no flush"},
-            "sequential": {"value": nodes * args.steps / ms_seq / 1e3, "unit": "MLUPS",
-                           "ms_per_step": ms_seq / args.steps,
+            "sequential": {"value": nodes * steps / ms_seq / 1e3, "unit": "MLUPS",
+                           "ms_per_step": ms_seq / steps,
                            "what": "one context per case, each stepped on its own kernels"},
             "speedup_vs_sequential": ms_seq / ms_batch,
-            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": measured_peak_gbs()[0],
-                         "achieved": 144.0 * nodes / (ms_batch / args.steps * 1e-3) / 1e9,
-                         "frac": 144.0 * nodes / (ms_batch / args.steps * 1e-3) / 1e9 / measured_peak_gbs()[0],
+            "roofline": {"bound": "hbm", "unit": "GB/s", "peak": peak, "achieved": achieved,
+                         "frac": achieved / peak, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "what": "whole batch step, algorithmic 144 B per D2Q9 FP32 node update"},
             "tuning": {"mode": mode, "bx": tuning["bx"],
                        "ms_per_step_candidates": dict(zip(["batched bx32", "batched bx64", "batched bx128",
                                                            "per-slot", "per-slot concurrent"],
                                                           tuning["ms_per_step"]))},
             "clocks": clk}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
 # D3Q19 serving requests: A = kappa = 0.01 (xi = 1), tau_f = 1.5 (dynamic
@@ -499,25 +524,35 @@ def drive_server(srv, trace, cases):
     return results, end - start
 
 
-def run_serve_workload(args):
-    """Poisson-arriving D3Q19 droplet-deformation requests: the serving loop
-    (FP16 deviation store, continuous batching under a 150 GB budget)
-    against the same requests served one at a time in plain FP32."""
+SERVE_ARMS = {
+    # the configured serving loop: FP16-dev storage, continuous batching
+    "batched_fp16dev": dict(precision="fp16dev", chunk_steps=250),
+    # the same requests one at a time in plain FP32 (the configured baseline)
+    "sequential_fp32": dict(precision="fp32", max_running=1, chunk_steps=1000),
+    # one at a time in the same FP16-dev storage: separates the gain of
+    # batching from the gain of the storage format
+    "sequential_fp16dev": dict(precision="fp16dev", max_running=1, chunk_steps=1000),
+}
+
+
+def serve_summary(n_requests, max_steps, target_nodes, arms=tuple(SERVE_ARMS)):
+    """Poisson-arriving D3Q19 droplet-deformation requests through the
+    serving loop, one run per arm of SERVE_ARMS on the same trace."""
     import torch
     import paper_2212_01617_gb300 as fre
     from paper_2212_01617_gb300 import inputs
-    trace = inputs.serving_trace(args.serve_requests)
+    trace = inputs.serving_trace(n_requests)
     cases = [serve_case_params(c) for c in trace]
     stream = torch.cuda.Stream()
     out = {}
     with torch.cuda.stream(stream):
-        arms = [("batched_fp16dev", dict(precision="fp16dev", target_nodes=args.serve_target_nodes,
-                                         chunk_steps=250)),
-                ("sequential_fp32", dict(precision="fp32", max_running=1, chunk_steps=1000))]
-        for name, kw in arms:
+        for name in arms:
+            kw = dict(SERVE_ARMS[name])
             prec = kw["precision"]
+            if "max_running" not in kw:
+                kw["target_nodes"] = target_nodes
             srv = fre.Server("d3q19", budget_bytes=150 << 30, check_every=1000, tol_D=1e-4,
-                             max_steps=args.serve_max_steps, stream=stream.cuda_stream, **kw)
+                             max_steps=max_steps, stream=stream.cuda_stream, **kw)
             cs = [(dict(p, precision=prec), d) for p, d in cases]
             res, wall = drive_server(srv, trace, cs)
             st = srv.stats()
@@ -535,21 +570,35 @@ def run_serve_workload(args):
                          "batch_mode_at_end": {0: "batched", 1: "per-slot", 2: "per-slot concurrent"}.get(
                              st["batch_mode"]),
                          "autotunes": st["tunes"], "graph_captures": st["captures"]}
-            log(f"{name}: {json.dumps(out[name])}")
-    b, s_ = out["batched_fp16dev"], out["sequential_fp32"]
+            log(f"serve {name}: {json.dumps(out[name])}")
+    summary = {"requests": len(trace), "max_steps": max_steps, "target_nodes": target_nodes, "arms": out}
+    b = out.get("batched_fp16dev")
+    for base in ("sequential_fp32", "sequential_fp16dev"):
+        s_ = out.get(base)
+        if b and s_:
+            summary[f"vs_{base}"] = {"throughput_ratio": b["aggregate_mlups"] / s_["aggregate_mlups"],
+                                     "speedup_p50": s_["p50_s"] / b["p50_s"],
+                                     "speedup_p99": s_["p99_s"] / b["p99_s"]}
+    return summary
+
+
+def run_serve_workload(args):
+    """Poisson-arriving D3Q19 droplet-deformation requests: the serving loop
+    (FP16 deviation store, continuous batching under a 150 GB budget)
+    against the same requests served one at a time in plain FP32 and in
+    FP16-dev storage."""
+    sm = serve_summary(args.serve_requests, args.serve_max_steps, args.serve_target_nodes)
+    b, s_ = sm["arms"]["batched_fp16dev"], sm["arms"]["sequential_fp32"]
     line = {"metric": "serving D3Q19 FRE-LBM: aggregate MLUPS and p50/p99 time-to-result",
             "value": b["aggregate_mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16-store/f32",
             "data": "synthetic",
-            "config": {"workload": f"{len(trace)} Poisson requests (20/s), D3Q19 sizes 64^3, 96^3, 128x64x64, "
-                                   "192x96x96, shear or four-roller, Ca U(0.05,0.45), R/H U(0.1,0.3), run until "
-                                   "|dD| < 1e-4 per 1000 steps or breakup, 150 GB budget",
+            "config": {"workload": f"{sm['requests']} Poisson requests (20/s), D3Q19 sizes 64^3, 96^3, "
+                                   "128x64x64, 192x96x96, shear or four-roller, Ca U(0.05,0.45), R/H U(0.1,0.3), "
+                                   "run until |dD| < 1e-4 per 1000 steps or breakup, 150 GB budget",
                        "max_steps": args.serve_max_steps, "target_nodes": args.serve_target_nodes},
-            "p50_s": b["p50_s"], "p99_s": b["p99_s"],
-            "sequential_fp32": s_,
-            "batched_fp16dev": b,
-            "speedup_p50": s_["p50_s"] / b["p50_s"], "speedup_p99": s_["p99_s"] / b["p99_s"],
-            "throughput_ratio": b["aggregate_mlups"] / s_["aggregate_mlups"]}
+            "p50_s": b["p50_s"], "p99_s": b["p99_s"], **{k: v for k, v in sm.items() if k != "arms"},
+            **sm["arms"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -560,7 +609,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precisions", default="fp32,fp16dev,bf16dev,fp16dev+couette,bf16dev+couette")
+    ap.add_argument("--precisions", default="fp32,fp16dev,bf16dev,fp16dev+rest,bf16dev+rest")
     ap.add_argument("--e2e-steps", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -570,6 +619,11 @@ def main():
     ap.add_argument("--workload", choices=["lattice", "batch", "serve"], default="lattice",
                     help="lattice: the 512x256x256 D3Q19 lattice (default); batch: 64 uneven D2Q9 cases; "
                          "serve: Poisson-arriving D3Q19 requests through the serving loop")
+    ap.add_argument("--no-batch-serve", action="store_true",
+                    help="leave the batch and serving summaries out of the default line")
+    ap.add_argument("--summary-requests", type=int, default=12,
+                    help="requests of the serving summary in the default line")
+    ap.add_argument("--summary-max-steps", type=int, default=8000)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-target-nodes", type=int, default=8_000_000)
     ap.add_argument("--serve-max-steps", type=int, default=30000)
@@ -621,6 +675,14 @@ def main():
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
 
+    # batch and serving summaries (one GPU, rank 0 of a single-rank run)
+    batch, serve = None, None
+    if rank == 0 and ws == 1 and not args.no_batch_serve:
+        bl = batch_summary(200, 40)
+        batch = {k: bl[k] for k in ("value", "unit", "ms_per_step", "sequential", "speedup_vs_sequential",
+                                    "roofline", "tuning", "config")}
+        serve = serve_summary(args.summary_requests, args.summary_max_steps, args.serve_target_nodes)
+
     if rank == 0:
         variants = {}
         for prec, rr in runs.items():
@@ -633,6 +695,7 @@ def main():
                 "mu_ms": rr["ms_mu"] / args.steps,
                 "update_alg_gbs": ab * rr["n"] / t / 1e9,
                 "update_frac_of_measured_hbm": ab * rr["n"] / t / 1e9 / peak,
+                "update_frac_of_nominal_hbm": ab * rr["n"] / t / 1e9 / NOMINAL_HBM_GBS,
                 "step_alg_frac_of_measured_hbm": ab * rr["n"] / (rr["ms"] / args.steps * 1e-3)
                 / 1e9 / peak,
                 "D_after_run": rr["obs"]["D"], "mass": rr["obs"]["mass"], "kernel_path": rr["path"],
@@ -647,18 +710,24 @@ def main():
             "data": "synthetic", "config": base_config(main_prec),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "kernel": (f"k_wsrow<19,{main_prec},update,pull> (fused pull + collide of f and g; "
                                     "warp-specialised, bulk-copy staged x-rows)" if r["path"] == 2 else
                                     f"update kernel, path {r['path']}"),
                          "algorithmic_bytes_per_launch": ALG_BYTES[split_prec(main_prec)[0]] * n,
                          "peak_source": peak_src,
-                         "step_achieved": step_achieved, "step_frac": step_achieved / peak},
+                         "step_achieved": step_achieved, "step_frac": step_achieved / peak,
+                         "step_frac_of_nominal": step_achieved / NOMINAL_HBM_GBS},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": r["launches"],
             "clocks": r["clocks"],
             "variants": variants,
         }
+        if batch is not None:
+            line["batch"] = batch
+        if serve is not None:
+            line["serve"] = serve
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -60,8 +60,9 @@ typedef enum { FRE_D2Q9 = 0, FRE_D3Q19 = 1 } fre_lattice;
 
 /* Storage of the populations on the device.  FP64 and FP32 store f_i and
  * g_i as is and compute in the same precision.  FP16DEV and BF16DEV store
- * f_i - w_i rho0 (the deviation from the rest equilibrium; see
- * FRE_FLAG_COUETTE_REFERENCE) and g_i (i != 0) in 16 bits (round to nearest
+ * f_i - fr_i, the deviation from a reference equilibrium (the Couette
+ * equilibrium of the shear device, w_i rho0 elsewhere; see
+ * FRE_FLAG_REST_REFERENCE), and g_i (i != 0) in 16 bits (round to nearest
  * even), keep g_0 in FP32 and compute in FP32. */
 typedef enum { FRE_FP64 = 0, FRE_FP32 = 1, FRE_FP16DEV = 2, FRE_BF16DEV = 3 } fre_precision;
 
@@ -99,14 +100,30 @@ typedef struct {
 /* Run the update on x-chunk work units instead of whole x-rows (both stage
  * their rows in shared memory with bulk copies; for validation/tuning). */
 #define FRE_FLAG_CHUNKED_UPDATE 2u
-/* 16-bit formats on the shear device: store f_i as the deviation from the
- * equilibrium (Eq. feq) of rho0 and the plane Couette velocity between the
- * walls, (U(y), 0, 0) with U(y) = u_wall (2 (y + 1/2) / ny - 1), instead of
- * from the rest equilibrium w_i rho0.  The 16-bit values then carry the
- * departure from the base shear flow only (on the 64^3 shear twin of the
- * benchmark lattice the FP16 error in D drops from 3.4e-3 to 3e-5 at the
- * same speed).  Ignored by FP64, FP32 and the other devices. */
+/* Reference state of the 16-bit f stores on the shear device.  By default
+ * f_i is stored as the deviation from the equilibrium (Eq. feq) of rho0 and
+ * the plane Couette velocity between the walls, (U(y), 0, 0) with U(y) =
+ * u_wall (2 (y + 1/2) / ny - 1): the base flow the moving walls drive, the
+ * state of the device before a droplet deforms it.  The 16-bit values then
+ * carry the departure from that base flow only.  FRE_FLAG_REST_REFERENCE
+ * stores f_i - w_i rho0 instead, the deviation from the equilibrium at rest;
+ * every moving f_i then also carries the base flow 3 w_i rho0 c_ix U(y), on
+ * which FP16 spends its mantissa (on the 64^3 shear twin of the benchmark
+ * lattice the FP16 error in D is 3.2e-3 with the rest reference and 4.1e-5
+ * with the Couette one, at the same speed).  FRE_FLAG_COUETTE_REFERENCE
+ * names the default; setting both is an argument error.  FP64, FP32 and
+ * the devices without moving walls ignore both (their reference is
+ * w_i rho0). */
 #define FRE_FLAG_COUETTE_REFERENCE 4u
+#define FRE_FLAG_REST_REFERENCE 8u
+/* Test of the failure path of the row kernels, not for production: their
+ * producer warps issue no copies and every pipeline wait gives up after
+ * 5 ms instead of 2 s.  Each step's kernels then end early with the
+ * context's error word set, and the next synchronising call (fre_observables,
+ * fre_copy_fields, fre_store_populations, fre_step_timed) returns
+ * FRE_ERR_CUDA; the GPU and other contexts are unaffected.  The populations
+ * of such a context are left undefined: initialise it again before use. */
+#define FRE_FLAG_TEST_PIPELINE_STALL 16u
 /* Bits 8..15: log2 of the x-chunk width of the row kernels (0 = automatic:
  * 128 when nx allows it, else the whole row).  A tuning knob; every valid
  * width computes the same update. */
@@ -217,9 +234,10 @@ int fre_kernel_path(const fre_ctx *c);
  *
  * Scratch: the per-block partial sums live in a static 57,600-byte device
  * array inside the library, which every GPU that loads the library keeps
- * until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress), so make the first call on
- * each device before any stream capture.  Every call writes all the
+ * until the process exits.  The first call in a CUDA context (per device,
+ * and again after a cudaDeviceReset) looks up that array's device address
+ * (cudaGetSymbolAddress) and keeps it for that context, so make the first
+ * call on each device before any stream capture.  Every call writes all the
  * partials it later reads, so nothing has to start at zero, but all calls
  * share the one array: calls whose work overlaps on the GPU (different
  * streams, or host threads, without ordering between them) race and give
@@ -281,6 +299,15 @@ size_t fre_batch_bytes_in_use(const fre_batch *b);
  * tuning is in force: none ran yet, or the slot count has since changed by
  * more than a factor 2 (smaller changes keep the tuned mode). */
 fre_status fre_batch_tuning(const fre_batch *b, int *mode, int *bx, double *ms_per_step);
+
+/* Pin the launch mode instead of tuning it: mode 0 (one launch per kernel
+ * for all slots, block width bx = 32, 64 or 128), 1 (each slot's own
+ * kernels, one slot after another) or 2 (each slot's own kernels on four
+ * concurrent graph branches); -1 returns to the autotuner.  Every mode
+ * computes the same update of every slot.  Waits for the queued steps;
+ * FRE_ERR_ARG for an unknown mode or width.  For tests and for callers that
+ * know their best mode. */
+fre_status fre_batch_set_mode(fre_batch *b, int mode, int bx);
 
 /* Wait for the batch's queued work. */
 fre_status fre_batch_synchronize(fre_batch *b);
@@ -374,6 +401,10 @@ fre_status fre_server_stats(const fre_server *s, fre_serve_stats *out);
 
 /* Seconds since fre_server_create (the clock of the result timestamps). */
 double fre_server_clock(const fre_server *s);
+
+/* The batch the server advances (owned by the server; do not destroy), e.g.
+ * to pin its launch mode with fre_batch_set_mode. */
+fre_batch *fre_server_batch(fre_server *s);
 
 /* Destroy the server, its batch and its pool; NULL-safe. */
 void fre_server_destroy(fre_server *s);

@@ -34,12 +34,14 @@ EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_field
            "fre_kernel_path", "fre_moments_noalloc",
            "fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
            "fre_batch_observables", "fre_batch_context", "fre_batch_slots", "fre_batch_bytes_in_use",
-           "fre_batch_tuning", "fre_batch_synchronize", "fre_batch_destroy",
+           "fre_batch_tuning", "fre_batch_set_mode", "fre_batch_synchronize", "fre_batch_destroy",
            "fre_server_create", "fre_server_submit", "fre_server_advance", "fre_server_results",
-           "fre_server_stats", "fre_server_clock", "fre_server_destroy",
+           "fre_server_stats", "fre_server_clock", "fre_server_batch", "fre_server_destroy",
            "fre_destroy", "fre_last_error"]
 FRE_FLAG_GENERIC_KERNELS = 1
 FRE_FLAG_COUETTE_REFERENCE = 4
+FRE_FLAG_REST_REFERENCE = 8
+FRE_FLAG_TEST_PIPELINE_STALL = 16
 
 
 class FreError(RuntimeError):
@@ -150,6 +152,7 @@ def load_library(path: str = LIB_PATH):
         L.fre_batch_bytes_in_use.restype = C.c_size_t
         L.fre_batch_bytes_in_use.argtypes = [vp]
         L.fre_batch_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.fre_batch_set_mode.argtypes = [vp, C.c_int, C.c_int]
         L.fre_batch_synchronize.argtypes = [vp]
         L.fre_batch_destroy.argtypes = [vp]
         L.fre_batch_destroy.restype = None
@@ -162,12 +165,14 @@ def load_library(path: str = LIB_PATH):
         L.fre_server_stats.argtypes = [vp, C.POINTER(fre_serve_stats)]
         L.fre_server_clock.restype = C.c_double
         L.fre_server_clock.argtypes = [vp]
+        L.fre_server_batch.restype = vp
+        L.fre_server_batch.argtypes = [vp]
         L.fre_server_destroy.restype = None
         L.fre_server_destroy.argtypes = [vp]
         for name in ("fre_server_create", "fre_server_submit", "fre_server_advance", "fre_server_stats"):
             getattr(L, name).restype = C.c_int
         for name in ("fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
-                     "fre_batch_observables", "fre_batch_tuning", "fre_batch_synchronize"):
+                     "fre_batch_observables", "fre_batch_tuning", "fre_batch_set_mode", "fre_batch_synchronize"):
             getattr(L, name).restype = C.c_int
         for name in ("fre_create", "fre_init_droplet", "fre_init_fields", "fre_load_populations",
                      "fre_store_populations", "fre_step", "fre_step_timed", "fre_copy_fields",
@@ -460,6 +465,11 @@ class Batch:
         s = load_library().fre_batch_tuning(self.h, C.byref(mode), C.byref(bx), _dptr(ms))
         return {"tuned": s == FRE_OK, "mode": mode.value, "bx": bx.value, "ms_per_step": ms.tolist()}
 
+    def set_mode(self, mode: int, bx: int = 64):
+        """Pin the launch mode (0 batched, 1 per-slot, 2 concurrent per-slot;
+        -1 back to the autotuner)."""
+        _check(load_library().fre_batch_set_mode(self.h, int(mode), int(bx)), "fre_batch_set_mode")
+
     def synchronize(self):
         _check(load_library().fre_batch_synchronize(self.h), "fre_batch_synchronize")
 
@@ -524,3 +534,8 @@ class Server:
 
     def clock(self) -> float:
         return float(load_library().fre_server_clock(self.h))
+
+    def set_batch_mode(self, mode: int, bx: int = 64):
+        """Pin the launch mode of the server's batch (fre_batch_set_mode)."""
+        b = load_library().fre_server_batch(self.h)
+        _check(load_library().fre_batch_set_mode(b, int(mode), int(bx)), "fre_batch_set_mode")

@@ -53,6 +53,8 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
     if (p->device < FRE_SHEAR || p->device > FRE_PERIODIC) return bad("unknown device");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bad("lattice sizes must be >= 1");
     if (p->lattice == FRE_D2Q9 && p->nz != 1) return bad("D2Q9 needs nz = 1");
+    if ((p->flags & FRE_FLAG_COUETTE_REFERENCE) && (p->flags & FRE_FLAG_REST_REFERENCE))
+        return bad("FRE_FLAG_COUETTE_REFERENCE and FRE_FLAG_REST_REFERENCE exclude each other");
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) return bad("tau_f and tau_g must be > 1/2");
     if (!(p->A >= 0.0) || !(p->kappa >= 0.0)) return bad("A and kappa must be >= 0");
     if (!std::isfinite(p->gamma_mob) || !std::isfinite(p->u_wall) || !(p->rho0 > 0.0))
@@ -162,8 +164,9 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.G = c->G;
     L.P = c->P;
     const double tf = c->P.tau_f, tg = c->P.tau_g;
-    // reference profile of the 16-bit f stores (FRE_FLAG_COUETTE_REFERENCE)
-    const bool shear = c->G.device == FRE_SHEAR && (c->p.flags & FRE_FLAG_COUETTE_REFERENCE) &&
+    // reference profile of the 16-bit f stores: the Couette profile of the
+    // shear device unless FRE_FLAG_REST_REFERENCE
+    const bool shear = c->G.device == FRE_SHEAR && !(c->p.flags & FRE_FLAG_REST_REFERENCE) &&
                        (c->p.precision == FRE_FP16DEV || c->p.precision == FRE_BF16DEV);
     L.F = {float(1.0 / tf), float(1.0 / tg), float(1.0 - 0.5 / tf), float(3.0 * c->P.Gamma),
            float(c->P.A), float(c->P.kappa), float(c->P.rho0), float(c->G.uwall),
@@ -182,6 +185,8 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.stream = c->stream;
     L.W = c->row_w;
     L.err = c->err_dev;
+    L.stall = (c->p.flags & FRE_FLAG_TEST_PIPELINE_STALL) ? 1 : 0;
+    L.wait_ns = L.stall ? 5000000ull : 2000000000ull;
     return L;
 }
 

@@ -39,6 +39,7 @@ struct fre_batch {
     int mode = 0;  // 0 batched, 1 per-slot, 2 per-slot on concurrent streams
     int bx = 64;
     bool tuned = false;
+    bool pinned = false;   // mode fixed by fre_batch_set_mode: no tuning
     int tuned_nslots = 0;  // slot count the tuning was measured on
     double tuned_ms[5] = {0, 0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128, per-slot, concurrent
     // streams and events of the concurrent mode (graph branches)
@@ -82,7 +83,7 @@ std::vector<int> active(const fre_batch *b) {
 void invalidate(fre_batch *b) {
     b->tables_valid = false;
     drop_graph(b);
-    if (b->tuned) {
+    if (b->tuned && !b->pinned) {
         const int n = (int)active(b).size();
         if (2 * n < b->tuned_nslots || n > 2 * b->tuned_nslots) b->tuned = false;
     }
@@ -317,9 +318,17 @@ fre_status autotune(fre_batch *b, long long *taken) {
     const int bxs[5] = {32, 64, 128, 64, 64};
     double best = 1e300;
     int best_k = 1;
-    cudaEvent_t e0, e1;
-    BCUDA(cudaEventCreate(&e0));
-    BCUDA(cudaEventCreate(&e1));
+    // the two timing events, destroyed on every way out of the loop
+    struct Events {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() {
+            for (auto ev : e)
+                if (ev) cudaEventDestroy(ev);
+        }
+    } ev;
+    BCUDA(cudaEventCreate(&ev.e[0]));
+    BCUDA(cudaEventCreate(&ev.e[1]));
+    const cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     for (int k = 0; k < 5; ++k) {
         b->mode = modes[k];
         b->bx = bxs[k];
@@ -344,8 +353,6 @@ fre_status autotune(fre_batch *b, long long *taken) {
             best_k = k;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->mode = modes[best_k];
     b->bx = bxs[best_k];
     b->tuned = true;
@@ -549,6 +556,30 @@ fre_status fre_batch_tuning(const fre_batch *b, int *mode, int *bx, double *ms_p
     if (ms_per_step)
         for (int k = 0; k < 5; ++k) ms_per_step[k] = b->tuned_ms[k];
     return b->tuned ? FRE_OK : FRE_ERR_STATE;
+}
+
+fre_status fre_batch_set_mode(fre_batch *b, int mode, int bx) {
+    fre_status s = benter(b);
+    if (s != FRE_OK) return s;
+    if (mode < -1 || mode > 2) return bfail(FRE_ERR_ARG, "fre_batch_set_mode: mode must be -1, 0, 1 or 2%s");
+    if (mode == 0 && bx != 32 && bx != 64 && bx != 128)
+        return bfail(FRE_ERR_ARG, "fre_batch_set_mode: bx must be 32, 64 or 128%s");
+    // queued steps of the old mode finish first; the next step captures anew
+    BCUDA(cudaStreamSynchronize(b->stream));
+    drop_graph(b);
+    b->tables_valid = false;
+    if (mode < 0) {
+        b->pinned = false;
+        b->tuned = false;
+        return FRE_OK;
+    }
+    b->pinned = true;
+    b->tuned = true;
+    b->mode = mode;
+    b->bx = mode == 0 ? bx : 64;
+    b->tuned_nslots = (int)active(b).size();
+    for (double &m : b->tuned_ms) m = 0.0;
+    return FRE_OK;
 }
 
 fre_status fre_batch_synchronize(fre_batch *b) {

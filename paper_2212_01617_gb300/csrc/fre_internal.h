@@ -30,8 +30,8 @@ struct Phys {
 // rounded once on the host: the GPU's FP64 pipe is narrow, so the kernels
 // do no double arithmetic per work unit or node.  u0, du: the reference
 // profile U(y) = u0 + y du of the 16-bit f stores (fref in fre_kernels.cuh):
-// the plane Couette profile of the shear device under
-// FRE_FLAG_COUETTE_REFERENCE, else 0 (the rest equilibrium).
+// the plane Couette profile of the shear device unless
+// FRE_FLAG_REST_REFERENCE, else 0 (the rest equilibrium).
 struct PhysF {
     float omega_f, omega_g, kf, gamma3, A, kappa, rho0, uwall, u0, du;
 };
@@ -39,7 +39,7 @@ struct PhysF {
 // One population buffer (A or B).  FP64/FP32: f, g are [q][np] arrays of
 // the storage type.  16-bit formats: f is [q][np] of deviations
 // f_i - fr_i(y) from the reference of the node's row (fref in
-// fre_kernels.cuh; w_i rho0 unless FRE_FLAG_COUETTE_REFERENCE); g holds
+// fre_kernels.cuh; the Couette equilibrium of the shear device, else w_i rho0); g holds
 // g_1..g_{q-1} as [q-1][np]; g0 is FP32 [np].
 struct Buf {
     void *f;
@@ -64,6 +64,8 @@ struct Launch {
     int W;                 // chunk width of the row kernels
     int pull;              // batched kernels: stream from the post-collision buffer
     int *err;              // device error word (pipeline wait timed out)
+    unsigned long long wait_ns;  // limit of every pipeline wait
+    int stall;             // FRE_FLAG_TEST_PIPELINE_STALL: producers issue no copies
     double *staging;       // FP64 staging of host I/O (n doubles per field)
     cudaStream_t stream;
 };

@@ -65,12 +65,13 @@ __device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v) {
 
 // Reference state of the 16-bit f formats.  f is stored as the deviation
 // f_i - fr_i(y) from the second-order equilibrium (Eq. feq) of density rho0
-// and velocity (U(y), 0, 0).  By default U = 0: the rest equilibrium
-// w_i rho0.  Under FRE_FLAG_COUETTE_REFERENCE the shear device takes the
-// plane Couette profile between its walls, U(y) = u_w (2 (y + 1/2) / ny -
-// 1), so the stored values carry the departure from the base flow only
-// instead of spending the 16-bit mantissa on the 3 w_i rho0 c_ix U part of
-// every moving population.  U(y) = u0 + y du with u0, du rounded on the host.
+// and velocity (U(y), 0, 0).  The shear device takes the plane Couette
+// profile between its walls, U(y) = u_w (2 (y + 1/2) / ny - 1), so the
+// stored values carry the departure from the base flow only instead of
+// spending the 16-bit mantissa on the 3 w_i rho0 c_ix U part of every
+// moving population; under FRE_FLAG_REST_REFERENCE, and on the other
+// devices, U = 0: the rest equilibrium w_i rho0.  U(y) = u0 + y du with u0,
+// du rounded on the host.
 __device__ __forceinline__ float couette_u(const Launch &L, int y) { return fmaf(float(y), L.F.du, L.F.u0); }
 template <int Q, typename T>
 __device__ __forceinline__ T fref(int i, T rho0, T U) {

@@ -2,6 +2,7 @@
 // observables, computed from caller-owned device populations without any
 // device allocation.  The per-block partial sums live in a file-scope
 // __device__ array instead of context memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -22,10 +23,49 @@ constexpr long long kMaxNodes = 1LL << 30;
 // Shared by every call on a device; holds the last call's partials.
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
-// Device address of g_scratch, looked up once per device.
-constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {};
+// Device address of g_scratch, looked up once per CUDA context.  The
+// address belongs to the module loaded into a context: after a
+// cudaDeviceReset, or with another context current, the module may sit
+// elsewhere, so the cache is keyed on the context's unique id (never reused
+// within a process), not on the device index.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    double *ptr;
+};
+constexpr int kMaxContexts = 64;
+ScratchAddr g_scratch_addr[kMaxContexts] = {};
+int g_scratch_n = 0, g_scratch_next = 0;
 std::mutex g_setup_mutex;
+
+// Driver entry points for the id of the current context, resolved through
+// the runtime (no link-time dependency on the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Id of the context current on this thread; false if there is none yet.
+// Called with g_setup_mutex held.
+bool current_context_id(unsigned long long *id) {
+    static bool resolved = false;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!resolved) {
+        resolved = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -163,18 +203,18 @@ fre_status fre_moments_noalloc(int lattice, int nx, int ny, int nz, const double
         return na_fail(FRE_ERR_ARG, "fre_moments_noalloc: more than 2^30 nodes (the largest lattice it accepts)");
     if (!f_dev || !g_dev || !out_dev) return na_fail(FRE_ERR_ARG, "fre_moments_noalloc: NULL pointer");
 
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return na_fail(FRE_ERR_CUDA, "fre_moments_noalloc: no usable current CUDA device");
-    }
-    double *scratch;
+    double *scratch = nullptr;
     {
-        // first call on this device: look up the device address of the
-        // file-scope scratch array (the host-side symbol is not an address
-        // a kernel may use)
+        // first call in a context: look up the device address of the
+        // file-scope scratch array (the host-side symbol is not an address a
+        // kernel may use); cudaGetSymbolAddress also makes the device's
+        // primary context current if no context is current yet
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
+        unsigned long long id = 0;
+        bool have_id = current_context_id(&id);
+        for (int k = 0; have_id && k < g_scratch_n; ++k)
+            if (g_scratch_addr[k].ctx_id == id) scratch = g_scratch_addr[k].ptr;
+        if (!scratch) {
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess || !p) {
@@ -184,9 +224,14 @@ fre_status fre_moments_noalloc(int lattice, int nx, int ny, int nz, const double
                          cudaGetErrorString(e));
                 return na_fail(FRE_ERR_CUDA, msg);
             }
-            g_scratch_ptr[dev] = static_cast<double *>(p);
+            scratch = static_cast<double *>(p);
+            if (!have_id) have_id = current_context_id(&id);
+            if (have_id) {
+                g_scratch_addr[g_scratch_next] = {id, scratch};
+                g_scratch_next = (g_scratch_next + 1) % kMaxContexts;
+                if (g_scratch_n < kMaxContexts) ++g_scratch_n;
+            }
         }
-        scratch = g_scratch_ptr[dev];
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     long long nb = (n + kThreads - 1) / kThreads;

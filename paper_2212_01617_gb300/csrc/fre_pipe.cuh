@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <mutex>
 
 #include "fre_rows.cuh"
 
@@ -50,58 +51,84 @@ __device__ __forceinline__ Unit unit_at(const Geo &G, int W, int b) {
 }
 
 // Launch shape of the persistent kernels: SM count, resident blocks and the
-// dynamic shared-memory opt-in.
+// dynamic shared-memory opt-in.  The tables are process-wide and shared by
+// every context, so one mutex guards them (contexts may be created and
+// stepped from several host threads at once); entries are per device.
 struct LaunchShape {
+    static std::mutex &lock() {
+        static std::mutex m;
+        return m;
+    }
+    static int device() {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            dev = 0;
+        }
+        return dev;
+    }
     // raise a kernel's dynamic shared-memory opt-in to at least `smem`; one
-    // record per kernel, so that no caller lowers what another one raised
-    // (a launch above the opt-in fails with an invalid-argument error)
+    // record per kernel and device, so that no caller lowers what another
+    // one raised (a launch above the opt-in fails with an invalid-argument
+    // error)
     static void opt_in(const void *fn, size_t smem) {
-        static const void *fns[128] = {};
-        static size_t vals[128] = {};
+        struct Rec {
+            const void *fn;
+            int dev;
+            size_t smem;
+        };
+        static Rec recs[256] = {};
         static int n = 0;
+        const int dev = device();
+        std::lock_guard<std::mutex> g(lock());
         for (int k = 0; k < n; ++k) {
-            if (fns[k] != fn) continue;
-            if (smem > vals[k]) {
-                vals[k] = smem;
+            if (recs[k].fn != fn || recs[k].dev != dev) continue;
+            if (smem > recs[k].smem) {
+                recs[k].smem = smem;
                 cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             }
             return;
         }
-        if (n < 128) {
-            fns[n] = fn;
-            vals[n] = smem;
-            ++n;
-        }
+        if (n < 256) recs[n++] = {fn, dev, smem};
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    // resident blocks per SM of a kernel (cached per kernel and block size)
+    // resident blocks per SM of a kernel (cached per kernel, device, block
+    // size and shared memory)
     static int blocks_per_sm(const void *fn, int threads, size_t smem) {
-        static const void *last_fn[16] = {};
-        static int last_t[16] = {}, last_nb[16] = {};
-        for (int k = 0; k < 16; ++k)
-            if (last_fn[k] == fn && last_t[k] == threads) return last_nb[k];
+        struct Rec {
+            const void *fn;
+            int dev, threads;
+            size_t smem;
+            int nb;
+        };
+        static Rec recs[32] = {};
+        static int slot = 0;
+        const int dev = device();
+        std::lock_guard<std::mutex> g(lock());
+        for (int k = 0; k < 32; ++k)
+            if (recs[k].fn == fn && recs[k].dev == dev && recs[k].threads == threads && recs[k].smem == smem)
+                return recs[k].nb;
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) {
             cudaGetLastError();
             nb = 1;
         }
         if (nb < 1) nb = 1;
-        static int slot = 0;
-        last_fn[slot] = fn;
-        last_t[slot] = threads;
-        last_nb[slot] = nb;
-        slot = (slot + 1) & 15;
+        recs[slot] = {fn, dev, threads, smem, nb};
+        slot = (slot + 1) & 31;
         return nb;
     }
     static int sms() {
-        static int n = 0;
-        if (!n) {
-            int dev = 0;
-            cudaGetDevice(&dev);
+        static int counts[64] = {};
+        const int dev = device();
+        std::lock_guard<std::mutex> g(lock());
+        if (dev < 0 || dev >= 64) return 152;
+        if (!counts[dev]) {
+            int n = 0;
             cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-            if (n <= 0) n = 1;
+            counts[dev] = n > 0 ? n : 1;
         }
-        return n;
+        return counts[dev];
     }
 };
 

@@ -288,6 +288,8 @@ fre_status fre_server_stats(const fre_server *s, fre_serve_stats *out) {
 
 double fre_server_clock(const fre_server *s) { return s ? s->now() : 0.0; }
 
+fre_batch *fre_server_batch(fre_server *s) { return s ? s->batch : nullptr; }
+
 void fre_server_destroy(fre_server *s) {
     if (!s) return;
     cudaSetDevice(s->device_id);

@@ -32,8 +32,9 @@ __device__ __forceinline__ void mbar_arrive(unsigned bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 // Bounded wait with a suspend hint (the warp sleeps in hardware instead of
-// spinning); false after ~2 s.
-__device__ __forceinline__ bool mbar_wait_hint(unsigned bar, unsigned parity) {
+// spinning); false once limit_ns have passed (2 s; a few ms under
+// FRE_FLAG_TEST_PIPELINE_STALL).
+__device__ __forceinline__ bool mbar_wait_hint(unsigned bar, unsigned parity, unsigned long long limit_ns) {
     const unsigned long long t0 = global_ns();
     while (true) {
         unsigned done;
@@ -43,7 +44,7 @@ __device__ __forceinline__ bool mbar_wait_hint(unsigned bar, unsigned parity) {
             : "r"(bar), "r"(parity), "r"(1000000u)
             : "memory");
         if (done) return true;
-        if (global_ns() - t0 > 2000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 // named barrier among the consumer threads only (id 1)
@@ -139,13 +140,16 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
 
     if (producer) {
         // ------------------------------------------------------ producer warp
+        // test of the timeout path: no copies are issued, so every consumer
+        // wait on `full` runs out and the block leaves with an error code
+        if (L.stall) return;
         const int lane = threadIdx.x - ncons;
         int k = 0;
         for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
             const int s = k % NST;
             if (k >= NST) {
                 bool ok = true;
-                if (lane == 0) ok = mbar_wait_hint(smem_addr(&empty[s]), (unsigned)(((k / NST) - 1) & 1));
+                if (lane == 0) ok = mbar_wait_hint(smem_addr(&empty[s]), (unsigned)(((k / NST) - 1) & 1), L.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) {
                     if (lane == 0) atomicExch(L.err, 2);
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
     for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
         const int s = k % NST;
         unsigned char *cur = sm + s * stage_bytes;
-        const bool ok = mbar_wait_hint(smem_addr(&full[s]), (unsigned)((k / NST) & 1));
+        const bool ok = mbar_wait_hint(smem_addr(&full[s]), (unsigned)((k / NST) & 1), L.wait_ns);
         if (!ok) {
             atomicExch(L.err, 3);
             cabort = 1;
@@ -542,8 +546,9 @@ __host__ __device__ constexpr int pair_index(int i) {
 
 // Per-row constants of the update for the 16-bit f formats, whose stored
 // f is the deviation from the reference fr_i(y) (Eq. feq at rho0 and
-// (U(y), 0, 0): U = 0, the rest equilibrium, or the Couette profile of the
-// shear device under FRE_FLAG_COUETTE_REFERENCE).  The update pulls deviations stored against the
+// (U(y), 0, 0): the Couette profile of the shear device, or U = 0, the rest
+// equilibrium, under FRE_FLAG_REST_REFERENCE and on the other devices).
+// The update pulls deviations stored against the
 // reference of their source row y - c_iy (or, on a wall link, the local
 // deviation of opp(i)); d_i = d'_i + o_i is then the deviation from this
 // row's reference, and the BGK step on deviations,
@@ -673,6 +678,9 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
     __syncthreads();
 
     if (producer) {
+        // test of the timeout path: no copies are issued, so every consumer
+        // wait on `full` runs out and the block leaves with an error code
+        if (L.stall) return;
         const int lane = threadIdx.x - ncons;
         const CoLane col = co_lane<Q>(L, lane);
         int k = 0;
@@ -680,7 +688,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
             const int s = k % NST;
             if (k >= NST) {
                 bool ok = true;
-                if (lane == 0) ok = mbar_wait_hint(smem_addr(&empty[s]), (unsigned)(((k / NST) - 1) & 1));
+                if (lane == 0) ok = mbar_wait_hint(smem_addr(&empty[s]), (unsigned)(((k / NST) - 1) & 1), L.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) {
                     if (lane == 0) atomicExch(L.err, 4);
@@ -788,7 +796,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
         const unsigned char *cur = sm + s * stage_bytes;
         // a warp whose wait timed out leaves; the producer then times out
         // on the stage it never releases, and every other wait runs out too
-        const bool ok = __all_sync(0xffffffffu, mbar_wait_hint(smem_addr(&full[s]), (unsigned)((k / NST) & 1)));
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_hint(smem_addr(&full[s]), (unsigned)((k / NST) & 1), L.wait_ns));
         if (!ok) {
             if ((threadIdx.x & 31) == 0) atomicExch(L.err, 5);
             break;

@@ -172,3 +172,46 @@ def test_batch_argument_errors(fre):
             b.remove(3)
         b.step(5)  # an empty batch steps nothing
         assert b.slots() == []
+
+
+# C3-like D2Q9 slots (the benchmarked batch workload's kinds and physics:
+# A = kappa = 0.01, tau_f = 2, tau_g = 1, Gamma = 1; shear Ny = Nx/2,
+# four-roller Ny = Nx; Ca 0.2 and R/H 0.2 give u_w = Ca sigma / (2 mu R/H))
+C3_PHYS = dict(tau_f=2.0, tau_g=1.0, A=0.01, kappa=0.01, gamma_mob=1.0, rho0=1.0)
+_SIGMA = (8.0 * 0.01 * 0.01 / 9.0) ** 0.5
+_UW = 0.2 * _SIGMA / (2.0 * 0.5 * 0.2)
+C3_LIKE = [
+    ("shear", (64, 32, 1), (31.5, 15.5, 0.0, 6.4), dict(u_wall=_UW)),
+    ("four_roller", (64, 64, 1), (31.5, 31.5, 0.0, 6.4), dict(u_wall=_UW)),
+    ("shear", (128, 64, 1), (63.5, 31.5, 0.0, 12.8), dict(u_wall=_UW)),
+    ("four_roller", (96, 96, 1), (47.5, 47.5, 0.0, 9.6), dict(u_wall=_UW)),
+    ("shear", (160, 80, 1), (79.5, 39.5, 0.0, 16.0), dict(u_wall=_UW)),
+]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_fp32_batch_slots_vs_oracle(fre, orc, mode):
+    """FP32 slots of a C3-like batch (shear and four-roller D2Q9 cases of
+    uneven sizes), each launch mode pinned in turn, against the FP64 oracle
+    after 200 steps: 1e-5 relative L-inf on rho and phi, 1e-4 on u against
+    max(|u|, 0.01) (the FP32 bounds of the row and per-node kernels)."""
+    with fre.Batch("d2q9", "fp32") as b:
+        b.set_mode(mode, 64)
+        slots, oracles = [], []
+        for device, shape, drop, kw in C3_LIKE:
+            nx, ny, nz = shape
+            args = dict(C3_PHYS, **kw)
+            slots.append(b.add(*drop, lattice="d2q9", device=device, nx=nx, ny=ny, nz=nz, **args))
+            o = orc.Oracle(0, DEV[device], nx, ny, nz, args["tau_f"], args["tau_g"], args["A"], args["kappa"],
+                           args["gamma_mob"], args["u_wall"], args["rho0"])
+            o.init_droplet(*drop)
+            oracles.append(o)
+        b.step(150)
+        b.step(50)
+        t = b.tuning()
+        assert t["mode"] == mode
+        for s, o in zip(slots, oracles):
+            o.step(200)
+            assert b.steps_taken(s) == 200
+            e = errs(b.fields(s), o.fields(), u_floor=0.01)
+            assert all(v < (1e-4 if k.startswith("u") else 1e-5) for k, v in e.items()), (s, mode, e)

@@ -509,6 +509,125 @@ def test_brute_force_one_step(orc, lattice, shape):
     assert np.abs(go - g_new).max() < 1e-13
 
 
+# ------------------------------------------- four-roller links, one step
+
+def _four_roller_geometry(nx, ny, u_w):
+    """The four-roller device from its description alone (Sec. 3; layout
+    read from the device figure): four cylinders of radius nx/8 along z,
+    centred at ((nx-1)/2 +- nx/4, (ny-1)/2 +- ny/4); top right and bottom
+    left turn counter-clockwise, top left and bottom right clockwise, all at
+    surface speed u_w.  Returns the roller id per (y, x) (0 fluid) and the
+    centres and angular velocities by id."""
+    r = nx / 8.0
+    cx, cy = 0.5 * (nx - 1), 0.5 * (ny - 1)
+    om = u_w / r
+    rollers = {1: (cx + nx / 4, cy + ny / 4, om), 2: (cx - nx / 4, cy + ny / 4, -om),
+               3: (cx - nx / 4, cy - ny / 4, om), 4: (cx + nx / 4, cy - ny / 4, -om)}
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    ident = np.zeros((ny, nx), dtype=int)
+    for k in (4, 3, 2, 1):  # the first roller that contains a node claims it
+        x0, y0, _ = rollers[k]
+        ident[(xx - x0) ** 2 + (yy - y0) ** 2 <= r * r] = k
+    return ident, rollers
+
+
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 16, 16)), (1, (3, 16, 16))])
+def test_brute_force_one_step_four_roller(orc, lattice, shape):
+    """One step of the four-roller device on a small lattice from random
+    populations, recomputed from the geometry alone: the staircase mask,
+    stencil values at solids as the w-weighted mean of their fluid
+    neighbours, and on every link whose source x - c_i is a roller node the
+    half-way bounce-back f_i(x) = f*_ibar(x) + 2 w_i rho0 (c_i . u_w) / cs^2
+    (g: phi(x, t) in place of rho0) with the wall velocity of the rigid
+    rotation at the link's wall point, u_w = omega_k z x (x - c_i / 2 - c_k).
+    Every fluid population agrees with the oracle to 1e-13.  The link wall
+    point and the ghost rule are readings (no closed form fixes them); this
+    pins their indices, signs and points."""
+    nz, ny, nx = shape
+    c, _ = _lat(orc, lattice)
+    q, d = c.shape[0], (2 if lattice == 0 else 3)
+    w = np.array([{0: 4 / 9, 1: 1 / 9, 2: 1 / 36}[int(v)] if d == 2 else {0: 1 / 3, 1: 1 / 18, 2: 1 / 36}[int(v)]
+                  for v in (c ** 2).sum(1)])
+    opp = [int(np.flatnonzero((c == -c[i]).all(1))[0]) for i in range(q)]
+    cd = c[:, :d]
+    ci = c.astype(int)
+    tau_f, tau_g, A, kappa, Gamma, u_w, rho0 = 0.8, 1.3, 0.03, 0.05, 0.7, 0.04, 1.0
+    ident2, rollers = _four_roller_geometry(nx, ny, u_w)
+    ident = np.broadcast_to(ident2, shape)
+    solid = ident > 0
+    fluid = ~solid
+    rng = np.random.default_rng(9)
+    f = w[:, None, None, None] * (1.0 + 0.1 * rng.uniform(-1, 1, (q,) + shape))
+    g = w[:, None, None, None] * rng.uniform(-0.9, 0.9, (q,) + shape)
+    f[:, solid] = 0.0
+    g[:, solid] = 0.0
+
+    o = orc.Oracle(lattice, orc.FOUR_ROLLER, nx, ny, nz, tau_f, tau_g, A, kappa, Gamma, u_w, rho0)
+    o.load_populations(f, g)
+    o.step(1)
+    fo, go = o.populations()
+
+    def nb(a, i):
+        """a(x + c_i), periodic ([nz][ny][nx] arrays)."""
+        return np.roll(a, (-ci[i, 2], -ci[i, 1], -ci[i, 0]), axis=(0, 1, 2))
+
+    def ghosts(a):
+        num = sum(w[j] * nb(np.where(fluid, a, 0.0), j) for j in range(1, q))
+        den = sum(w[j] * nb(fluid.astype(float), j) for j in range(1, q))
+        out = a.copy()
+        out[solid] = np.where(den[solid] > 0, num[solid] / np.where(den[solid] > 0, den[solid], 1.0), 0.0)
+        return out
+
+    rho = np.where(fluid, f.sum(0), 0.0)
+    phi = ghosts(np.where(fluid, g.sum(0), 0.0))
+    lap = (2 / CS2) * sum(w[i] * (nb(phi, i) - phi) for i in range(1, q))
+    mu = ghosts(np.where(fluid, A * (phi ** 3 - phi) - kappa * lap, 0.0))
+    grad = lambda a, k: (1 / CS2) * sum(w[i] * cd[i, k] * nb(a, i) for i in range(1, q))  # noqa: E731
+    F = [mu * grad(phi, k) - grad(phi * mu, k) for k in range(d)]
+    u = [np.where(fluid, (sum(cd[i, k] * f[i] for i in range(q)) + 0.5 * F[k]) / np.where(fluid, rho, 1.0), 0.0)
+         for k in range(d)]
+
+    post_f = np.zeros_like(f)
+    post_g = np.zeros_like(g)
+    for idx in zip(*np.nonzero(fluid)):
+        r, ph, m = rho[idx], phi[idx], mu[idx]
+        uu = np.array([u[k][idx] for k in range(d)])
+        FF = np.array([F[k][idx] for k in range(d)])
+        second = [r * (CS2 * (a == b) + uu[a] * uu[b]) for a in range(d) for b in range(a, d)]
+        feq = _fit(cd, w, np.array([r, *(r * uu), *second]))
+        kk = 1 - 0.5 / tau_f
+        sec_s = [kk * (uu[a] * FF[b] + FF[a] * uu[b]) for a in range(d) for b in range(a, d)]
+        S = _fit(cd, w, np.array([0.0, *(kk * FF), *sec_s]))
+        sec_g = [Gamma * m * (a == b) + ph * uu[a] * uu[b] for a in range(d) for b in range(a, d)]
+        geq = _fit(cd, w, np.array([ph, *(ph * uu), *sec_g]), fixed=Gamma * m / CS2)
+        fi = f[(slice(None),) + idx]
+        gi = g[(slice(None),) + idx]
+        post_f[(slice(None),) + idx] = fi - (fi - feq) / tau_f + S
+        post_g[(slice(None),) + idx] = gi - (gi - geq) / tau_g
+
+    f_new = np.zeros_like(f)
+    g_new = np.zeros_like(g)
+    links = 0
+    for (z, y, x) in zip(*np.nonzero(fluid)):
+        for i in range(q):
+            xs, ys, zs = (x - ci[i, 0]) % nx, (y - ci[i, 1]) % ny, (z - ci[i, 2]) % nz
+            k = ident[zs, ys, xs]
+            if k == 0:
+                f_new[i, z, y, x] = post_f[i, zs, ys, xs]
+                g_new[i, z, y, x] = post_g[i, zs, ys, xs]
+                continue
+            links += 1
+            x0, y0, om = rollers[k]
+            xw, yw = x - 0.5 * ci[i, 0], y - 0.5 * ci[i, 1]
+            uw = np.array([-om * (yw - y0), om * (xw - x0), 0.0])[:d]
+            cu = float(cd[i] @ uw)
+            f_new[i, z, y, x] = post_f[opp[i], z, y, x] + 2 * w[i] * rho0 * cu / CS2
+            g_new[i, z, y, x] = post_g[opp[i], z, y, x] + 2 * w[i] * phi[z, y, x] * cu / CS2
+    assert links >= 40 * nz  # the step crosses many roller links
+    assert np.abs(fo[:, fluid] - f_new[:, fluid]).max() < 1e-13
+    assert np.abs(go[:, fluid] - g_new[:, fluid]).max() < 1e-13
+
+
 # ------------------------------------------------- Taylor small deformation
 
 def test_taylor_deformation_golden():

@@ -103,9 +103,9 @@ def test_d3q19_fp64_four_roller(fre, orc):
     sim, o = pair(fre, orc, "d3q19", "four_roller", 32, 32, 6, u_wall=0.01)
     sim.init_droplet(15.5, 15.5, 2.5, 5.0)
     o.init_droplet(15.5, 15.5, 2.5, 5.0)
-    sim.step(200)
-    o.step(200)
-    compare_fields(sim, o, 1e-12)
+    sim.step(500)
+    o.step(500)
+    compare_fields(sim, o, 1e-12, FIELDS + ("mu",))
     sim.close()
 
 

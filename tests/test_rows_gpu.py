@@ -55,12 +55,12 @@ def make(fre, lattice, device, nx, ny, nz, precision, flags=0, **kw):
                           flags=flags, **args)
 
 
-COUETTE = 4  # FRE_FLAG_COUETTE_REFERENCE
+REST = 8  # FRE_FLAG_REST_REFERENCE
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}")
-@pytest.mark.parametrize("precision,ref", [("fp32", 0), ("fp16dev", 0), ("bf16dev", 0), ("fp16dev", COUETTE),
-                                           ("bf16dev", COUETTE)])
+@pytest.mark.parametrize("precision,ref", [("fp32", 0), ("fp16dev", 0), ("bf16dev", 0), ("fp16dev", REST),
+                                           ("bf16dev", REST)])
 def test_row_kernels_match_per_node_kernels(fre, orc, case, precision, ref):
     """The row kernels and the per-node kernels compute the same update,
     arranged differently (the row kernels split the collision into parts
@@ -70,9 +70,9 @@ def test_row_kernels_match_per_node_kernels(fre, orc, case, precision, ref):
     (populations up to ~0.5 round to ~3e-8 per step in FP32; 200 steps of
     such errors stay below 1e-6 in the velocity moments), FP16 3e-3, BF16
     2e-2 (the 16-bit bounds of the D3Q19 test below), with f stored against
-    the rest equilibrium (ref 0) or the Couette equilibrium of the shear
-    walls (FRE_FLAG_COUETTE_REFERENCE; the periodic device has no walls and
-    keeps the rest equilibrium)."""
+    the Couette equilibrium of the shear walls (ref 0, the default; the
+    periodic device has no walls and keeps the rest equilibrium) or the
+    rest equilibrium (FRE_FLAG_REST_REFERENCE)."""
     lattice, device, nx, ny, nz, kw = case
     rows = make(fre, lattice, device, nx, ny, nz, precision, flags=ref, **kw)
     gen = make(fre, lattice, device, nx, ny, nz, precision, flags=1 | ref, **kw)
@@ -115,12 +115,13 @@ def test_row_kernels_random_populations_fp32(fre, orc):
         assert np.abs(a[k] - b[k]).max() < 1e-6, k
 
 
-@pytest.mark.parametrize("precision,ref,tol", [("fp16dev", 0, 3e-3), ("bf16dev", 0, 2e-2),
-                                               ("fp16dev", COUETTE, 3e-4), ("bf16dev", COUETTE, 3e-3)])
+@pytest.mark.parametrize("precision,ref,tol", [("fp16dev", REST, 3e-3), ("bf16dev", REST, 2e-2),
+                                               ("fp16dev", 0, 3e-4), ("bf16dev", 0, 3e-3)])
 def test_16bit_storage_vs_fp64_oracle(fre, orc, precision, ref, tol):
     """16-bit deviation storage (FP32 arithmetic) vs the FP64 oracle after 500
     steps of the D3Q19 shear droplet: relative L-inf of rho, u, phi, with f
-    stored against the rest equilibrium or the Couette equilibrium."""
+    stored against the Couette equilibrium (the default) or the rest
+    equilibrium."""
     nx, ny, nz = 64, 24, 16
     kw = dict(u_wall=0.03, tau_f=2.0, tau_g=2.0, gamma_mob=0.5)
     sim = make(fre, "d3q19", "shear", nx, ny, nz, precision, flags=ref, **kw)
