@@ -111,6 +111,35 @@ struct Pop {
             *p = from_float<S>(v - fref<Q, T>(i, rho0, U));
         }
     }
+    // store and return the value as stored (16-bit formats: rounded), so
+    // that the rest population can close the collision invariants on the
+    // stored populations
+    __device__ __forceinline__ static T stf_back(const Buf &b, long long np, int i, long long k, T v, T rho0, T U) {
+        S *p = static_cast<S *>(b.f) + (size_t)i * np + k;
+        if constexpr (!Fmt<FMT>::DEV) {
+            *p = v;
+            return v;
+        } else {
+            const T r = fref<Q, T>(i, rho0, U);
+            const S s = from_float<S>(v - r);
+            *p = s;
+            return to_float(s) + r;
+        }
+    }
+    __device__ __forceinline__ static T stg_back(const Buf &b, long long np, int i, long long k, T v) {
+        if constexpr (!Fmt<FMT>::DEV) {
+            static_cast<S *>(b.g)[(size_t)i * np + k] = v;
+            return v;
+        } else {
+            if (i == 0) {
+                b.g0[k] = v;
+                return v;
+            }
+            const S s = from_float<S>(v);
+            static_cast<S *>(b.g)[(size_t)(i - 1) * np + k] = s;
+            return to_float(s);
+        }
+    }
     __device__ __forceinline__ static void stg(const Buf &b, long long np, int i, long long k, T v) {
         if constexpr (!Fmt<FMT>::DEV) {
             static_cast<S *>(b.g)[(size_t)i * np + k] = v;
@@ -425,12 +454,12 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
         const T fs = f[i] - (f[i] - feq) * of + S;
         const T geq = w * (gmu3 + m.phi * poly);
         const T gs = g[i] - (g[i] - geq) * og;
-        fsum += fs;
-        gsum += gs;
-        P::stf(L.dst, L.G.np, i, n, fs, T(L.P.rho0), U);
-        P::stg(L.dst, L.G.np, i, n, gs);
+        fsum += P::stf_back(L.dst, L.G.np, i, n, fs, T(L.P.rho0), U);
+        gsum += P::stg_back(L.dst, L.G.np, i, n, gs);
     }
-    // rest populations close the collision invariants: sum f* = rho, sum g* = phi
+    // rest populations close the collision invariants on the values as
+    // stored: sum f* = rho, sum g* = phi (in the 16-bit formats up to the
+    // rounding of the stored f*_0, g*_0 being FP32)
     P::stf(L.dst, L.G.np, 0, n, m.rho - fsum, T(L.P.rho0), U);
     P::stg(L.dst, L.G.np, 0, n, m.phi - gsum);
 }
