@@ -153,7 +153,10 @@ typedef struct {
 typedef struct fre_ctx fre_ctx;
 
 /* Device bytes a context with these parameters allocates (populations in
- * two buffers, phi/mu fields, geometry, reduction scratch); 0 if invalid. */
+ * two buffers, phi/mu fields, geometry, reduction scratch, the component
+ * labelling of fre_components); 0 if invalid.  The FP64 staging of the
+ * host field and population copies (48 bytes per node, made on their first
+ * use) is not included. */
 size_t fre_device_bytes(const fre_params *p);
 
 /* Create a context.  cuda_stream is a cudaStream_t (NULL: the context
@@ -201,6 +204,22 @@ fre_status fre_copy_fields(fre_ctx *c, double *rho, double *ux, double *uy,
 /* Observables of the current step (FP64 device reductions); synchronises.
  * Returns FRE_ERR_UNSTABLE (with *out filled) when out->status != 0. */
 fre_status fre_observables(fre_ctx *c, fre_obs *out);
+
+/* Connected components of the droplet phase, for breakup detection (Sec. 3:
+ * a drop that breaks up leaves separate drops).  The phase is the set of
+ * fluid nodes with phi > 0 at the current step (the decision taken in the
+ * context's compute precision); two of its nodes are connected when a
+ * lattice velocity links them (D2Q9: 8 neighbours, D3Q19: 18), with the
+ * device's periodic wrap (x and z always, y except across the shear
+ * walls).  *count receives the number of components of at least min_size
+ * nodes (min_size <= 1: all); sizes (nullable when max_sizes is 0) the node
+ * counts of up to max_sizes of them, largest first, 0 past the last;
+ * labels (nullable) n ints: -1 outside the phase, else the smallest node
+ * index of the node's component (every component, whatever its size; the
+ * labels do not depend on the order of the GPU's threads).  Uses 8 bytes
+ * of device memory per node, allocated on the first call and counted by
+ * fre_device_bytes.  Synchronises. */
+fre_status fre_components(fre_ctx *c, long long min_size, int *count, long long *sizes, int max_sizes, int *labels);
 
 /* Steps taken since the last initialisation. */
 long long fre_step_count(const fre_ctx *c);
@@ -322,10 +341,11 @@ void fre_batch_destroy(fre_batch *b);
  * together, checked every check_every of their own steps and retired when a
  * stopping rule holds (Sec. 3 measures the deformation D of the droplet):
  *   FRE_SERVE_CONVERGED  |D - D_prev| < tol_D between consecutive checks;
- *   FRE_SERVE_BREAKUP    no node with phi > 0 left, or the Laplace pressure
- *                        dp at the centroid below breakup_frac (d - 1)
- *                        sigma / R0, sigma = sqrt(8 kappa A / 9): the
- *                        centroid left the liquid, the drop split;
+ *   FRE_SERVE_BREAKUP    no node with phi > 0 left, or the phase phi > 0 has
+ *                        fallen apart into two or more drops: connected
+ *                        components (fre_components) of at least
+ *                        breakup_min_frac of the initial droplet's nodes
+ *                        (4/3 pi R^3, or pi R^2 in 2D; at least 1);
  *   FRE_SERVE_UNSTABLE   non-finite values or |u| > 0.3;
  *   FRE_SERVE_MAX_STEPS  max_steps reached.
  * Retired contexts stay allocated in a pool and serve later requests of the
@@ -351,7 +371,8 @@ typedef struct {
     int check_every;         /* steps of a request between two checks */
     double tol_D;            /* convergence threshold on |D - D_prev| */
     long long max_steps;     /* step cap of a request */
-    double breakup_frac;     /* breakup threshold on dp, fraction of (d-1) sigma / R0 */
+    double breakup_min_frac; /* smallest drop that counts toward a breakup, as a
+                                fraction of the initial droplet's nodes, in [0, 1] */
 } fre_serve_config;
 
 typedef struct {

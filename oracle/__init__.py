@@ -92,6 +92,8 @@ def lib():
             L.orc_feq.argtypes = [C.c_int, C.c_double, dp, dp]
             L.orc_geq.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, dp, dp]
             L.orc_guo.argtypes = [C.c_int, C.c_double, dp, dp, dp]
+            L.orc_label_phase.restype = C.c_int
+            L.orc_label_phase.argtypes = [C.c_void_p, dp, C.POINTER(C.c_int)]
             L.orc_num_threads.restype = C.c_int
             L.orc_set_num_threads.argtypes = [C.c_int]
             _lib = L
@@ -204,3 +206,17 @@ class Oracle:
         o = Obs()
         lib().orc_observables(self._h, C.byref(o))
         return o.as_dict()
+
+    def label_phase(self, phi=None):
+        """Components of the phase phi > 0 (phi: [nz][ny][nx], default the
+        oracle's own current phi): (count, labels), labels -1 outside the
+        phase, else the smallest node index of the component."""
+        if phi is None:
+            phi = self.fields()["phi"]
+        phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+        assert phi.size == self.n
+        labels = np.zeros(self.n, dtype=np.int32)
+        count = lib().orc_label_phase(self._h, _ptr(phi), labels.ctypes.data_as(C.POINTER(C.c_int)))
+        if count < 0:
+            raise MemoryError("oracle: label_phase")
+        return count, labels.reshape(self.shape)

@@ -42,9 +42,11 @@
  *     cylinders of radius nx/8 centred at ((nx-1)/2 +- nx/4, (ny-1)/2 +- ny/4),
  *     surface speed u_wall, top-right and bottom-left counter-clockwise, the
  *     other two clockwise, periodic outer box), fully periodic box.
- * Parity unpinned: the four-roller wall point of a link (x - c_i/2) and the
- * weighted-mean stencil rule at roller solids are readings that no closed
- * form fixes; they are checked only against the CUDA path.
+ * The four-roller wall point of a link (x - c_i/2) and the weighted-mean
+ * stencil rule at roller solids are readings that no closed form fixes;
+ * the tests recompute one step of them from the geometry alone (indices,
+ * signs, points).  For a rigid rotation c_i . u_w does not depend on where
+ * along the link the wall point sits (c_i . (z x c_i) = 0).
  *
  * Canonical direction order (also the exchange order of the populations):
  *   D2Q9 : 0 (0,0); 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1); 5 (1,1); 6 (-1,1);
@@ -713,6 +715,51 @@ int orc_observables(orc_state *s, orc_obs *o)
     }
     o->status = bad ? 1 : (umax > 0.3 ? 2 : 0);
     return 0;
+}
+
+/* ---------------------------------------------------- droplet components */
+
+/* Connected components of the droplet phase, for breakup detection (Sec. 3:
+ * a drop that breaks up leaves two or more separate drops).  The phase is
+ * the set of fluid nodes with phi > 0 (phi = +1 inside the droplet).  Two
+ * nodes of the phase are connected when a lattice velocity links them
+ * (D2Q9: the 8 neighbours, D3Q19: the 18), with the device's periodic wrap:
+ * x and z always, y except across the shear walls.  labels[n] = -1 outside
+ * the phase, else the smallest node index of n's component.  A plain
+ * breadth-first flood fill started from each unvisited phase node in
+ * increasing index order, so the start node is its component's smallest
+ * index.  Returns the number of components (-1 if out of memory). */
+int orc_label_phase(const orc_state *s, const double *phi, int *labels)
+{
+    const long long n = s->n;
+    long long *queue = (long long *)malloc((size_t)(n > 0 ? n : 1) * sizeof(long long));
+    if (!queue) return -1;
+    for (long long k = 0; k < n; ++k)
+        labels[k] = (!s->solid[k] && phi[k] > 0.0) ? -2 : -1; /* -2: not yet visited */
+    int count = 0;
+    for (long long start = 0; start < n; ++start) {
+        if (labels[start] != -2) continue;
+        ++count;
+        long long head = 0, tail = 0;
+        queue[tail++] = start;
+        labels[start] = (int)start;
+        while (head < tail) {
+            long long m = queue[head++];
+            int x, y, z;
+            coords(s, m, &x, &y, &z);
+            for (int i = 1; i < s->q; ++i) {
+                int yn = y + s->c[i][1];
+                if (s->p.device == ORC_SHEAR && (yn < 0 || yn >= s->p.ny)) continue;
+                long long nb = node(s, wrap(x + s->c[i][0], s->p.nx), wrap(yn, s->p.ny),
+                                    wrap(z + s->c[i][2], s->p.nz));
+                if (labels[nb] != -2) continue;
+                labels[nb] = (int)start;
+                queue[tail++] = nb;
+            }
+        }
+    }
+    free(queue);
+    return count;
 }
 
 int orc_num_threads(void)

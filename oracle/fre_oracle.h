@@ -70,6 +70,11 @@ int orc_fields(orc_state *s, double *rho, double *ux, double *uy, double *uz,
                double *phi, double *mu);
 int orc_observables(orc_state *s, orc_obs *out);
 
+/* Components of the phase phi > 0 (fluid nodes; phi given per node, n
+ * values): labels[n] = -1 outside, else the smallest node index of the
+ * component; returns the number of components.  See fre_oracle.c. */
+int orc_label_phase(const orc_state *s, const double *phi, int *labels);
+
 /* single-node building blocks, exposed so the tests can pin them */
 int orc_lattice_info(int lattice, int *q, int *c /* q*3 */, double *w /* q */);
 void orc_feq(int lattice, double rho, const double u[3], double *out);

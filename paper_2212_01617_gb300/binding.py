@@ -31,7 +31,7 @@ DEVICES = {"shear": FRE_SHEAR, "four_roller": FRE_FOUR_ROLLER, "periodic": FRE_P
 EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_fields",
            "fre_load_populations", "fre_store_populations", "fre_step", "fre_step_timed",
            "fre_copy_fields", "fre_observables", "fre_step_count", "fre_uses_row_kernels",
-           "fre_kernel_path", "fre_moments_noalloc",
+           "fre_kernel_path", "fre_components", "fre_moments_noalloc",
            "fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
            "fre_batch_observables", "fre_batch_context", "fre_batch_slots", "fre_batch_bytes_in_use",
            "fre_batch_tuning", "fre_batch_set_mode", "fre_batch_synchronize", "fre_batch_destroy",
@@ -81,7 +81,7 @@ SERVE_OUTCOMES = {0: "running", 1: "converged", 2: "breakup", 3: "max_steps", 4:
 class fre_serve_config(C.Structure):
     _fields_ = [("budget_bytes", C.c_size_t), ("target_nodes", C.c_longlong), ("max_running", C.c_int),
                 ("chunk_steps", C.c_int), ("check_every", C.c_int), ("tol_D", C.c_double),
-                ("max_steps", C.c_longlong), ("breakup_frac", C.c_double)]
+                ("max_steps", C.c_longlong), ("breakup_min_frac", C.c_double)]
 
 
 class fre_serve_result(C.Structure):
@@ -134,6 +134,9 @@ def load_library(path: str = LIB_PATH):
         L.fre_uses_row_kernels.argtypes = [vp]
         L.fre_kernel_path.restype = C.c_int
         L.fre_kernel_path.argtypes = [vp]
+        L.fre_components.restype = C.c_int
+        L.fre_components.argtypes = [vp, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.c_int,
+                                     C.POINTER(C.c_int)]
         L.fre_moments_noalloc.restype = C.c_int
         L.fre_moments_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]
         L.fre_destroy.argtypes = [vp]
@@ -286,6 +289,19 @@ def fre_kernel_path(h) -> int:
     return int(load_library().fre_kernel_path(h))
 
 
+def fre_components(h, min_size=1, max_sizes=16, n=None):
+    """Components of the phase phi > 0: (count, sizes largest first, labels
+    or None).  Labels are returned when n (the node count) is given."""
+    cnt = C.c_int(0)
+    sz = np.zeros(max(max_sizes, 1), dtype=np.int64)
+    lab = np.zeros(n, dtype=np.int32) if n else None
+    _check(load_library().fre_components(h, int(min_size), C.byref(cnt),
+                                         sz.ctypes.data_as(C.POINTER(C.c_longlong)), int(max_sizes),
+                                         lab.ctypes.data_as(C.POINTER(C.c_int)) if lab is not None else None),
+           "fre_components")
+    return cnt.value, [int(v) for v in sz[:max_sizes] if v > 0], lab
+
+
 def fre_moments_noalloc(lattice, nx, ny, nz, f_dev_ptr, g_dev_ptr, out_dev_ptr, stream=None):
     """Device pointers in, device pointer out; queued on `stream`."""
     lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
@@ -360,6 +376,11 @@ class Simulation:
 
     def observables(self) -> dict:
         return fre_observables(self.h)
+
+    def components(self, min_size=1, max_sizes=16, labels=False):
+        """(count, sizes, labels[nz][ny][nx] or None) of the phase phi > 0."""
+        cnt, sz, lab = fre_components(self.h, min_size, max_sizes, self.n if labels else None)
+        return cnt, sz, (lab.reshape(self.shape) if lab is not None else None)
 
     @property
     def steps_taken(self) -> int:
@@ -480,11 +501,11 @@ class Server:
 
     def __init__(self, lattice="d3q19", precision="fp16dev", budget_bytes=150 << 30, target_nodes=0,
                  max_running=0, chunk_steps=250, check_every=1000, tol_D=1e-4, max_steps=100000,
-                 breakup_frac=0.25, stream=None):
+                 breakup_min_frac=0.005, stream=None):
         self.lattice = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg = fre_serve_config(int(budget_bytes), int(target_nodes), int(max_running), int(chunk_steps),
-                               int(check_every), float(tol_D), int(max_steps), float(breakup_frac))
+                               int(check_every), float(tol_D), int(max_steps), float(breakup_min_frac))
         h = C.c_void_p()
         st = stream if stream is not None else current_stream_handle()
         _check(load_library().fre_server_create(self.lattice, self.precision, C.byref(cfg),

@@ -2,6 +2,7 @@
 // memory, geometry, and the launch sequence of one time step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -83,9 +84,16 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
     return true;
 }
 
+// roots the component labelling lists at most (fre_components)
+constexpr int kCclCap = 4096;
+
+// device bytes of the component labelling: labels and sizes per node, the
+// root list (allocated on first use, counted in the budget from the start)
+size_t ccl_bytes(const Sizes &s) { return 2 * sizeof(int) * (size_t)s.n + 16 * (size_t)kCclCap + 256; }
+
 size_t total_bytes(const Sizes &s) {
     return 2 * s.buf_bytes + 3 * s.field_bytes + s.solid_bytes + sizeof(double) * fre::kRedDoublesHost +
-           sizeof(fre_obs);
+           sizeof(fre_obs) + ccl_bytes(s);
 }
 
 fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
@@ -270,6 +278,21 @@ fre_status ensure_staging(fre_ctx *c) {
     fre_status s = dev_alloc(c, &p, sizeof(double) * 6 * (size_t)c->G.n);
     if (s != FRE_OK) return s;
     c->staging = static_cast<double *>(p);
+    return FRE_OK;
+}
+
+fre_status ensure_ccl(fre_ctx *c) {
+    if (c->ccl.labels) return FRE_OK;
+    const size_t n = (size_t)c->G.n;
+    void *p = nullptr;
+    fre_status s = dev_alloc(c, &p, 2 * sizeof(int) * n + 16 * (size_t)kCclCap + 256);
+    if (s != FRE_OK) return s;
+    char *b = static_cast<char *>(p);
+    c->ccl.pairs = reinterpret_cast<long long *>(b);
+    c->ccl.count = reinterpret_cast<int *>(b + 16 * (size_t)kCclCap);
+    c->ccl.labels = reinterpret_cast<int *>(b + 16 * (size_t)kCclCap + 256);
+    c->ccl.sizes = c->ccl.labels + n;
+    c->ccl.cap = kCclCap;
     return FRE_OK;
 }
 
@@ -621,6 +644,38 @@ fre_status fre_observables(fre_ctx *c, fre_obs *out) {
     if (out->status != 0)
         return fail(FRE_ERR_UNSTABLE, "fre_observables: %s", out->status == 1 ? "non-finite values" : "|u| > 0.3");
     return FRE_OK;
+}
+
+fre_status fre_components(fre_ctx *c, long long min_size, int *count, long long *sizes, int max_sizes, int *labels) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (!count || max_sizes < 0 || (max_sizes > 0 && !sizes))
+        return fail(FRE_ERR_ARG, "fre_components: count is NULL, or sizes is NULL with max_sizes > 0");
+    if (!c->initialised) return fail(FRE_ERR_STATE, "fre_components: not initialised");
+    s = ensure_ccl(c);
+    if (s != FRE_OK) return s;
+    fre::Launch L = launch_of(c);
+    current_phi_mu(c, L);
+    fre::ccl_label(L, c->p.lattice, c->p.precision, min_size < 1 ? 1 : min_size, c->ccl);
+    int nroots = 0;
+    FRE_CUDA(cudaMemcpyAsync(&nroots, c->ccl.count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    s = check_launch("fre_components");
+    if (s != FRE_OK) return s;
+    FRE_CUDA(cudaStreamSynchronize(c->stream));
+    *count = nroots;
+    if (max_sizes > 0) {
+        const int k = nroots < c->ccl.cap ? nroots : c->ccl.cap;
+        std::vector<long long> pairs(2 * (size_t)k);
+        if (k) FRE_CUDA(cudaMemcpy(pairs.data(), c->ccl.pairs, sizeof(long long) * 2 * (size_t)k,
+                                   cudaMemcpyDeviceToHost));
+        std::vector<long long> sz(k);
+        for (int j = 0; j < k; ++j) sz[j] = pairs[2 * (size_t)j];
+        std::sort(sz.begin(), sz.end(), [](long long a, long long b) { return a > b; });
+        for (int j = 0; j < max_sizes; ++j) sizes[j] = j < k ? sz[j] : 0;
+    }
+    if (labels)
+        FRE_CUDA(cudaMemcpy(labels, c->ccl.labels, sizeof(int) * (size_t)c->G.n, cudaMemcpyDeviceToHost));
+    return check_device_error(c);
 }
 
 long long fre_step_count(const fre_ctx *c) { return c ? c->step : -1; }

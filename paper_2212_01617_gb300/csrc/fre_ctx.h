@@ -27,6 +27,7 @@ struct fre_ctx {
     fre_obs *obs_host = nullptr;
     int *err_dev = nullptr;  // set by a kernel whose bounded wait timed out
     double *staging = nullptr;
+    fre::CclBuffers ccl{};  // component labelling, allocated on first use
     std::vector<void *> allocs;
     int cur = 0;        // buffer holding the state
     int pp = 1;         // phi buffer holding phi of the previous step

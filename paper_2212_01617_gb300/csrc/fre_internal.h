@@ -120,6 +120,20 @@ struct BatchKernels {
 const BatchKernels *batch_kernels_d2q9(int precision);
 const BatchKernels *batch_kernels_d3q19(int precision);
 
+// Device buffers of the component labelling (fre_components): labels and
+// sizes [n], a count and up to `cap` (size, root) pairs.
+struct CclBuffers {
+    int *labels;
+    int *sizes;
+    int *count;
+    long long *pairs;
+    int cap;
+};
+// Label the connected components of the phase phi > 0 of L.phi (fre_ccl.cu)
+// and list the roots of those with at least min_size nodes; queued on
+// L.stream.
+void ccl_label(const Launch &L, int lattice, int precision, long long min_size, const CclBuffers &B);
+
 const KernelSet *kernels_d2q9(int precision);
 const KernelSet *kernels_d3q19(int precision);
 

@@ -79,6 +79,14 @@ __device__ __forceinline__ T fref(int i, T rho0, T U) {
     return T(Lat<Q>::w(i)) * rho0 * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * U * U);
 }
 
+// fr_i - w_i rho0: the small part of the reference, O(U), evaluated apart so
+// that deviations from w_i rho0 never pass through values of size w_i
+template <int Q, typename T>
+__device__ __forceinline__ T eref(int i, T rho0, T U) {
+    const T cu = T(Lat<Q>::cx(i)) * U;
+    return T(Lat<Q>::w(i)) * rho0 * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * U * U);
+}
+
 // Population access for one buffer in a given storage format.  ldf / stf
 // take rho0 and U of the row of node k (the reference of the 16-bit f
 // formats; unused by the others).
@@ -110,6 +118,19 @@ struct Pop {
         } else {
             *p = from_float<S>(v - fref<Q, T>(i, rho0, U));
         }
+    }
+    // 16-bit formats: f_i - w_i rho0 of a stored f (deviation d from
+    // fr_i(U) plus the small part of the reference)
+    __device__ __forceinline__ static T ldw(const Buf &b, long long np, int i, long long k, T rho0, T U) {
+        return to_float(__ldg(static_cast<const S *>(b.f) + (size_t)i * np + k)) + eref<Q, T>(i, rho0, U);
+    }
+    // 16-bit formats: store f_i given as W = f_i - w_i rho0; returns W as
+    // stored (the rounded deviation plus the small part of the reference)
+    __device__ __forceinline__ static T stw_back(const Buf &b, long long np, int i, long long k, T W, T rho0, T U) {
+        const T e = eref<Q, T>(i, rho0, U);
+        const S s = from_float<S>(W - e);
+        static_cast<S *>(b.f)[(size_t)i * np + k] = s;
+        return to_float(s) + e;
     }
     // store and return the value as stored (16-bit formats: rounded), so
     // that the rest population can close the collision invariants on the
@@ -260,37 +281,56 @@ __device__ __forceinline__ int pull_source(const Geo &G, const Site &s, int i, T
 //   f_i = f*_ibar + 2 w_i rho0 (c_i . u_w)/cs^2,
 //   g_i = g*_ibar + 2 w_i phi(x, t-1) (c_i . u_w)/cs^2)
 // or read in place.
+//
+// 16-bit formats: f_i is assembled from its deviation from w_i rho0, W_i =
+// d_i + (fr_i - w_i rho0), all small numbers, and *wsum (if not NULL)
+// receives sum_i W_i = rho - rho0 without the FP32 cancellation of sums of
+// values near w_i.
 template <int Q, int FMT, bool PULL, bool WANT_F>
 __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename Fmt<FMT>::T *f,
-                                       typename Fmt<FMT>::T *g) {
+                                       typename Fmt<FMT>::T *g, typename Fmt<FMT>::T *wsum = nullptr) {
     using T = typename Fmt<FMT>::T;
     using P = Pop<Q, FMT>;
+    constexpr bool DEV = Fmt<FMT>::DEV;
     const T rho0 = T(L.P.rho0);
     // U of this node's row; a pulled population comes from row y - c_iy
-    const T U = Fmt<FMT>::DEV ? T(couette_u(L, s.y)) : T(0);
+    const T U = DEV ? T(couette_u(L, s.y)) : T(0);
     const long long np = L.G.np;
     const int n = s.n;
+    T ws = T(0);
+    // f_i from W_i (16-bit formats) or as stored
+    auto ldf = [&](int i, int k, T Uk, T extra) {
+        if constexpr (DEV) {
+            const T W = P::ldw(L.src, np, i, k, rho0, Uk) + extra;
+            ws += W;
+            return W + T(Lat<Q>::w(i)) * rho0;
+        } else {
+            return P::ldf(L.src, np, i, k, rho0, Uk) + extra;
+        }
+    };
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         if (!PULL || i == 0) {
-            if (WANT_F) f[i] = P::ldf(L.src, np, i, n, rho0, U);
+            if (WANT_F) f[i] = ldf(i, n, U, T(0));
             g[i] = P::ldg(L.src, np, i, n);
             continue;
         }
         T uwx = T(0), uwy = T(0);
         const int src = pull_source<Q, T>(L.G, s, i, uwx, uwy);
         if (src >= 0) {
-            if (WANT_F) f[i] = P::ldf(L.src, np, i, src, rho0, Fmt<FMT>::DEV ? T(couette_u(L, s.y - Lat<Q>::cy(i))) : T(0));
+            if (WANT_F) f[i] = ldf(i, src, DEV ? T(couette_u(L, s.y - Lat<Q>::cy(i))) : T(0), T(0));
             g[i] = P::ldg(L.src, np, i, src);
         } else {
             const int o = Lat<Q>::opp(i);
             const T cu = T(Lat<Q>::cx(i)) * uwx + T(Lat<Q>::cy(i)) * uwy;
             const T wi2 = T(2.0 * Lat<Q>::w(i) * 3.0);
-            if (WANT_F) f[i] = P::ldf(L.src, np, o, n, rho0, U) + wi2 * rho0 * cu;
+            // w_opp(i) = w_i: the opposite's deviation carries over
+            if (WANT_F) f[i] = ldf(o, n, U, wi2 * rho0 * cu);
             const T php = static_cast<const T *>(L.phi_prev)[n];
             g[i] = P::ldg(L.src, np, o, n) + wi2 * php * cu;
         }
     }
+    if (wsum) *wsum = ws;
 }
 
 // Macroscopic state of a node: moments, force and velocity (Algorithm 1
@@ -429,7 +469,8 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
     using P = Pop<Q, FMT>;
     const int n = s.n;
     T f[Q], g[Q];
-    gather<Q, FMT, PULL, true>(L, s, f, g);
+    T wsum = T(0);  // 16-bit formats: rho - rho0 from the small deviations
+    gather<Q, FMT, PULL, true>(L, s, f, g, &wsum);
     const Macro<T> m = macro_of<Q, FMT>(L, s, f, g);
 
     // FP32 computes take the constants rounded on the host
@@ -454,13 +495,20 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
         const T fs = f[i] - (f[i] - feq) * of + S;
         const T geq = w * (gmu3 + m.phi * poly);
         const T gs = g[i] - (g[i] - geq) * og;
-        fsum += P::stf_back(L.dst, L.G.np, i, n, fs, T(L.P.rho0), U);
+        if constexpr (Fmt<FMT>::DEV)
+            fsum += P::stw_back(L.dst, L.G.np, i, n, fs - T(Lat<Q>::w(i)) * T(L.P.rho0), T(L.P.rho0), U);
+        else
+            fsum += P::stf_back(L.dst, L.G.np, i, n, fs, T(L.P.rho0), U);
         gsum += P::stg_back(L.dst, L.G.np, i, n, gs);
     }
     // rest populations close the collision invariants on the values as
     // stored: sum f* = rho, sum g* = phi (in the 16-bit formats up to the
-    // rounding of the stored f*_0, g*_0 being FP32)
-    P::stf(L.dst, L.G.np, 0, n, m.rho - fsum, T(L.P.rho0), U);
+    // rounding of the stored f*_0; g*_0 is FP32).  16-bit f closes on the
+    // deviations from w_i rho0: (rho - rho0) - sum_{i>0} W*_i
+    if constexpr (Fmt<FMT>::DEV)
+        P::stw_back(L.dst, L.G.np, 0, n, wsum - fsum, T(L.P.rho0), U);
+    else
+        P::stf(L.dst, L.G.np, 0, n, m.rho - fsum, T(L.P.rho0), U);
     P::stg(L.dst, L.G.np, 0, n, m.phi - gsum);
 }
 

@@ -27,6 +27,7 @@ struct Request {
     double cx, cy, cz, R;
     fre_ctx *c = nullptr;
     int slot = -1;
+    long long min_drop = 1;  // nodes a component needs to count as a drop
     fre_obs last{};
 };
 
@@ -38,7 +39,6 @@ fre::ServeLimits limits_of(const fre_serve_config &cfg) {
     l.check_every = cfg.check_every;
     l.tol_D = cfg.tol_D;
     l.max_steps = cfg.max_steps;
-    l.breakup_frac = cfg.breakup_frac;
     return l;
 }
 
@@ -72,11 +72,14 @@ struct fre_server {
 
 namespace {
 
-// Laplace pressure of the initial droplet, (d - 1) sigma / R with the
-// interface tension sigma = sqrt(8 kappa A / 9) of the free energy (Sec. 2.3).
-double laplace_ref(const fre_params &p, double R) {
-    const double sigma = std::sqrt(8.0 * p.kappa * p.A / 9.0);
-    return (p.lattice == FRE_D3Q19 ? 2.0 : 1.0) * sigma / R;
+// Nodes a connected component of the phase phi > 0 needs to count as a
+// drop: breakup_min_frac of the initial droplet's nodes (4/3 pi R^3, or
+// pi R^2 in 2D), at least 1.
+long long min_drop_nodes(const fre_params &p, double R, double frac) {
+    const double pi = 3.14159265358979323846;
+    const double v0 = p.lattice == FRE_D3Q19 ? 4.0 / 3.0 * pi * R * R * R : pi * R * R;
+    const double m = std::floor(frac * v0);
+    return m > 1.0 ? (long long)m : 1;
 }
 
 void destroy_pooled(fre_server *s, size_t k) {
@@ -171,8 +174,10 @@ fre_status fre_server_create(int lattice, int precision, const fre_serve_config 
                              fre_server **out) {
     if (!out || !cfg) return sfail(FRE_ERR_ARG, "fre_server_create: NULL argument");
     *out = nullptr;
-    if (cfg->chunk_steps < 1 || cfg->check_every < 1 || cfg->max_steps < 1 || !(cfg->tol_D >= 0.0))
-        return sfail(FRE_ERR_ARG, "fre_server_create: chunk_steps, check_every, max_steps must be >= 1, tol_D >= 0");
+    if (cfg->chunk_steps < 1 || cfg->check_every < 1 || cfg->max_steps < 1 || !(cfg->tol_D >= 0.0) ||
+        !(cfg->breakup_min_frac >= 0.0 && cfg->breakup_min_frac <= 1.0))
+        return sfail(FRE_ERR_ARG, "fre_server_create: chunk_steps, check_every, max_steps must be >= 1, tol_D >= 0, "
+                                  "0 <= breakup_min_frac <= 1");
     fre_server *s = new fre_server(*cfg);
     s->lattice = lattice;
     s->precision = precision;
@@ -210,9 +215,10 @@ fre_status fre_server_submit(fre_server *s, const fre_params *p, double cx, doub
     const size_t bytes = (R > 0.0 && std::isfinite(cx) && std::isfinite(cy) && std::isfinite(cz))
                              ? fre_device_bytes(p) : 0;
     const long long nodes = (long long)p->nx * p->ny * p->nz;
-    *id = s->policy.submit(nodes, bytes, bytes ? laplace_ref(*p, R) : 0.0, s->now());
+    *id = s->policy.submit(nodes, bytes, s->now());
     Request r;
     r.p = *p;
+    r.min_drop = bytes ? min_drop_nodes(*p, R, s->cfg.breakup_min_frac) : 1;
     r.cx = cx;
     r.cy = cy;
     r.cz = cz;
@@ -251,7 +257,14 @@ fre_status fre_server_advance(fre_server *s, int *running) {
                     continue;
                 }
                 r.last = o;
-                const int outcome = s->policy.checked(id, o.D, o.dp, o.drop_count, o.status, s->now());
+                int drops = 0;
+                if (o.status == 0 && o.drop_count > 0.0 &&
+                    fre_components(r.c, r.min_drop, &drops, nullptr, 0, nullptr) != FRE_OK) {
+                    s->policy.failed(id, s->now());
+                    retire(s, r);
+                    continue;
+                }
+                const int outcome = s->policy.checked(id, o.D, drops, o.drop_count, o.status, s->now());
                 if (outcome != fre::SERVE_RUNNING) retire(s, r);
             }
         }

@@ -681,6 +681,10 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
     // self-fed mode: releases of each stage so far (a count that only rises;
     // the warp that brings it to a multiple of the consumer warps is last)
     __shared__ unsigned rel_s[SELF ? NST : 1];
+    // self-fed mode: the per-lane lookups of the refill (couette_consts),
+    // made once per block
+    __shared__ CoLane colane_s[SELF ? 32 : 1];
+    if (SELF && threadIdx.x < 32) colane_s[threadIdx.x] = co_lane<Q>(L, threadIdx.x);
     // a stage is released by each consumer warp on its own once it has read
     // it, so the consumer warps never wait for one another
     if (threadIdx.x == 0) {
@@ -810,7 +814,7 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
     // timeout test, whose waits then run out)
     if constexpr (SELF) {
         if (threadIdx.x < 32 && !L.stall) {
-            const CoLane col = co_lane<Q>(L, threadIdx.x);
+            const CoLane col = colane_s[threadIdx.x];
             for (int k = 0; k < NST; ++k) {
                 const int unit = blockIdx.x + k * gridDim.x;
                 if (unit < nunits) produce(unit, k, threadIdx.x, col);
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 fence_async_smem();
                 const int kn = k + NST;
                 const int un = blockIdx.x + kn * (int)gridDim.x;
-                if (un < nunits) produce(un, kn, threadIdx.x & 31, co_lane<Q>(L, threadIdx.x & 31));
+                if (un < nunits) produce(un, kn, threadIdx.x & 31, colane_s[threadIdx.x & 31]);
             }
         } else {
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));

@@ -7,9 +7,10 @@
 // Stopping rules (checked every `check_every` steps of a request):
 //   converged -- |D - D_prev| < tol_D between two consecutive checks, D the
 //                deformation of the droplet's moment ellipse (Sec. 3);
-//   breakup   -- no node with phi > 0 is left, or the Laplace pressure at
-//                the droplet centroid fell below breakup_frac x (d - 1) sigma
-//                / R0 (the centroid has left the liquid: the drop split);
+//   breakup   -- no node with phi > 0 is left, or the phase phi > 0 falls
+//                apart into two or more connected components (the drop
+//                split; the executor counts the components large enough to
+//                be drops, fre_components);
 //   unstable  -- the observables saw non-finite values or |u| > 0.3;
 //   max_steps -- the request reached its step cap.
 #pragma once
@@ -39,19 +40,18 @@ struct ServeLimits {
     int check_every = 1000;      // steps between two checks of a request
     double tol_D = 1e-4;         // convergence threshold on |D - D_prev|
     long long max_steps = 100000;
-    double breakup_frac = 0.25;
 };
 
 struct ServeJob {
     long long id = 0;
     long long nodes = 0;
     size_t bytes = 0;
-    double dp_ref = 0.0;  // (d - 1) sigma / R0, the Laplace pressure at start
     double t_submit = 0.0, t_admit = -1.0, t_done = -1.0;
     long long steps = 0;      // steps taken since admission
     long long next_check = 0;  // step count of its next check
     int checks = 0;
-    double D_prev = 0.0, D = 0.0, dp = 0.0;
+    double D_prev = 0.0, D = 0.0;
+    int components = 0;  // drops found at the last check
     int outcome = SERVE_RUNNING;
     bool running = false;
 };
@@ -66,12 +66,11 @@ class ServePolicy {
 
     // Queue a request; returns its id.  A request that can never fit the
     // budget is finished at once as REJECTED.
-    long long submit(long long nodes, size_t bytes, double dp_ref, double t_now) {
+    long long submit(long long nodes, size_t bytes, double t_now) {
         ServeJob j;
         j.id = next_id_++;
         j.nodes = nodes;
         j.bytes = bytes;
-        j.dp_ref = dp_ref;
         j.t_submit = t_now;
         jobs_[j.id] = j;
         if (bytes == 0 || bytes > lim_.budget_bytes) {
@@ -146,20 +145,21 @@ class ServePolicy {
         return best;
     }
 
-    // Result of a check: D, Laplace pressure dp, nodes with phi > 0, and the
-    // observables status (0 ok).  Returns the outcome (RUNNING to go on).
-    int checked(long long id, double D, double dp, double drop_count, int status, double t_now) {
+    // Result of a check: D, the number of drops (connected components of
+    // the phase phi > 0 large enough to count), the nodes with phi > 0, and
+    // the observables status (0 ok).  Returns the outcome (RUNNING to go on).
+    int checked(long long id, double D, int components, double drop_count, int status, double t_now) {
         auto it = jobs_.find(id);
         if (it == jobs_.end() || !it->second.running) return SERVE_FAILED;
         ServeJob &j = it->second;
         j.D_prev = j.D;
         j.D = D;
-        j.dp = dp;
+        j.components = components;
         ++j.checks;
         j.next_check = j.steps + lim_.check_every;
         int out = SERVE_RUNNING;
         if (status != 0) out = SERVE_UNSTABLE;
-        else if (drop_count <= 0.0 || dp < lim_.breakup_frac * j.dp_ref) out = SERVE_BREAKUP;
+        else if (drop_count <= 0.0 || components >= 2) out = SERVE_BREAKUP;
         else if (j.checks >= 2 && (j.D - j.D_prev < lim_.tol_D && j.D_prev - j.D < lim_.tol_D)) out = SERVE_CONVERGED;
         else if (j.steps >= lim_.max_steps) out = SERVE_MAX_STEPS;
         if (out != SERVE_RUNNING) finish(j, out, t_now);

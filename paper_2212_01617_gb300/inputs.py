@@ -75,3 +75,28 @@ def serving_trace(n: int = 400, rate: float = 20.0, seed: int = SEED + 4):
                     "ca": float(r.uniform(0.05, 0.45)),
                     "r_over_h": float(r.uniform(0.1, 0.3))})
     return out
+
+
+def multi_drop_phi(shape, n_drops: int, seed: int = SEED + 5, r_min: float = 1.5, r_max: float = 6.0,
+                   periodic=(True, True, True)):
+    """A phi field [nz][ny][nx] holding n_drops drops of random centres and
+    radii (uniform in [r_min, r_max]): phi = the largest of tanh((R_k - d_k)
+    / sqrt(2)) over the drops, d_k the distance to drop k's centre, taken
+    with the periodic wrap along the axes flagged in `periodic` (z, y, x)."""
+    r = rng(seed)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    phi = -np.ones(shape)
+    for _ in range(n_drops):
+        c = (r.uniform(0, nz), r.uniform(0, ny), r.uniform(0, nx))
+        R = r.uniform(r_min, r_max)
+        d2 = np.zeros(shape)
+        for coord, n, cc, per in ((z, nz, c[0], periodic[0]), (y, ny, c[1], periodic[1]), (x, nx, c[2], periodic[2])):
+            if n == 1:
+                continue
+            dd = np.abs(coord - cc)
+            if per:
+                dd = np.minimum(dd, n - dd)
+            d2 += dd * dd
+        phi = np.maximum(phi, np.tanh((R - np.sqrt(d2)) / np.sqrt(2.0)))
+    return phi

@@ -7,7 +7,7 @@
 extern "C" {
 
 void *sp_create(unsigned long long budget, long long target_nodes, int max_running, int check_every, double tol_D,
-                long long max_steps, double breakup_frac) {
+                long long max_steps) {
     fre::ServeLimits l;
     l.budget_bytes = (size_t)budget;
     l.target_nodes = target_nodes;
@@ -15,14 +15,13 @@ void *sp_create(unsigned long long budget, long long target_nodes, int max_runni
     l.check_every = check_every;
     l.tol_D = tol_D;
     l.max_steps = max_steps;
-    l.breakup_frac = breakup_frac;
     return new fre::ServePolicy(l);
 }
 
 void sp_destroy(void *p) { delete static_cast<fre::ServePolicy *>(p); }
 
-long long sp_submit(void *p, long long nodes, unsigned long long bytes, double dp_ref, double t) {
-    return static_cast<fre::ServePolicy *>(p)->submit(nodes, (size_t)bytes, dp_ref, t);
+long long sp_submit(void *p, long long nodes, unsigned long long bytes, double t) {
+    return static_cast<fre::ServePolicy *>(p)->submit(nodes, (size_t)bytes, t);
 }
 
 static int copy_ids(const std::vector<long long> &v, long long *out, int max) {
@@ -44,8 +43,8 @@ int sp_due(void *p, long long *out, int max) { return copy_ids(static_cast<fre::
 
 long long sp_steps_to_next_check(void *p) { return static_cast<fre::ServePolicy *>(p)->steps_to_next_check(); }
 
-int sp_checked(void *p, long long id, double D, double dp, double count, int status, double t) {
-    return static_cast<fre::ServePolicy *>(p)->checked(id, D, dp, count, status, t);
+int sp_checked(void *p, long long id, double D, int components, double count, int status, double t) {
+    return static_cast<fre::ServePolicy *>(p)->checked(id, D, components, count, status, t);
 }
 
 int sp_take_finished(void *p, long long *out, int max) {

@@ -45,12 +45,13 @@ def test_device_bytes_and_validation(fre):
     p = fre.make_params("d3q19", "fp32", "shear", 512, 256, 256, 1.0, 1.0)
     n = 512 * 256 * 256
     b = fre.fre_device_bytes(p)
-    # two buffers of f and g, 19 FP32 populations each, plus three FP32 fields
-    assert b >= 2 * 2 * 19 * 4 * n + 3 * 4 * n
-    assert b < 2 * 2 * 19 * 4 * n + 3 * 4 * n + (1 << 22)
+    # two buffers of f and g, 19 FP32 populations each, three FP32 fields and
+    # the labels and sizes of the component labelling (two ints per node)
+    assert b >= 2 * 2 * 19 * 4 * n + 3 * 4 * n + 2 * 4 * n
+    assert b < 2 * 2 * 19 * 4 * n + 3 * 4 * n + 2 * 4 * n + (1 << 22)
     p16 = fre.make_params("d3q19", "fp16dev", "shear", 512, 256, 256, 1.0, 1.0)
     b16 = fre.fre_device_bytes(p16)
-    assert abs(b16 - (2 * (19 * 2 + 18 * 2 + 4) * n + 3 * 4 * n)) < (1 << 22)
+    assert abs(b16 - (2 * (19 * 2 + 18 * 2 + 4) * n + 3 * 4 * n + 2 * 4 * n)) < (1 << 22)
     bad = [
         fre.make_params("d2q9", "fp64", "shear", 16, 8, 2),          # D2Q9 with nz != 1
         fre.make_params("d2q9", "fp64", "shear", 16, 8, 1, tau_f=0.5),  # tau must be > 1/2

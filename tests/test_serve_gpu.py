@@ -113,8 +113,8 @@ REQS3 = [
     ("periodic", (64, 10, 8), (32.0, 5.0, 4.0, 3.0), dict()),
 ]
 # every request runs exactly 1 + 300 steps: no convergence (tol_D = 0) and
-# no breakup test (breakup_frac far below any Laplace pressure)
-SERVE3 = dict(chunk_steps=50, check_every=100, tol_D=0.0, max_steps=300, breakup_frac=-1e30)
+# no breakup within 300 steps of these small, weakly sheared drops
+SERVE3 = dict(chunk_steps=50, check_every=100, tol_D=0.0, max_steps=300)
 
 
 def serve3(fre, precision, mode, reqs):

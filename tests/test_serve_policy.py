@@ -24,10 +24,10 @@ def sp(tmp_path_factory):
     L = C.CDLL(out)
     vp, ll, d = C.c_void_p, C.c_longlong, C.c_double
     L.sp_create.restype = vp
-    L.sp_create.argtypes = [C.c_ulonglong, ll, C.c_int, C.c_int, d, ll, d]
+    L.sp_create.argtypes = [C.c_ulonglong, ll, C.c_int, C.c_int, d, ll]
     L.sp_destroy.argtypes = [vp]
     L.sp_submit.restype = ll
-    L.sp_submit.argtypes = [vp, ll, C.c_ulonglong, d, d]
+    L.sp_submit.argtypes = [vp, ll, C.c_ulonglong, d]
     for name in ("sp_admit", "sp_due", "sp_take_finished"):
         getattr(L, name).restype = C.c_int
     L.sp_admit.argtypes = [vp, d, C.POINTER(ll), C.c_int]
@@ -38,7 +38,7 @@ def sp(tmp_path_factory):
     L.sp_steps_to_next_check.restype = ll
     L.sp_steps_to_next_check.argtypes = [vp]
     L.sp_checked.restype = C.c_int
-    L.sp_checked.argtypes = [vp, ll, d, d, d, C.c_int, d]
+    L.sp_checked.argtypes = [vp, ll, d, C.c_int, d, C.c_int, d]
     L.sp_job.restype = C.c_int
     L.sp_job.argtypes = [vp, ll, C.POINTER(C.c_int), C.POINTER(ll), C.POINTER(d), C.POINTER(d)]
     for name in ("sp_running", "sp_queued"):
@@ -53,9 +53,9 @@ def sp(tmp_path_factory):
 
 class Policy:
     def __init__(self, L, budget, target_nodes=0, max_running=0, check_every=1000, tol_D=1e-4,
-                 max_steps=100000, breakup_frac=0.25):
+                 max_steps=100000):
         self.L = L
-        self.h = L.sp_create(budget, target_nodes, max_running, check_every, tol_D, max_steps, breakup_frac)
+        self.h = L.sp_create(budget, target_nodes, max_running, check_every, tol_D, max_steps)
 
     def __del__(self):
         self.L.sp_destroy(self.h)
@@ -65,8 +65,8 @@ class Policy:
         n = fn(self.h, *a, buf, 4096)
         return [buf[i] for i in range(n)]
 
-    def submit(self, nodes, nbytes, dp_ref=1.0, t=0.0):
-        return self.L.sp_submit(self.h, nodes, nbytes, dp_ref, t)
+    def submit(self, nodes, nbytes, t=0.0):
+        return self.L.sp_submit(self.h, nodes, nbytes, t)
 
     def admit(self, t=0.0):
         return self._ids(self.L.sp_admit, t)
@@ -83,8 +83,8 @@ class Policy:
     def next_check(self):
         return self.L.sp_steps_to_next_check(self.h)
 
-    def checked(self, rid, D, dp=1.0, count=10.0, status=0, t=0.0):
-        return self.L.sp_checked(self.h, rid, D, dp, count, status, t)
+    def checked(self, rid, D, components=1, count=10.0, status=0, t=0.0):
+        return self.L.sp_checked(self.h, rid, D, components, count, status, t)
 
     def failed(self, rid, t=0.0):
         self.L.sp_failed(self.h, rid, t)
@@ -183,23 +183,23 @@ def test_convergence_rule(sp):
 
 
 def test_breakup_unstable_and_cap(sp):
-    p = Policy(sp, budget=1000, check_every=100, max_steps=250, breakup_frac=0.25)
-    a = p.submit(1, 10, dp_ref=0.01)
-    b = p.submit(1, 10, dp_ref=0.01)
-    c = p.submit(1, 10, dp_ref=0.01)
-    d = p.submit(1, 10, dp_ref=0.01)
+    p = Policy(sp, budget=1000, check_every=100, max_steps=250)
+    a = p.submit(1, 10)
+    b = p.submit(1, 10)
+    c = p.submit(1, 10)
+    d = p.submit(1, 10)
     p.admit()
     p.advanced(100)
-    assert p.checked(a, 0.3, dp=0.0024) == BREAKUP  # below a quarter of the reference
-    assert p.checked(b, 0.3, dp=0.009, count=0.0) == BREAKUP  # no liquid left
-    assert p.checked(c, 0.3, dp=0.009, status=1) == UNSTABLE
-    assert p.checked(d, 0.3, dp=0.009) == RUNNING
+    assert p.checked(a, 0.3, components=2) == BREAKUP  # the drop split in two
+    assert p.checked(b, 0.3, count=0.0) == BREAKUP  # no liquid left
+    assert p.checked(c, 0.3, status=1) == UNSTABLE
+    assert p.checked(d, 0.3) == RUNNING
     p.advanced(100)
-    assert p.checked(d, 0.1, dp=0.009) == RUNNING
+    assert p.checked(d, 0.1) == RUNNING
     assert p.next_check() == 50  # the cap comes before the next check
     p.advanced(50)
     assert p.due() == [d]
-    assert p.checked(d, 0.3, dp=0.009) == MAX_STEPS
+    assert p.checked(d, 0.3) == MAX_STEPS
     assert [p.job(x)["outcome"] for x in (a, b, c, d)] == [BREAKUP, BREAKUP, UNSTABLE, MAX_STEPS]
     assert p.finished() == [a, b, c, d]
 
@@ -223,7 +223,7 @@ def test_fake_executor_with_injected_failures(sp):
     t, i = 0.0, 0
     while len(finished) < n_req:
         while i < n_req and arrivals[i] <= t:
-            ids.append(p.submit(int(sizes[i]), int(sizes[i]), 1.0, t))
+            ids.append(p.submit(int(sizes[i]), int(sizes[i]), t))
             i += 1
         for rid in p.admit(t):
             starts += 1
