@@ -178,6 +178,22 @@ fre_status fre_init_droplet(fre_ctx *c, double cx, double cy, double cz, double 
 fre_status fre_init_fields(fre_ctx *c, const double *rho, const double *ux,
                            const double *uy, const double *uz, const double *phi);
 
+/* Consistent initial populations (Sec. 2.3: the populations start at their
+ * equilibrium and their kinetic moments are aligned by collisions before the
+ * simulated time begins, after Mei et al., Computers & Fluids 2006).  From
+ * the current state, which must be freshly initialised or loaded (step 0):
+ * take u0 = sum c_i f_i / rho, phi0 = sum g_i, mu0 and the force F0 as they
+ * stand; then `iterations` times collide f with the velocity of f_eq and of
+ * the forcing term held at u0 and the force at F0 (the density rho = sum f_i
+ * is free) and stream it with the walls' rules; finally set g = g_eq(phi0,
+ * mu0, u0).  The pressure field, the Laplace pressure of a droplet among
+ * it, and the non-equilibrium parts of f then match the initial flow and
+ * interface, so the first steps carry no start-up pressure waves.  The step
+ * counter stays 0.  Runs on the per-node kernels (any storage format and
+ * device) and synchronises; FRE_ERR_STATE if the context has stepped since
+ * its initialisation. */
+fre_status fre_init_consistent(fre_ctx *c, int iterations);
+
 /* Replace the state by host FP64 pre-collision populations [q][n]; the step
  * counter restarts at 0.  16-bit formats round them to their storage. */
 fre_status fre_load_populations(fre_ctx *c, const double *f, const double *g);

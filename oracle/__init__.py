@@ -92,6 +92,8 @@ def lib():
             L.orc_feq.argtypes = [C.c_int, C.c_double, dp, dp]
             L.orc_geq.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, dp, dp]
             L.orc_guo.argtypes = [C.c_int, C.c_double, dp, dp, dp]
+            L.orc_init_consistent.restype = C.c_int
+            L.orc_init_consistent.argtypes = [C.c_void_p, C.c_int]
             L.orc_label_phase.restype = C.c_int
             L.orc_label_phase.argtypes = [C.c_void_p, dp, C.POINTER(C.c_int)]
             L.orc_num_threads.restype = C.c_int
@@ -180,6 +182,12 @@ class Oracle:
                 for a in (rho, ux, uy, uz, phi)]
         if lib().orc_init_fields(self._h, *[_ptr(a) for a in arrs]) != 0:
             raise ValueError("oracle: init_fields failed")
+
+    def init_consistent(self, iterations: int):
+        """Consistent initial populations from the current state (Sec. 2.3,
+        Mei et al.): f relaxed with u and F held, g at equilibrium."""
+        if lib().orc_init_consistent(self._h, int(iterations)) != 0:
+            raise ValueError("oracle: init_consistent failed")
 
     def load_populations(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)

@@ -70,6 +70,11 @@ int orc_fields(orc_state *s, double *rho, double *ux, double *uy, double *uz,
                double *phi, double *mu);
 int orc_observables(orc_state *s, orc_obs *out);
 
+/* Consistent initial populations (Sec. 2.3, Mei et al.): `iterations`
+ * collide-and-stream passes of f with the velocity and force of the current
+ * state held, rho free; g set to g_eq.  See fre_oracle.c. */
+int orc_init_consistent(orc_state *s, int iterations);
+
 /* Components of the phase phi > 0 (fluid nodes; phi given per node, n
  * values): labels[n] = -1 outside, else the smallest node index of the
  * component; returns the number of components.  See fre_oracle.c. */

@@ -28,7 +28,7 @@ LATTICES = {"d2q9": FRE_D2Q9, "d3q19": FRE_D3Q19}
 DEVICES = {"shear": FRE_SHEAR, "four_roller": FRE_FOUR_ROLLER, "periodic": FRE_PERIODIC}
 
 # every entry point declared in include/fre.h
-EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_fields",
+EXPORTS = ["fre_device_bytes", "fre_create", "fre_init_droplet", "fre_init_fields", "fre_init_consistent",
            "fre_load_populations", "fre_store_populations", "fre_step", "fre_step_timed",
            "fre_copy_fields", "fre_observables", "fre_step_count", "fre_uses_row_kernels",
            "fre_kernel_path", "fre_components", "fre_moments_noalloc",
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
         L.fre_create.argtypes = [C.POINTER(fre_params), vp, C.POINTER(vp)]
         L.fre_init_droplet.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double]
         L.fre_init_fields.argtypes = [vp, dp, dp, dp, dp, dp]
+        L.fre_init_consistent.argtypes = [vp, C.c_int]
         L.fre_load_populations.argtypes = [vp, dp, dp]
         L.fre_store_populations.argtypes = [vp, dp, dp]
         L.fre_step.argtypes = [vp, C.c_int]
@@ -177,7 +178,7 @@ def load_library(path: str = LIB_PATH):
         for name in ("fre_batch_create", "fre_batch_add", "fre_batch_remove", "fre_batch_step",
                      "fre_batch_observables", "fre_batch_tuning", "fre_batch_set_mode", "fre_batch_synchronize"):
             getattr(L, name).restype = C.c_int
-        for name in ("fre_create", "fre_init_droplet", "fre_init_fields", "fre_load_populations",
+        for name in ("fre_create", "fre_init_droplet", "fre_init_fields", "fre_init_consistent", "fre_load_populations",
                      "fre_store_populations", "fre_step", "fre_step_timed", "fre_copy_fields",
                      "fre_observables"):
             getattr(L, name).restype = C.c_int
@@ -240,6 +241,10 @@ def fre_init_fields(h, rho, ux, uy, uz, phi):
     arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
             for a in (rho, ux, uy, uz, phi)]
     _check(load_library().fre_init_fields(h, *[_dptr(a) for a in arrs]), "fre_init_fields")
+
+
+def fre_init_consistent(h, iterations: int):
+    _check(load_library().fre_init_consistent(h, int(iterations)), "fre_init_consistent")
 
 
 def fre_load_populations(h, f, g):
@@ -353,6 +358,9 @@ class Simulation:
 
     def init_fields(self, rho, ux, uy, uz, phi):
         fre_init_fields(self.h, rho, ux, uy, uz, phi)
+
+    def init_consistent(self, iterations: int):
+        fre_init_consistent(self.h, iterations)
 
     def load_populations(self, f, g):
         fre_load_populations(self.h, f, g)

@@ -41,6 +41,7 @@ struct Sizes {
     int q, sz_store, sz_comp;
     long long n, np;
     size_t buf_bytes, field_bytes, solid_bytes;
+    size_t cst_bytes;  // per-row constants of the 16-bit row update (upper bound)
 };
 
 bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
@@ -81,6 +82,8 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
     }
     s.field_bytes = (size_t)s.np * s.sz_comp;
     s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) : 0;
+    s.cst_bytes = (p->precision == FRE_FP16DEV || p->precision == FRE_BF16DEV)
+                      ? 8 * 2 * (size_t)p->ny * (6 + s.q - 1) : 0;
     return true;
 }
 
@@ -93,7 +96,7 @@ size_t ccl_bytes(const Sizes &s) { return 2 * sizeof(int) * (size_t)s.n + 16 * (
 
 size_t total_bytes(const Sizes &s) {
     return 2 * s.buf_bytes + 3 * s.field_bytes + s.solid_bytes + sizeof(double) * fre::kRedDoublesHost +
-           sizeof(fre_obs) + ccl_bytes(s);
+           sizeof(fre_obs) + ccl_bytes(s) + s.cst_bytes;
 }
 
 fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
@@ -193,6 +196,7 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.stream = c->stream;
     L.W = c->row_w;
     L.err = c->err_dev;
+    L.cst = c->cst;
     L.stall = (c->p.flags & FRE_FLAG_TEST_PIPELINE_STALL) ? 1 : 0;
     L.wait_ns = L.stall ? 5000000ull : 2000000000ull;
     return L;
@@ -224,6 +228,12 @@ void fre::ctx_launch_step(fre_ctx *c) {
     c->step++;
 }
 
+// The per-row constants of the 16-bit row update for the context's current
+// parameters (after creation and after every change of parameters).
+void fre::ctx_row_consts(fre_ctx *c) {
+    if (c->cst && c->ks->row_consts) c->ks->row_consts(ctx_launch(c), c->cst);
+}
+
 bool fre::same_geometry(const fre_params *p, const fre_params *q) {
     return p->lattice == q->lattice && p->precision == q->precision && p->device == q->device && p->nx == q->nx &&
            p->ny == q->ny && p->nz == q->nz && p->flags == q->flags;
@@ -239,6 +249,7 @@ fre_status fre::ctx_reparam(fre_ctx *c, const fre_params *p) {
     c->G.uwall = p->u_wall;
     c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0};
     c->initialised = false;
+    fre::ctx_row_consts(c);
     return FRE_OK;
 }
 
@@ -440,6 +451,13 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     }
     c->fullrow = c->rows && !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable &&
                  c->ks->fullrow_usable(c->G);
+    if (c->fullrow && c->ks->row_consts) {
+        void *t;
+        fre_status st = dev_alloc(c, &t, sizeof(float2) * 2 * (size_t)p->ny * (6 + s.q - 1));
+        if (st != FRE_OK) return bail(st);
+        c->cst = static_cast<float2 *>(t);
+        fre::ctx_row_consts(c);
+    }
     cudaGetLastError();
     *out = c;
     return FRE_OK;
@@ -485,6 +503,35 @@ fre_status fre_init_fields(fre_ctx *c, const double *rho, const double *ux, cons
     if (s != FRE_OK) return s;
     FRE_CUDA(cudaStreamSynchronize(c->stream));
     return FRE_OK;
+}
+
+fre_status fre_init_consistent(fre_ctx *c, int iterations) {
+    fre_status s = enter(c);
+    if (s != FRE_OK) return s;
+    if (iterations < 0) return fail(FRE_ERR_ARG, "fre_init_consistent: iterations < 0");
+    if (!c->initialised || !c->local || c->step != 0)
+        return fail(FRE_ERR_STATE, "fre_init_consistent: call it right after an initialisation or a load");
+    s = ensure_staging(c);
+    if (s != FRE_OK) return s;
+    fre::Launch L = launch_of(c);
+    current_phi_mu(c, L);  // phi0, mu0 (and roller ghosts) of the in-place state
+    c->ks->mei_prep(L);
+    bool pull = false;
+    for (int it = 0; it < iterations; ++it) {
+        L = launch_of(c);
+        c->ks->mei_iter(L, pull);
+        c->cur ^= 1;
+        pull = true;
+    }
+    L = launch_of(c);
+    c->ks->mei_final(L, pull);
+    c->cur ^= 1;
+    c->local = true;
+    c->step = 0;
+    s = check_launch("fre_init_consistent");
+    if (s != FRE_OK) return s;
+    FRE_CUDA(cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
 }
 
 fre_status fre_load_populations(fre_ctx *c, const double *f, const double *g) {

@@ -66,6 +66,7 @@ struct Launch {
     int *err;              // device error word (pipeline wait timed out)
     unsigned long long wait_ns;  // limit of every pipeline wait
     int stall;             // FRE_FLAG_TEST_PIPELINE_STALL: producers issue no copies
+    const float2 *cst;     // 16-bit row update: per-row constants [2][ny][6 + q - 1]
     double *staging;       // FP64 staging of host I/O (n doubles per field)
     cudaStream_t stream;
 };
@@ -85,6 +86,12 @@ struct KernelSet {
     void (*load_plane)(const Launch &, int lattice_g, int i);  // staging -> src
     void (*set_phi)(const Launch &, int analytic, double cx, double cy, double cz, double R);
     void (*init_eq)(const Launch &, int from_staging);  // f = f_eq, g = g_eq into src
+    // consistent initialisation: u0 and F0 of the in-place state into
+    // staging; one collide(u0, F0 held)-and-stream pass of f src -> dst; the
+    // pulled f and g = g_eq(phi, mu, u0) into dst as the pre-collision state
+    void (*mei_prep)(const Launch &);
+    void (*mei_iter)(const Launch &, bool pull);
+    void (*mei_final)(const Launch &, bool pull);
     // row kernels of the hot path (nullptr where the format has none)
     int (*row_width)(const Geo &, int pref);  // chunk width of the row kernels, 0 = n/a
     void (*phi_rows)(const Launch &, bool pull);
@@ -92,6 +99,9 @@ struct KernelSet {
     void (*update_rows)(const Launch &, bool pull);
     // full-row variant of the update (one bulk copy per population row)
     bool (*fullrow_usable)(const Geo &);
+    // the per-row constants of the 16-bit row update into tab (nullptr
+    // where the format has none)
+    void (*row_consts)(const Launch &, float2 *tab);
     void (*update_fullrow)(const Launch &, bool pull);
     void (*phi_fullrow)(const Launch &, bool pull);
     void (*mu_fullrow)(const Launch &);

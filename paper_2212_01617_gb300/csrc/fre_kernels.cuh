@@ -656,6 +656,130 @@ __global__ void __launch_bounds__(kBlock) k_init_eq(Launch L, int from_staging) 
     P::stg(L.src, L.G.np, 0, n, phi - gsum);
 }
 
+// ------------------------------------------------ consistent initialisation
+//
+// Consistent initial populations (Sec. 2.3: equilibrium populations whose
+// kinetic moments are aligned by collisions before the simulated time
+// starts, after Mei et al.): with the velocity u0 and the force F0 of the
+// initial state held fixed, f is collided (density free) and streamed
+// `iterations` times; g ends at g_eq(phi0, mu0, u0).  Staging fields 0..2
+// hold u0, 3..5 hold F0.
+
+// u0 = sum c_i f_i / rho and F0 (from the current phi and mu fields) of
+// the in-place state
+template <int Q, int FMT>
+__global__ void __launch_bounds__(kBlock) k_mei_prep(Launch L) {
+    using T = typename Fmt<FMT>::T;
+    FRE_SITE_OR_RETURN(L, s);
+    const long long N = L.G.n;
+    double *st = L.staging;
+    if (is_solid(L.G, s.n)) {
+        for (int k = 0; k < 6; ++k) st[k * N + s.n] = 0.0;
+        return;
+    }
+    T f[Q], g[Q];
+    gather<Q, FMT, false, true>(L, s, f, g);
+    const Macro<T> m = macro_of<Q, FMT>(L, s, f, g);
+    T jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        jx += T(Lat<Q>::cx(i)) * f[i];
+        jy += T(Lat<Q>::cy(i)) * f[i];
+        jz += T(Lat<Q>::cz(i)) * f[i];
+    }
+    st[0 * N + s.n] = jx / m.rho;
+    st[1 * N + s.n] = jy / m.rho;
+    st[2 * N + s.n] = jz / m.rho;
+    st[3 * N + s.n] = m.Fx;
+    st[4 * N + s.n] = m.Fy;
+    st[5 * N + s.n] = m.Fz;
+}
+
+// one pass: pull (or read in place) f, collide with u0 and F0 held, store
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_mei_iter(Launch L) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
+    FRE_SITE_OR_RETURN(L, s);
+    if (is_solid(L.G, s.n)) return;
+    const int n = s.n;
+    const long long N = L.G.n;
+    T f[Q], g[Q];
+    T wsum = T(0);
+    gather<Q, FMT, PULL, true>(L, s, f, g, &wsum);
+    T rho = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) rho += f[i];
+    const double *st = L.staging;
+    const T ux = T(st[n]), uy = T(st[N + n]), uz = T(st[2 * N + n]);
+    const T Fx = T(st[3 * N + n]), Fy = T(st[4 * N + n]), Fz = T(st[5 * N + n]);
+    const bool f32 = sizeof(T) == 4;
+    const T of = f32 ? T(L.F.omega_f) : T(1.0 / L.P.tau_f);
+    const T kf = f32 ? T(L.F.kf) : T(1.0 - 0.5 / L.P.tau_f);
+    const T rho0 = T(L.P.rho0);
+    const T U = Fmt<FMT>::DEV ? T(couette_u(L, s.y)) : T(0);
+    const T usq = ux * ux + uy * uy + uz * uz;
+    const T uF = ux * Fx + uy * Fy + uz * Fz;
+    T fsum = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const T cx = T(Lat<Q>::cx(i)), cy = T(Lat<Q>::cy(i)), cz = T(Lat<Q>::cz(i));
+        const T w = T(Lat<Q>::w(i));
+        const T cu = cx * ux + cy * uy + cz * uz;
+        const T cF = cx * Fx + cy * Fy + cz * Fz;
+        const T feq = w * rho * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+        const T S = kf * w * (T(3) * (cF - uF) + T(9) * cu * cF);
+        const T fs = f[i] - (f[i] - feq) * of + S;
+        if constexpr (Fmt<FMT>::DEV)
+            fsum += P::stw_back(L.dst, L.G.np, i, n, fs - w * rho0, rho0, U);
+        else
+            fsum += P::stf_back(L.dst, L.G.np, i, n, fs, rho0, U);
+    }
+    // the rest population closes the mass on the stored values
+    if constexpr (Fmt<FMT>::DEV)
+        P::stw_back(L.dst, L.G.np, 0, n, wsum - fsum, rho0, U);
+    else
+        P::stf(L.dst, L.G.np, 0, n, rho - fsum, rho0, U);
+}
+
+// the pre-collision state of step 0: the pulled f, and g = g_eq(phi0, mu0, u0)
+template <int Q, int FMT, bool PULL>
+__global__ void __launch_bounds__(kBlock) k_mei_final(Launch L) {
+    using T = typename Fmt<FMT>::T;
+    using P = Pop<Q, FMT>;
+    FRE_SITE_OR_RETURN(L, s);
+    const int n = s.n;
+    const long long N = L.G.n;
+    const T rho0 = T(L.P.rho0);
+    const T U = Fmt<FMT>::DEV ? T(couette_u(L, s.y)) : T(0);
+    if (is_solid(L.G, n)) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            P::stf(L.dst, L.G.np, i, n, T(0), rho0, U);
+            P::stg(L.dst, L.G.np, i, n, T(0));
+        }
+        return;
+    }
+    T f[Q], g[Q];
+    gather<Q, FMT, PULL, true>(L, s, f, g);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) P::stf(L.dst, L.G.np, i, n, f[i], rho0, U);
+    const double *st = L.staging;
+    const T ux = T(st[n]), uy = T(st[N + n]), uz = T(st[2 * N + n]);
+    const T phi = static_cast<const T *>(L.phi)[n];
+    const T mu = static_cast<const T *>(L.mu)[n];
+    const T usq = ux * ux + uy * uy + uz * uz;
+    const T gmu3 = T(3.0 * L.P.Gamma) * mu;
+    T gsum = T(0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const T cu = T(Lat<Q>::cx(i)) * ux + T(Lat<Q>::cy(i)) * uy + T(Lat<Q>::cz(i)) * uz;
+        const T ge = T(Lat<Q>::w(i)) * (gmu3 + phi * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq));
+        gsum += P::stg_back(L.dst, L.G.np, i, n, ge);
+    }
+    P::stg(L.dst, L.G.np, 0, n, phi - gsum);
+}
+
 // ------------------------------------------------------------ observables
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -903,6 +1027,15 @@ struct Launchers {
     }
     static void init_eq(const Launch &L, int from_staging) {
         k_init_eq<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L, from_staging);
+    }
+    static void mei_prep(const Launch &L) { k_mei_prep<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L); }
+    static void mei_iter(const Launch &L, bool pull) {
+        if (pull) k_mei_iter<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+        else k_mei_iter<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+    }
+    static void mei_final(const Launch &L, bool pull) {
+        if (pull) k_mei_final<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+        else k_mei_final<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
     }
 };
 

@@ -162,8 +162,9 @@ template <int Q, int FMT>
 const KernelSet *kernel_set() {
     using GL = Launchers<Q, FMT>;
     static const KernelSet ks = {GL::phi, GL::ghost, GL::mu, GL::update, GL::obs, GL::macro, GL::pull_plane,
-                                 GL::load_plane, GL::set_phi, GL::init_eq, nullptr, nullptr, nullptr, nullptr,
-                                 nullptr, nullptr, nullptr, nullptr};
+                                 GL::load_plane, GL::set_phi, GL::init_eq, GL::mei_prep, GL::mei_iter,
+                                 GL::mei_final, nullptr, nullptr, nullptr, nullptr,
+                                 nullptr, nullptr, nullptr, nullptr, nullptr};
     return &ks;
 }
 

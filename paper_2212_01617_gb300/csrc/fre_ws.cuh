@@ -627,6 +627,25 @@ __device__ __forceinline__ void couette_consts(const Launch &L, const CoLane &c,
     }
 }
 
+// Table of the per-row constants of the 16-bit update, [2][ny][6 + q - 1]
+// float2 (index 0: in-place update, 1: pulled), written once per context and
+// parameter set (they depend on y, the wall speed, omega_f and rho0 only):
+// one warp per (pull, y).
+template <int Q>
+__global__ void __launch_bounds__(32) k_row_consts(Launch L, float2 *tab) {
+    constexpr int NC = 6 + (Q - 1);
+    const int y = blockIdx.x, pull = blockIdx.y;
+    const CoLane col = co_lane<Q>(L, threadIdx.x);
+    float2 *out = tab + ((size_t)pull * L.G.ny + y) * NC;
+    if (pull) couette_consts<Q, true>(L, col, y, out, threadIdx.x);
+    else couette_consts<Q, false>(L, col, y, out, threadIdx.x);
+}
+
+template <int Q>
+void launch_row_consts(const Launch &L, float2 *tab) {
+    k_row_consts<Q><<<dim3((unsigned)L.G.ny, 2), 32, 0, L.stream>>>(L, tab);
+}
+
 // Rows of a work unit run side by side, one consumer group of nx/2 threads
 // each (the kernel's RPX): the update takes all R rows of a unit at once;
 // the phi and mu passes loop over them, except on rows whose half length is
@@ -659,13 +678,10 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NST], empty[NST];
     __shared__ unsigned wall_s[NST][R];
-    // per-row constants of the 16-bit update (couette_consts): a ring of
-    // NST + 1 slots, since a consumer warp still reads those of unit k after
-    // it has released the stage of unit k, until the producer may refill
-    // the stage with unit k + NST
+    // per-row constants of the 16-bit update (couette_consts), read from the
+    // context's table L.cst ([pull][y][NCST], computed once per parameter set)
     constexpr bool CST = DEV && KIND == WS_UPDATE;
     constexpr int NCST = CST ? 6 + (Q - 1) : 2;
-    __shared__ __align__(16) float2 cst_s[CST ? NST + 1 : 1][R][NCST];
     const int nx = NXC ? NXC : L.G.nx;
     const int ny = L.G.ny, nz = L.G.nz;
     const int nyu = ny / R;  // units per z plane
@@ -681,10 +697,6 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
     // self-fed mode: releases of each stage so far (a count that only rises;
     // the warp that brings it to a multiple of the consumer warps is last)
     __shared__ unsigned rel_s[SELF ? NST : 1];
-    // self-fed mode: the per-lane lookups of the refill (couette_consts),
-    // made once per block
-    __shared__ CoLane colane_s[SELF ? 32 : 1];
-    if (SELF && threadIdx.x < 32) colane_s[threadIdx.x] = co_lane<Q>(L, threadIdx.x);
     // a stage is released by each consumer warp on its own once it has read
     // it, so the consumer warps never wait for one another
     if (threadIdx.x == 0) {
@@ -699,7 +711,7 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
 
     // Stage the rows of the block's k-th unit `unit` into stage k % NST and
     // arrive on its `full` barrier (one whole warp; lane = its lane).
-    auto produce = [&](int unit, int k, int lane, const CoLane &col) {
+    auto produce = [&](int unit, int k, int lane) {
         const int s = k % NST;
         const int y0 = (unit % nyu) * R, z = unit / nyu;
         unsigned char *buf = sm + s * stage_bytes;
@@ -713,9 +725,7 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 wall_s[s][r] = (PULL && shear) ? ((y0 + r == 0 ? cy_mask<Q>(1) : 0u) |
                                                   (y0 + r == ny - 1 ? cy_mask<Q>(-1) : 0u))
                                                : 0u;
-            // the 16-bit update arrives once its row constants are in place
-            if (CST) mbar_expect_tx(bar, FL::tx_bytes(nx));
-            else mbar_expect(bar, FL::tx_bytes(nx));
+            mbar_expect(bar, FL::tx_bytes(nx));
         }
         __syncwarp();
         for (int gi = lane; gi < FL::ngroups(); gi += 32) {
@@ -780,12 +790,6 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 }
             }
         }
-        if constexpr (CST) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) couette_consts<Q, PULL>(L, col, y0 + r, cst_s[k % (NST + 1)][r], lane);
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar);
-        }
     };
 
     if (producer) {
@@ -793,7 +797,6 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
         // wait on `full` runs out and the block leaves with an error code
         if (L.stall) return;
         const int lane = threadIdx.x - ncons;
-        const CoLane col = co_lane<Q>(L, lane);
         int k = 0;
         for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
             const int s = k % NST;
@@ -806,7 +809,7 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                     break;  // the consumers then time out on `full` and leave
                 }
             }
-            produce(unit, k, lane, col);
+            produce(unit, k, lane);
         }
         return;
     }
@@ -814,10 +817,9 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
     // timeout test, whose waits then run out)
     if constexpr (SELF) {
         if (threadIdx.x < 32 && !L.stall) {
-            const CoLane col = colane_s[threadIdx.x];
             for (int k = 0; k < NST; ++k) {
                 const int unit = blockIdx.x + k * gridDim.x;
-                if (unit < nunits) produce(unit, k, threadIdx.x, col);
+                if (unit < nunits) produce(unit, k, threadIdx.x);
             }
         }
     }
@@ -840,7 +842,7 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 fence_async_smem();
                 const int kn = k + NST;
                 const int un = blockIdx.x + kn * (int)gridDim.x;
-                if (un < nunits) produce(un, kn, threadIdx.x & 31, colane_s[threadIdx.x & 31]);
+                if (un < nunits) produce(un, kn, threadIdx.x & 31);
             }
         } else {
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -1057,7 +1059,8 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 float2 sf = f[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
                 float2 ph = TWO ? p2(0.f) : g[0];
                 // 16-bit f: row constants (offsets o_i summed into the moments)
-                const float4 *cst = reinterpret_cast<const float4 *>(cst_s[CST ? k % (NST + 1) : 0][r]);
+                const float4 *cst =
+                    CST ? reinterpret_cast<const float4 *>(L.cst + ((size_t)(PULL ? 1 : 0) * ny + y) * NCST) : nullptr;
                 if constexpr (CST) {
                     const float4 c01 = cst[0], c23 = cst[1];
                     sf = add2(sf, make_float2(c01.x, c01.y));
@@ -1312,8 +1315,10 @@ const KernelSet *kernel_set_ws() {
     } else {
         using WL = WsLaunchers<Q, FMT>;
         static const KernelSet ks = {GL::phi, GL::ghost, GL::mu, GL::update, GL::obs, GL::macro, GL::pull_plane,
-                                     GL::load_plane, GL::set_phi, GL::init_eq, WsEntry<Q, FMT>::width, WL::phi,
+                                     GL::load_plane, GL::set_phi, GL::init_eq, GL::mei_prep, GL::mei_iter,
+                                     GL::mei_final, WsEntry<Q, FMT>::width, WL::phi,
                                      WL::mu, WL::update, WsRowLaunchers<Q, FMT>::usable,
+                                     Fmt<FMT>::DEV ? launch_row_consts<Q> : nullptr,
                                      WsRowLaunchers<Q, FMT>::update, WsRowLaunchers<Q, FMT>::phi,
                                      WsRowLaunchers<Q, FMT>::mu};
         return &ks;
