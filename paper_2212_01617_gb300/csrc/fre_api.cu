@@ -41,7 +41,6 @@ struct Sizes {
     int q, sz_store, sz_comp;
     long long n, np;
     size_t buf_bytes, field_bytes, solid_bytes;
-    size_t cst_bytes;  // per-row constants of the 16-bit row update (upper bound)
 };
 
 bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
@@ -82,8 +81,6 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
     }
     s.field_bytes = (size_t)s.np * s.sz_comp;
     s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) : 0;
-    s.cst_bytes = (p->precision == FRE_FP16DEV || p->precision == FRE_BF16DEV)
-                      ? 8 * 2 * (size_t)p->ny * (6 + s.q - 1) : 0;
     return true;
 }
 
@@ -96,7 +93,7 @@ size_t ccl_bytes(const Sizes &s) { return 2 * sizeof(int) * (size_t)s.n + 16 * (
 
 size_t total_bytes(const Sizes &s) {
     return 2 * s.buf_bytes + 3 * s.field_bytes + s.solid_bytes + sizeof(double) * fre::kRedDoublesHost +
-           sizeof(fre_obs) + ccl_bytes(s) + s.cst_bytes;
+           sizeof(fre_obs) + ccl_bytes(s);
 }
 
 fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
@@ -196,7 +193,6 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.stream = c->stream;
     L.W = c->row_w;
     L.err = c->err_dev;
-    L.cst = c->cst;
     L.stall = (c->p.flags & FRE_FLAG_TEST_PIPELINE_STALL) ? 1 : 0;
     L.wait_ns = L.stall ? 5000000ull : 2000000000ull;
     return L;
@@ -228,12 +224,6 @@ void fre::ctx_launch_step(fre_ctx *c) {
     c->step++;
 }
 
-// The per-row constants of the 16-bit row update for the context's current
-// parameters (after creation and after every change of parameters).
-void fre::ctx_row_consts(fre_ctx *c) {
-    if (c->cst && c->ks->row_consts) c->ks->row_consts(ctx_launch(c), c->cst);
-}
-
 bool fre::same_geometry(const fre_params *p, const fre_params *q) {
     return p->lattice == q->lattice && p->precision == q->precision && p->device == q->device && p->nx == q->nx &&
            p->ny == q->ny && p->nz == q->nz && p->flags == q->flags;
@@ -249,7 +239,6 @@ fre_status fre::ctx_reparam(fre_ctx *c, const fre_params *p) {
     c->G.uwall = p->u_wall;
     c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0};
     c->initialised = false;
-    fre::ctx_row_consts(c);
     return FRE_OK;
 }
 
@@ -451,13 +440,6 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     }
     c->fullrow = c->rows && !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable &&
                  c->ks->fullrow_usable(c->G);
-    if (c->fullrow && c->ks->row_consts) {
-        void *t;
-        fre_status st = dev_alloc(c, &t, sizeof(float2) * 2 * (size_t)p->ny * (6 + s.q - 1));
-        if (st != FRE_OK) return bail(st);
-        c->cst = static_cast<float2 *>(t);
-        fre::ctx_row_consts(c);
-    }
     cudaGetLastError();
     *out = c;
     return FRE_OK;

@@ -28,7 +28,6 @@ struct fre_ctx {
     int *err_dev = nullptr;  // set by a kernel whose bounded wait timed out
     double *staging = nullptr;
     fre::CclBuffers ccl{};  // component labelling, allocated on first use
-    float2 *cst = nullptr;  // 16-bit row update: per-row constants
     std::vector<void *> allocs;
     int cur = 0;        // buffer holding the state
     int pp = 1;         // phi buffer holding phi of the previous step
@@ -45,9 +44,6 @@ namespace fre {
 Launch ctx_launch(fre_ctx *c);
 // the kernels of one time step on the context stream; advances the state
 void ctx_launch_step(fre_ctx *c);
-// recompute the per-row constants of the 16-bit row update (queued on the
-// context stream)
-void ctx_row_consts(fre_ctx *c);
 // give a context new physical parameters of the same geometry (lattice,
 // precision, device, sizes and flags equal); the state must be
 // re-initialised before the next step

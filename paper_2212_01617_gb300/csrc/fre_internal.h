@@ -66,7 +66,6 @@ struct Launch {
     int *err;              // device error word (pipeline wait timed out)
     unsigned long long wait_ns;  // limit of every pipeline wait
     int stall;             // FRE_FLAG_TEST_PIPELINE_STALL: producers issue no copies
-    const float2 *cst;     // 16-bit row update: per-row constants [2][ny][6 + q - 1]
     double *staging;       // FP64 staging of host I/O (n doubles per field)
     cudaStream_t stream;
 };
@@ -99,9 +98,6 @@ struct KernelSet {
     void (*update_rows)(const Launch &, bool pull);
     // full-row variant of the update (one bulk copy per population row)
     bool (*fullrow_usable)(const Geo &);
-    // the per-row constants of the 16-bit row update into tab (nullptr
-    // where the format has none)
-    void (*row_consts)(const Launch &, float2 *tab);
     void (*update_fullrow)(const Launch &, bool pull);
     void (*phi_fullrow)(const Launch &, bool pull);
     void (*mu_fullrow)(const Launch &);

@@ -164,7 +164,7 @@ const KernelSet *kernel_set() {
     static const KernelSet ks = {GL::phi, GL::ghost, GL::mu, GL::update, GL::obs, GL::macro, GL::pull_plane,
                                  GL::load_plane, GL::set_phi, GL::init_eq, GL::mei_prep, GL::mei_iter,
                                  GL::mei_final, nullptr, nullptr, nullptr, nullptr,
-                                 nullptr, nullptr, nullptr, nullptr, nullptr};
+                                 nullptr, nullptr, nullptr, nullptr};
     return &ks;
 }
 

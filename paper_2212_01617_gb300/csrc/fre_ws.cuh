@@ -627,25 +627,6 @@ __device__ __forceinline__ void couette_consts(const Launch &L, const CoLane &c,
     }
 }
 
-// Table of the per-row constants of the 16-bit update, [2][ny][6 + q - 1]
-// float2 (index 0: in-place update, 1: pulled), written once per context and
-// parameter set (they depend on y, the wall speed, omega_f and rho0 only):
-// one warp per (pull, y).
-template <int Q>
-__global__ void __launch_bounds__(32) k_row_consts(Launch L, float2 *tab) {
-    constexpr int NC = 6 + (Q - 1);
-    const int y = blockIdx.x, pull = blockIdx.y;
-    const CoLane col = co_lane<Q>(L, threadIdx.x);
-    float2 *out = tab + ((size_t)pull * L.G.ny + y) * NC;
-    if (pull) couette_consts<Q, true>(L, col, y, out, threadIdx.x);
-    else couette_consts<Q, false>(L, col, y, out, threadIdx.x);
-}
-
-template <int Q>
-void launch_row_consts(const Launch &L, float2 *tab) {
-    k_row_consts<Q><<<dim3((unsigned)L.G.ny, 2), 32, 0, L.stream>>>(L, tab);
-}
-
 // Rows of a work unit run side by side, one consumer group of nx/2 threads
 // each (the kernel's RPX): the update takes all R rows of a unit at once;
 // the phi and mu passes loop over them, except on rows whose half length is
@@ -659,29 +640,21 @@ struct RowsPar {
 
 // NXC: the row length as a compile-time constant (every shared-memory
 // offset then folds into the instruction), or 0 to take it from the launch.
-// Self-fed mode (the update with rows side by side, RPX > 1): no producer
-// warp; the consumer warp that releases a stage last refills it with the
-// block's unit NST ahead.  A block of 16 consumer warps then keeps 4 warps
-// per SM sub-partition and 128 registers a thread, where a 17th (producer)
-// warp would cap every thread at 96 registers and spill.
-template <int KIND, int RPX>
-struct WsSelfFed {
-    static constexpr bool value = KIND == WS_UPDATE && RPX > 1;
-};
-
 template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC, int RPX>
-__global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 : 32), KIND == WS_UPDATE ? 1 : 2)
-    k_wsrow(Launch L, int nunits) {
+__global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
     using FL = RowsLayout<Q, FMT, KIND, R>;
     constexpr bool DEV = Fmt<FMT>::DEV;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NST], empty[NST];
     __shared__ unsigned wall_s[NST][R];
-    // per-row constants of the 16-bit update (couette_consts), read from the
-    // context's table L.cst ([pull][y][NCST], computed once per parameter set)
+    // per-row constants of the 16-bit update (couette_consts): a ring of
+    // NST + 1 slots, since a consumer warp still reads those of unit k after
+    // it has released the stage of unit k, until the producer may refill
+    // the stage with unit k + NST
     constexpr bool CST = DEV && KIND == WS_UPDATE;
     constexpr int NCST = CST ? 6 + (Q - 1) : 2;
+    __shared__ __align__(16) float2 cst_s[CST ? NST + 1 : 1][R][NCST];
     const int nx = NXC ? NXC : L.G.nx;
     const int ny = L.G.ny, nz = L.G.nz;
     const int nyu = ny / R;  // units per z plane
@@ -690,113 +663,26 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
     constexpr int RP = RPX;
     static_assert(R % RP == 0, "rows side by side must divide the rows of a unit");
     const int ncons = RP * (nx / 2);
-    constexpr bool SELF = WsSelfFed<KIND, RPX>::value;
-    const bool producer = !SELF && threadIdx.x >= ncons;
+    const bool producer = threadIdx.x >= ncons;
     const unsigned stage_bytes = FL::stage(nx);
     const bool shear = L.G.device == FRE_SHEAR;
-    // self-fed mode: releases of each stage so far (a count that only rises;
-    // the warp that brings it to a multiple of the consumer warps is last)
-    __shared__ unsigned rel_s[SELF ? NST : 1];
     // a stage is released by each consumer warp on its own once it has read
     // it, so the consumer warps never wait for one another
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init_count(smem_addr(&full[s]), 1);
             mbar_init_count(smem_addr(&empty[s]), (unsigned)(ncons / 32));
-            if (SELF) rel_s[s] = 0u;
         }
         fence_async_smem();
     }
     __syncthreads();
-
-    // Stage the rows of the block's k-th unit `unit` into stage k % NST and
-    // arrive on its `full` barrier (one whole warp; lane = its lane).
-    auto produce = [&](int unit, int k, int lane) {
-        const int s = k % NST;
-        const int y0 = (unit % nyu) * R, z = unit / nyu;
-        unsigned char *buf = sm + s * stage_bytes;
-        const unsigned bar = smem_addr(&full[s]);
-        // wall links of each row of the unit (bit i: population i pulls
-        // from beyond a shear wall: c_y > 0 on row 0, c_y < 0 on row ny - 1),
-        // published before the arrival that completes with the copies
-        if (lane == 0) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                wall_s[s][r] = (PULL && shear) ? ((y0 + r == 0 ? cy_mask<Q>(1) : 0u) |
-                                                  (y0 + r == ny - 1 ? cy_mask<Q>(-1) : 0u))
-                                               : 0u;
-            mbar_expect(bar, FL::tx_bytes(nx));
-        }
-        __syncwarp();
-        for (int gi = lane; gi < FL::ngroups(); gi += 32) {
-            if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q)) {
-                // ---- phi / mu stencil rows of one z plane
-                const int j = KIND == WS_MU ? gi : gi - 2 * Q;
-                const int fld = KIND == WS_MU ? 0 : j / (FL::NGRP > 0 ? FL::NGRP : 1);
-                const int grp = KIND == WS_MU ? j : j - fld * FL::NGRP;
-                // mu pass groups: cz = -1, 0, +1 (3D); update: cz = 0, +1, -1
-                const int cz = KIND == WS_MU ? (Lat<Q>::D == 3 ? grp - 1 : 0) : (grp == 0 ? 0 : (grp == 1 ? 1 : -1));
-                const bool full_y = KIND == WS_MU || cz == 0;  // R + 2 rows with y shifts
-                const int zn = wrapi(z + cz, nz);
-                const float *base = static_cast<const float *>(fld ? L.mu : L.phi) + (size_t)zn * ny * nx;
-                const int k0 = FL::fk(full_y ? -1 : 0, cz, 0);
-                unsigned char *dst = buf + FL::fld_row(nx, fld, k0);
-                if (!full_y) {
-                    bulk_load(dst, base + (size_t)y0 * nx, (unsigned)R * FL::fldb(nx), bar);
-                } else if (y0 >= 1 && y0 + R <= ny - 1) {
-                    bulk_load(dst, base + (size_t)(y0 - 1) * nx, (unsigned)(R + 2) * FL::fldb(nx), bar);
-                } else {
-                    for (int q = 0; q < R + 2; ++q) {
-                        int yn = y0 - 1 + q;
-                        yn = shear ? (yn < 0 ? 0 : (yn >= ny ? ny - 1 : yn)) : wrapi(yn, ny);
-                        bulk_load(dst + q * FL::fldb(nx), base + (size_t)yn * nx, FL::fldb(nx), bar);
-                    }
-                }
-                continue;
-            }
-            // ---- population rows: lattice lat (0 f, 1 g), direction i
-            const int lat = KIND == WS_PHI ? 1 : (gi >= Q);
-            const int i = KIND == WS_PHI ? gi : gi - lat * Q;
-            const int cy = PULL ? Lat<Q>::cy(i) : 0, cz = PULL ? Lat<Q>::cz(i) : 0;
-            const int zs = wrapi(z - cz, nz);
-            // source plane of population p, its element size, smem row r
-            auto plane = [&](int p) -> const char * {
-                if (!lat) return static_cast<const char *>(L.src.f) + (size_t)p * L.G.np * sizeof(S);
-                if (DEV && p == 0) return reinterpret_cast<const char *>(L.src.g0);
-                return static_cast<const char *>(L.src.g) + (size_t)(DEV ? p - 1 : p) * L.G.np * sizeof(S);
-            };
-            const unsigned esz = (lat && DEV && i == 0) ? 4u : (unsigned)sizeof(S);
-            const unsigned rb = (unsigned)nx * esz;
-            auto smrow = [&](int r) -> unsigned { return lat ? FL::g_row(nx, i, r) : FL::f_row(nx, i, r); };
-            const int ys0 = y0 - cy;
-            const bool inside = ys0 >= 0 && ys0 + R - 1 <= ny - 1;
-            if (inside) {
-                bulk_load(buf + smrow(0), plane(i) + ((size_t)zs * ny + ys0) * nx * esz, (unsigned)R * rb, bar);
-            } else {
-                for (int r = 0; r < R; ++r) {
-                    int ys = y0 + r - cy;
-                    int pi = i, zr = zs;
-                    if (ys < 0 || ys >= ny) {
-                        if (shear) {
-                            // wall link: the local row of the opposite population
-                            ys = y0 + r;
-                            zr = z;
-                            pi = Lat<Q>::opp(i);
-                        } else {
-                            ys = wrapi(ys, ny);
-                        }
-                    }
-                    bulk_load(buf + smrow(r), plane(pi) + ((size_t)zr * ny + ys) * nx * esz, rb, bar);
-                }
-            }
-        }
-    };
 
     if (producer) {
         // test of the timeout path: no copies are issued, so every consumer
         // wait on `full` runs out and the block leaves with an error code
         if (L.stall) return;
         const int lane = threadIdx.x - ncons;
+        const CoLane col = co_lane<Q>(L, lane);
         int k = 0;
         for (int unit = blockIdx.x; unit < nunits; unit += gridDim.x, ++k) {
             const int s = k % NST;
@@ -809,45 +695,94 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                     break;  // the consumers then time out on `full` and leave
                 }
             }
-            produce(unit, k, lane);
+            const int y0 = (unit % nyu) * R, z = unit / nyu;
+            unsigned char *buf = sm + s * stage_bytes;
+            const unsigned bar = smem_addr(&full[s]);
+            // wall links of each row of the unit (bit i: population i pulls
+            // from beyond a shear wall: c_y > 0 on row 0, c_y < 0 on row ny - 1),
+            // published before the arrival that completes with the copies
+            if (lane == 0) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    wall_s[s][r] = (PULL && shear) ? ((y0 + r == 0 ? cy_mask<Q>(1) : 0u) |
+                                                      (y0 + r == ny - 1 ? cy_mask<Q>(-1) : 0u))
+                                                   : 0u;
+                // the 16-bit update arrives once its row constants are in place
+                if (CST) mbar_expect_tx(bar, FL::tx_bytes(nx));
+                else mbar_expect(bar, FL::tx_bytes(nx));
+            }
+            __syncwarp();
+            for (int gi = lane; gi < FL::ngroups(); gi += 32) {
+                if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q)) {
+                    // ---- phi / mu stencil rows of one z plane
+                    const int j = KIND == WS_MU ? gi : gi - 2 * Q;
+                    const int fld = KIND == WS_MU ? 0 : j / (FL::NGRP > 0 ? FL::NGRP : 1);
+                    const int grp = KIND == WS_MU ? j : j - fld * FL::NGRP;
+                    // mu pass groups: cz = -1, 0, +1 (3D); update: cz = 0, +1, -1
+                    const int cz = KIND == WS_MU ? (Lat<Q>::D == 3 ? grp - 1 : 0) : (grp == 0 ? 0 : (grp == 1 ? 1 : -1));
+                    const bool full_y = KIND == WS_MU || cz == 0;  // R + 2 rows with y shifts
+                    const int zn = wrapi(z + cz, nz);
+                    const float *base = static_cast<const float *>(fld ? L.mu : L.phi) + (size_t)zn * ny * nx;
+                    const int k0 = FL::fk(full_y ? -1 : 0, cz, 0);
+                    unsigned char *dst = buf + FL::fld_row(nx, fld, k0);
+                    if (!full_y) {
+                        bulk_load(dst, base + (size_t)y0 * nx, (unsigned)R * FL::fldb(nx), bar);
+                    } else if (y0 >= 1 && y0 + R <= ny - 1) {
+                        bulk_load(dst, base + (size_t)(y0 - 1) * nx, (unsigned)(R + 2) * FL::fldb(nx), bar);
+                    } else {
+                        for (int q = 0; q < R + 2; ++q) {
+                            int yn = y0 - 1 + q;
+                            yn = shear ? (yn < 0 ? 0 : (yn >= ny ? ny - 1 : yn)) : wrapi(yn, ny);
+                            bulk_load(dst + q * FL::fldb(nx), base + (size_t)yn * nx, FL::fldb(nx), bar);
+                        }
+                    }
+                    continue;
+                }
+                // ---- population rows: lattice lat (0 f, 1 g), direction i
+                const int lat = KIND == WS_PHI ? 1 : (gi >= Q);
+                const int i = KIND == WS_PHI ? gi : gi - lat * Q;
+                const int cy = PULL ? Lat<Q>::cy(i) : 0, cz = PULL ? Lat<Q>::cz(i) : 0;
+                const int zs = wrapi(z - cz, nz);
+                // source plane of population p, its element size, smem row r
+                auto plane = [&](int p) -> const char * {
+                    if (!lat) return static_cast<const char *>(L.src.f) + (size_t)p * L.G.np * sizeof(S);
+                    if (DEV && p == 0) return reinterpret_cast<const char *>(L.src.g0);
+                    return static_cast<const char *>(L.src.g) + (size_t)(DEV ? p - 1 : p) * L.G.np * sizeof(S);
+                };
+                const unsigned esz = (lat && DEV && i == 0) ? 4u : (unsigned)sizeof(S);
+                const unsigned rb = (unsigned)nx * esz;
+                auto smrow = [&](int r) -> unsigned { return lat ? FL::g_row(nx, i, r) : FL::f_row(nx, i, r); };
+                const int ys0 = y0 - cy;
+                const bool inside = ys0 >= 0 && ys0 + R - 1 <= ny - 1;
+                if (inside) {
+                    bulk_load(buf + smrow(0), plane(i) + ((size_t)zs * ny + ys0) * nx * esz, (unsigned)R * rb, bar);
+                } else {
+                    for (int r = 0; r < R; ++r) {
+                        int ys = y0 + r - cy;
+                        int pi = i, zr = zs;
+                        if (ys < 0 || ys >= ny) {
+                            if (shear) {
+                                // wall link: the local row of the opposite population
+                                ys = y0 + r;
+                                zr = z;
+                                pi = Lat<Q>::opp(i);
+                            } else {
+                                ys = wrapi(ys, ny);
+                            }
+                        }
+                        bulk_load(buf + smrow(r), plane(pi) + ((size_t)zr * ny + ys) * nx * esz, rb, bar);
+                    }
+                }
+            }
+            if constexpr (CST) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) couette_consts<Q, PULL>(L, col, y0 + r, cst_s[k % (NST + 1)][r], lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar);
+            }
         }
         return;
     }
-    // self-fed mode: warp 0 stages the first NST units (none under the
-    // timeout test, whose waits then run out)
-    if constexpr (SELF) {
-        if (threadIdx.x < 32 && !L.stall) {
-            for (int k = 0; k < NST; ++k) {
-                const int unit = blockIdx.x + k * gridDim.x;
-                if (unit < nunits) produce(unit, k, threadIdx.x);
-            }
-        }
-    }
-    // release of stage s (unit k) by this warp; in self-fed mode the last of
-    // the consumer warps to release it refills it with the unit NST ahead
-    auto release = [&](int s, int k) {
-        __syncwarp();
-        if constexpr (SELF) {
-            const unsigned nw = (unsigned)(ncons / 32);
-            unsigned last = 0;
-            if ((threadIdx.x & 31) == 0) {
-                __threadfence_block();
-                last = (atomicAdd(&rel_s[s], 1u) + 1u) % nw == 0u ? 1u : 0u;
-            }
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (last && !L.stall) {
-                // every warp has read the stage: order those reads before
-                // the copies that overwrite it
-                __threadfence_block();
-                fence_async_smem();
-                const int kn = k + NST;
-                const int un = blockIdx.x + kn * (int)gridDim.x;
-                if (un < nunits) produce(un, kn, threadIdx.x & 31);
-            }
-        } else {
-            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-        }
-    };
 
     // ------------------------------------------------------------ consumers
     const float rho0 = L.F.rho0;
@@ -899,7 +834,8 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 };
                 out[q] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
             }
-            release(s, k);
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
             for (int q = 0; q < RT; ++q)
                 st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
@@ -924,7 +860,8 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 out[q] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
                               mul2(p2(L.F.kappa), lap));
             }
-            release(s, k);
+            __syncwarp();
+            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
 #pragma unroll
             for (int q = 0; q < RT; ++q)
                 st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
@@ -1028,13 +965,6 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                             const float *mr = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 1, FL::fk(cyk, czk, r)));
                             pv[h] = ld_shift(pr, x0, -Lat<Q>::cx(kk), nx);
                             mv[h] = ld_shift(mr, x0, -Lat<Q>::cx(kk), nx);
-                        } else if (R > 1 && r + cyk >= 0 && r + cyk < R) {
-                            // off-axis row (y + c_y, z + c_z) that is another row
-                            // of this unit: staged with the c_z group (c_x = 0)
-                            const float *pr = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(0, czk, r + cyk)));
-                            const float *mr = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 1, FL::fk(0, czk, r + cyk)));
-                            pv[h] = ld_pair(pr, x0);
-                            mv[h] = ld_pair(mr, x0);
                         } else {
                             // off-axis rows (c_x = 0): an aligned pair in global memory
                             const int kn = site_nb<Q>(st, kk);
@@ -1052,15 +982,15 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                 const float2 mu = ld_pair(reinterpret_cast<const float *>(cur + FL::fld_row(nx, 1, FL::fk(0, 0, r))), x0);
                 if (!TWO && r + RP >= R) {
                     // this warp is done with the stage
-                    release(s, k);
+                    __syncwarp();
+                    if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
                 }
 
                 // ---- moments, force, velocity (Eq. densMoment, ordeMoment, F, veloMoment)
                 float2 sf = f[0], jx = p2(0.f), jy = p2(0.f), jz = p2(0.f);
                 float2 ph = TWO ? p2(0.f) : g[0];
                 // 16-bit f: row constants (offsets o_i summed into the moments)
-                const float4 *cst =
-                    CST ? reinterpret_cast<const float4 *>(L.cst + ((size_t)(PULL ? 1 : 0) * ny + y) * NCST) : nullptr;
+                const float4 *cst = reinterpret_cast<const float4 *>(cst_s[CST ? k % (NST + 1) : 0][r]);
                 if constexpr (CST) {
                     const float4 c01 = cst[0], c23 = cst[1];
                     sf = add2(sf, make_float2(c01.x, c01.y));
@@ -1169,7 +1099,8 @@ __global__ void __launch_bounds__(RPX * 256 + (WsSelfFed<KIND, RPX>::value ? 0 :
                     else pull_g(std::false_type{});
                     if (r + RP >= R) {
                         // this warp is done with the stage
-                        release(s, k);
+                        __syncwarp();
+                        if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
                     }
                     // ---- phi (Eq. ordeMoment) and the collision of g
                     ph = g[0];
@@ -1238,7 +1169,7 @@ struct WsRowLaunchers {
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX>;
         LaunchShape::opt_in((const void *)fn, smem);
-        const int threads = RPX * (nx / 2) + (WsSelfFed<KIND, RPX>::value ? 0 : 32);
+        const int threads = RPX * (nx / 2) + 32;
         const int g = std::min(nu, LaunchShape::sms() *
                                        LaunchShape::blocks_per_sm((const void *)fn, threads, smem));
         fn<<<g, threads, smem, L.stream>>>(L, nu);
@@ -1250,8 +1181,7 @@ struct WsRowLaunchers {
         const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX>;
         LaunchShape::opt_in((const void *)fn, smem);
-        return LaunchShape::blocks_per_sm((const void *)fn, RPX * (nx / 2) + (WsSelfFed<KIND, RPX>::value ? 0 : 32),
-                                          smem);
+        return LaunchShape::blocks_per_sm((const void *)fn, RPX * (nx / 2) + 32, smem);
     }
     // a third stage deepens the copy pipeline, but on short rows (few
     // consumer warps per block) it can cost a resident block: keep it only
@@ -1318,7 +1248,6 @@ const KernelSet *kernel_set_ws() {
                                      GL::load_plane, GL::set_phi, GL::init_eq, GL::mei_prep, GL::mei_iter,
                                      GL::mei_final, WsEntry<Q, FMT>::width, WL::phi,
                                      WL::mu, WL::update, WsRowLaunchers<Q, FMT>::usable,
-                                     Fmt<FMT>::DEV ? launch_row_consts<Q> : nullptr,
                                      WsRowLaunchers<Q, FMT>::update, WsRowLaunchers<Q, FMT>::phi,
                                      WsRowLaunchers<Q, FMT>::mu};
         return &ks;

@@ -1,7 +1,10 @@
 """The consistent initialisation on the GPU (fre_init_consistent: Sec. 2.3,
 populations aligned by collisions before the simulated time starts) against
-the oracle's: FP64 relative L-inf < 1e-12 on rho, u, phi right after the
-passes and 200 steps later; FP32 < 1e-5; on both lattices and every device."""
+the oracle's, right after the passes and 200 steps later, on both lattices
+and every device: FP64 relative L-inf < 1e-12 on rho, u, phi; FP32 1e-5 on
+rho and phi and 1e-4 on u against max(|u|, 0.01), i.e. 1e-6 absolute (the
+FP32 bounds of the row and per-node kernels; a droplet at rest has only
+spurious currents of ~1e-4, against which FP32 rounding is not small)."""
 import numpy as np
 import pytest
 
@@ -29,8 +32,8 @@ def fre():
     return fre
 
 
-def errs(a, b):
-    uscale = max(max(np.abs(b[k]).max() for k in ("ux", "uy", "uz")), 1e-300)
+def errs(a, b, u_floor=1e-300):
+    uscale = max(max(np.abs(b[k]).max() for k in ("ux", "uy", "uz")), u_floor)
     return {k: np.abs(a[k] - b[k]).max() / (uscale if k.startswith("u") else np.abs(b[k]).max())
             for k in ("rho", "ux", "uy", "uz", "phi")}
 
@@ -47,12 +50,15 @@ def test_consistent_init_matches_oracle(fre, orc, case, precision, tol):
         s.init_droplet(*drop)
         s.init_consistent(60)
     assert sim.steps_taken == 0
-    e0 = errs(sim.fields(), o.fields())
+    floor = 0.0 if precision == "fp64" else 0.01
+    utol = tol if precision == "fp64" else 1e-4
+    e0 = errs(sim.fields(), o.fields(), floor)
     for s in (sim, o):
         s.step(200)
-    e1 = errs(sim.fields(), o.fields())
+    e1 = errs(sim.fields(), o.fields(), floor)
     sim.close()
-    assert max(e0.values()) < tol and max(e1.values()) < tol, (e0, e1)
+    for e in (e0, e1):
+        assert all(v < (utol if k.startswith("u") else tol) for k, v in e.items()), (e0, e1)
 
 
 def test_consistent_init_16bit_and_state_rule(fre, orc):
