@@ -246,8 +246,10 @@ int fre_uses_row_kernels(const fre_ctx *c);
 
 /* Kernels of the time step: 0 per-node kernels (any geometry and format),
  * 1 warp-specialised kernels on x-chunks, 2 warp-specialised kernels on
- * whole x-rows (shear/periodic devices, FP32 and 16-bit storage, nx up to
- * 512 and a multiple of 64, or of 32 with ny even); -1 for a NULL context. */
+ * whole x-rows (FP32 and 16-bit storage, nx up to 512 and a multiple of 64,
+ * or of 32 with ny even; the four-roller device stages the wall links of
+ * its rollers with the rows and takes its first, in-place step on the
+ * per-node kernels); -1 for a NULL context. */
 int fre_kernel_path(const fre_ctx *c);
 
 /* Conservation sums and droplet moments without any device allocation.

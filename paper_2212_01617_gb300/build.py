@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libfre.so")
 BUILD = os.path.join(PKG, "_build")
 
 SOURCES = ["fre_api.cu", "fre_batch.cu", "fre_ccl.cu", "fre_d2q9.cu", "fre_d3q19.cu", "fre_noalloc.cu",
-           "fre_serve.cu"]
+           "fre_rows_roller.cu", "fre_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

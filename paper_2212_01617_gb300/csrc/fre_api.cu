@@ -80,7 +80,7 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
         s.buf_bytes = (size_t)s.q * plane + (size_t)(s.q - 1) * plane + (size_t)s.np * 4;
     }
     s.field_bytes = (size_t)s.np * s.sz_comp;
-    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) : 0;
+    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) + 4 * (size_t)p->nx * p->ny : 0;
     return true;
 }
 
@@ -111,9 +111,13 @@ fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
     return FRE_OK;
 }
 
-// Four-roller geometry: roller id of every node and the solid nodes that
-// have a fluid stencil neighbour.
-void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<int> &ghost) {
+// Four-roller geometry: roller id of every node, the solid nodes that have
+// a fluid stencil neighbour, and the wall-link word of every (x, y) for the
+// row kernels (bit i: the source (x, y) - c_i lies in a roller; bits 24..26
+// that roller; bit 30: the node itself is a roller node).  The rollers are
+// extruded along z, so one plane of words serves every z.
+void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<int> &ghost,
+                   std::vector<unsigned> &links) {
     const fre_params &p = c->p;
     fre::Geo &G = c->G;
     const double cx = 0.5 * (p.nx - 1), cy = 0.5 * (p.ny - 1);
@@ -147,6 +151,21 @@ void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<in
                                    {-1, 0, -1}, {0, 1, 1},  {0, -1, -1}, {1, -1, 0}, {-1, 1, 0},
                                    {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1}};
     auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
+    links.assign((size_t)p.nx * p.ny, 0u);
+    for (int y = 0; y < p.ny; ++y)
+        for (int x = 0; x < p.nx; ++x) {
+            unsigned w = 0;
+            if (solid[(size_t)y * p.nx + x]) {
+                w = 1u << 30;
+            } else {
+                for (int i = 1; i < q; ++i) {
+                    const int *ci = q == 9 ? c9[i] : c19[i];
+                    const int k = solid[(size_t)wrap(y - ci[1], p.ny) * p.nx + wrap(x - ci[0], p.nx)];
+                    if (k) w |= (1u << i) | ((unsigned)k << 24);
+                }
+            }
+            links[(size_t)y * p.nx + x] = w;
+        }
     ghost.clear();
     for (int z = 0; z < p.nz; ++z)
         for (int y = 0; y < p.ny; ++y)
@@ -178,7 +197,13 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
                        (c->p.precision == FRE_FP16DEV || c->p.precision == FRE_BF16DEV);
     L.F = {float(1.0 / tf), float(1.0 / tg), float(1.0 - 0.5 / tf), float(3.0 * c->P.Gamma),
            float(c->P.A), float(c->P.kappa), float(c->P.rho0), float(c->G.uwall),
-           shear ? float(c->G.uwall * (1.0 / c->G.ny - 1.0)) : 0.f, shear ? float(2.0 * c->G.uwall / c->G.ny) : 0.f};
+           shear ? float(c->G.uwall * (1.0 / c->G.ny - 1.0)) : 0.f, shear ? float(2.0 * c->G.uwall / c->G.ny) : 0.f,
+           {}, {}, {}};
+    for (int k = 0; k < 5; ++k) {
+        L.F.rcx[k] = float(c->G.rcx[k]);
+        L.F.rcy[k] = float(c->G.rcy[k]);
+        L.F.rom[k] = float(c->G.om[k]);
+    }
     L.src = c->buf[c->cur];
     L.dst = c->buf[1 - c->cur];
     L.phi_prev = c->phi[c->pp];
@@ -203,9 +228,14 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
 void fre::ctx_launch_step(fre_ctx *c) {
     fre::Launch L = ctx_launch(c);
     const bool pull = !c->local;
-    if (c->fullrow) {
+    // the four-roller device takes its in-place first step on the per-node
+    // kernels (its row kernels stage wall links for pulled steps)
+    const bool roll = c->G.device == FRE_FOUR_ROLLER;
+    if (c->fullrow && (pull || !roll)) {
         c->ks->phi_fullrow(L, pull);
+        if (c->n_ghost) c->ks->ghost(L, L.phi);
         c->ks->mu_fullrow(L);
+        if (c->n_ghost) c->ks->ghost(L, L.mu);
         c->ks->update_fullrow(L, pull);
     } else if (c->rows) {
         c->ks->phi_rows(L, pull);
@@ -412,7 +442,8 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     if (p->device == FRE_FOUR_ROLLER) {
         std::vector<unsigned char> solid;
         std::vector<int> ghost;
-        build_rollers(c, solid, ghost);
+        std::vector<unsigned> links;
+        build_rollers(c, solid, ghost, links);
         void *d;
         fre_status st = dev_alloc(c, &d, s.solid_bytes);
         if (st != FRE_OK) return bail(st);
@@ -429,17 +460,25 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
                                 c->stream) != cudaSuccess)
                 return bail(fail(FRE_ERR_CUDA, "upload of the ghost list failed"));
         }
+        st = dev_alloc(c, &d, sizeof(unsigned) * links.size());
+        if (st != FRE_OK) return bail(st);
+        c->links = static_cast<unsigned *>(d);
+        if (cudaMemcpyAsync(c->links, links.data(), sizeof(unsigned) * links.size(), cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess)
+            return bail(fail(FRE_ERR_CUDA, "upload of the roller links failed"));
         if (cudaStreamSynchronize(c->stream) != cudaSuccess)
             return bail(fail(FRE_ERR_CUDA, "geometry upload: %s", cudaGetErrorString(cudaGetLastError())));
     }
     c->G.solid = c->solid;
+    c->G.links = c->links;
     if (!(p->flags & FRE_FLAG_GENERIC_KERNELS) && c->ks->row_width) {
         const unsigned sh = (p->flags >> FRE_FLAG_CHUNK_SHIFT) & 0xffu;
         c->row_w = c->ks->row_width(c->G, sh ? (1 << sh) : 0);
         c->rows = c->row_w > 0;
     }
-    c->fullrow = c->rows && !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable &&
-                 c->ks->fullrow_usable(c->G);
+    // the four-roller device has no chunked row kernels, only full rows
+    c->fullrow = !(p->flags & FRE_FLAG_GENERIC_KERNELS) && (c->rows || p->device == FRE_FOUR_ROLLER) &&
+                 !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable && c->ks->fullrow_usable(c->G);
     cudaGetLastError();
     *out = c;
     return FRE_OK;
@@ -590,19 +629,20 @@ fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launche
     for (int t = 0; t < nsteps; ++t) {
         fre::Launch L = launch_of(c);
         const bool pull = !c->local;
-        if (c->fullrow) c->ks->phi_fullrow(L, pull);
+        const bool full = c->fullrow && (pull || c->G.device != FRE_FOUR_ROLLER);
+        if (full) c->ks->phi_fullrow(L, pull);
         else if (c->rows) c->ks->phi_rows(L, pull);
         else c->ks->phi(L, pull);
         ++nl;
         cudaEventRecord(ev[3 * t + 1], c->stream);
         if (c->n_ghost) { c->ks->ghost(L, L.phi); ++nl; }
-        if (c->fullrow) c->ks->mu_fullrow(L);
+        if (full) c->ks->mu_fullrow(L);
         else if (c->rows) c->ks->mu_rows(L);
         else c->ks->mu(L);
         ++nl;
         if (c->n_ghost) { c->ks->ghost(L, L.mu); ++nl; }
         cudaEventRecord(ev[3 * t + 2], c->stream);
-        if (c->fullrow) c->ks->update_fullrow(L, pull);
+        if (full) c->ks->update_fullrow(L, pull);
         else if (c->rows) c->ks->update_rows(L, pull);
         else c->ks->update(L, pull);
         ++nl;
@@ -709,7 +749,7 @@ fre_status fre_components(fre_ctx *c, long long min_size, int *count, long long 
 
 long long fre_step_count(const fre_ctx *c) { return c ? c->step : -1; }
 
-int fre_uses_row_kernels(const fre_ctx *c) { return c && c->rows ? 1 : 0; }
+int fre_uses_row_kernels(const fre_ctx *c) { return c && (c->rows || c->fullrow) ? 1 : 0; }
 
 int fre_kernel_path(const fre_ctx *c) { return !c ? -1 : (c->fullrow ? 2 : (c->rows ? 1 : 0)); }
 

@@ -19,6 +19,7 @@ struct fre_ctx {
     void *phi[2]{};
     void *mu = nullptr;
     unsigned char *solid = nullptr;
+    unsigned *links = nullptr;  // four-roller: wall-link words per (x, y)
     int *ghost = nullptr;
     int n_ghost = 0;
     double *red = nullptr;

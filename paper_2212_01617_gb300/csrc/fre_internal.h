@@ -17,6 +17,7 @@ struct Geo {
     long long n;              // nodes
     long long np;             // plane stride of the population arrays (elements)
     const unsigned char *solid;  // roller id per node (0 = fluid); four-roller only
+    const unsigned *links;    // four-roller: wall-link word per (x, y) for the row kernels
     double rcx[5], rcy[5], om[5];  // roller centres and angular velocities (1..4)
     double uwall;             // shear wall speed
 };
@@ -34,6 +35,7 @@ struct Phys {
 // FRE_FLAG_REST_REFERENCE, else 0 (the rest equilibrium).
 struct PhysF {
     float omega_f, omega_g, kf, gamma3, A, kappa, rho0, uwall, u0, du;
+    float rcx[5], rcy[5], rom[5];  // four-roller: roller centres and angular velocities
 };
 
 // One population buffer (A or B).  FP64/FP32: f, g are [q][np] arrays of

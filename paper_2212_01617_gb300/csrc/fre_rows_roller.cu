@@ -1,0 +1,24 @@
+// Row kernels of the four-roller device (pulled phi pass and update, with
+// the per-node wall-link words staged beside the rows): a translation unit
+// of its own so that these instantiations compile alongside the others.
+#include "fre_ws.cuh"
+
+namespace fre {
+
+template <int Q, int FMT>
+void RollRows<Q, FMT>::phi(const Launch &L) {
+    WsRowLaunchers<Q, FMT>::template run_roll<WS_PHI>(L);
+}
+template <int Q, int FMT>
+void RollRows<Q, FMT>::update(const Launch &L) {
+    WsRowLaunchers<Q, FMT>::template run_roll<WS_UPDATE>(L);
+}
+
+template struct RollRows<9, FRE_FP32>;
+template struct RollRows<9, FRE_FP16DEV>;
+template struct RollRows<9, FRE_BF16DEV>;
+template struct RollRows<19, FRE_FP32>;
+template struct RollRows<19, FRE_FP16DEV>;
+template struct RollRows<19, FRE_BF16DEV>;
+
+}  // namespace fre

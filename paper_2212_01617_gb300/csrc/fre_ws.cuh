@@ -424,7 +424,7 @@ namespace fre {
 // memory and staged by one copy unless the pull offset wraps or meets a
 // wall; the phi / mu stencil rows of one z plane are one copy of R + 2 rows
 // (y0 - 1 .. y0 + R) unless they wrap or are clamped at a wall.
-template <int Q, int FMT, int KIND, int R>
+template <int Q, int FMT, int KIND, int R, bool ROLL = false>
 struct RowsLayout {
     using S = typename Fmt<FMT>::S;
     static constexpr bool DEV = Fmt<FMT>::DEV;
@@ -460,21 +460,35 @@ struct RowsLayout {
                              : (cz == 0 ? r + cy + 1 : (R + 2) + (cz > 0 ? 0 : R) + r);
     }
     // bytes that arrive per stage, and the stage extent
-    __host__ __device__ static unsigned tx_bytes(int nx) {
+    __host__ __device__ static unsigned base_tx(int nx) {
         if (KIND == WS_MU) return NFIELD * fldb(nx);
         if (KIND == WS_UPDATE) return Q * R * rowb(nx) + g_bytes(nx) + 2 * NFIELD * fldb(nx);
         return g_bytes(nx);
     }
-    __host__ __device__ static unsigned bytes(int nx) {
+    __host__ __device__ static unsigned base_bytes(int nx) {
         if (KIND == WS_UPDATE) return fld_off(nx) + 2 * NFIELD * fldb(nx);
-        return tx_bytes(nx);
+        return base_tx(nx);
     }
+    // four-roller device: the wall-link words (one uint32 per node) of the
+    // unit's R rows, after everything else
+    __host__ __device__ static unsigned lnk_off(int nx) { return (base_bytes(nx) + 15u) / 16u * 16u; }
+    __host__ __device__ static unsigned lnk_bytes(int nx) { return ROLL ? (unsigned)(R * nx * 4) : 0u; }
+    __host__ __device__ static unsigned tx_bytes(int nx) { return base_tx(nx) + lnk_bytes(nx); }
+    __host__ __device__ static unsigned bytes(int nx) { return ROLL ? lnk_off(nx) + lnk_bytes(nx) : base_bytes(nx); }
     __host__ __device__ static unsigned stage(int nx) { return (bytes(nx) + 127u) / 128u * 128u; }
-    // copy groups issued by the producer lanes
+    // copy groups issued by the producer lanes (the last one: the link words)
     __host__ __device__ static constexpr int ngroups() {
-        return KIND == WS_UPDATE ? 2 * Q + 2 * NGRP : (KIND == WS_PHI ? Q : NGRP);
+        return (KIND == WS_UPDATE ? 2 * Q + 2 * NGRP : (KIND == WS_PHI ? Q : NGRP)) + (ROLL ? 1 : 0);
     }
 };
+
+// Wall-link word of a node of the four-roller device (host-built table
+// [ny][nx], the same in every z plane since the rollers are extruded
+// along z): bit i (i < q) is set when the source x - c_i of population i
+// is a roller node; bits 24..26 hold that roller's number (one roller
+// borders a node); bit 30 marks a roller (solid) node itself.
+constexpr unsigned kLinkSolid = 1u << 30;
+
 
 // Two adjacent nodes per consumer thread: FP32 arithmetic on packed pairs
 // (the paired add / multiply / fused multiply-add of sm_100 and later).
@@ -490,6 +504,34 @@ __device__ __forceinline__ float2 acc_c(float2 acc, float2 a, int c) {
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+// A wall link of the four-roller device in the row kernels: the node's own
+// opposite population (read from global memory: the stage holds the pulled
+// rows) plus the moving-wall term 2 w_i dens (c_i . u_w) / cs^2 of the
+// roller's rigid rotation, c_i . u_w = omega_k (c_iy (x - X_k) - c_ix (y -
+// Y_k)) (the wall point along the link does not change it).  lat 0: f
+// (dens = rho0; 16-bit: the deviation from w_i rho0), 1: g (dens = phi of
+// the previous step).  idx: the node's index.
+template <int Q, int FMT>
+__device__ __forceinline__ float roll_link(const Launch &L, int lat, int i, size_t idx, int x, int y, unsigned lw,
+                                           float dens) {
+    using S = typename Fmt<FMT>::S;
+    constexpr bool DEV = Fmt<FMT>::DEV;
+    const int o = Lat<Q>::opp(i);
+    const size_t np = (size_t)L.G.np;
+    float v;
+    if (!lat) {
+        v = to_f(static_cast<const S *>(L.src.f)[(size_t)o * np + idx]);
+    } else if (DEV && o == 0) {
+        v = L.src.g0[idx];
+    } else {
+        v = to_f(static_cast<const S *>(L.src.g)[(size_t)(DEV ? o - 1 : o) * np + idx]);
+    }
+    const int k = (int)((lw >> 24) & 7u);
+    const float cu =
+        L.F.rom[k] * (float(Lat<Q>::cy(i)) * (float(x) - L.F.rcx[k]) - float(Lat<Q>::cx(i)) * (float(y) - L.F.rcy[k]));
+    return fmaf(float(6.0 * Lat<Q>::w(i)) * dens, cu, v);
+}
+
 // row[x], row[x + 1] for even x (one aligned vector load)
 __device__ __forceinline__ float2 ld_pair(const float *row, int x) { return *reinterpret_cast<const float2 *>(row + x); }
 __device__ __forceinline__ float2 ld_pair(const __half *row, int x) {
@@ -640,10 +682,12 @@ struct RowsPar {
 
 // NXC: the row length as a compile-time constant (every shared-memory
 // offset then folds into the instruction), or 0 to take it from the launch.
-template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC, int RPX>
+// ROLL: the four-roller device (wall links per node from the staged link
+// words, roller nodes stored as 0).
+template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
 __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
-    using FL = RowsLayout<Q, FMT, KIND, R>;
+    using FL = RowsLayout<Q, FMT, KIND, R, ROLL>;
     constexpr bool DEV = Fmt<FMT>::DEV;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NST], empty[NST];
@@ -713,6 +757,11 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
             }
             __syncwarp();
             for (int gi = lane; gi < FL::ngroups(); gi += 32) {
+                if (ROLL && gi == FL::ngroups() - 1) {
+                    // the link words of the unit's rows (contiguous in the table)
+                    bulk_load(buf + FL::lnk_off(nx), L.G.links + (size_t)y0 * nx, FL::lnk_bytes(nx), bar);
+                    continue;
+                }
                 if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q)) {
                     // ---- phi / mu stencil rows of one z plane
                     const int j = KIND == WS_MU ? gi : gi - 2 * Q;
@@ -811,6 +860,9 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 const int r = rg + q * RP;
                 const unsigned wall = wall_s[s][r];
                 const size_t row = ((size_t)z * ny + y0 + r) * nx;
+                // four-roller: the wall-link words of the pair's nodes
+                const uint2 lw = ROLL ? *reinterpret_cast<const uint2 *>(cur + FL::lnk_off(nx) + ((size_t)r * nx + x0) * 4)
+                                      : make_uint2(0u, 0u);
                 // rows without wall links (all but the first and last of the
                 // shear device) take every shift as a compile-time constant
                 auto pull_sum = [&](auto walls) {
@@ -828,11 +880,25 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                             const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
                             gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
                         }
+                        if constexpr (ROLL && PULL) {
+                            if (((lw.x | lw.y) >> i) & 1u) {
+                                const int y = y0 + r;
+                                if ((lw.x >> i) & 1u)
+                                    gv.x = roll_link<Q, FMT>(L, 1, i, row + x0, x0, y, lw.x, php[row + x0]);
+                                if ((lw.y >> i) & 1u)
+                                    gv.y = roll_link<Q, FMT>(L, 1, i, row + x0 + 1, x0 + 1, y, lw.y, php[row + x0 + 1]);
+                            }
+                        }
                         sum = add2(sum, gv);
                     }
                     return sum;
                 };
                 out[q] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
+                if constexpr (ROLL) {
+                    // roller nodes hold 0 (their stencil values come from the ghost fill)
+                    if (lw.x & kLinkSolid) out[q].x = 0.f;
+                    if (lw.y & kLinkSolid) out[q].y = 0.f;
+                }
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -877,6 +943,18 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 const int y = y0 + r;
                 const size_t row = ((size_t)z * ny + y) * nx;
                 const Site st = make_site(L.G, x0, y, z);
+                // four-roller: the wall-link words of the pair's nodes
+                const uint2 lw = ROLL ? *reinterpret_cast<const uint2 *>(cur + FL::lnk_off(nx) + ((size_t)r * nx + x0) * 4)
+                                      : make_uint2(0u, 0u);
+                const bool lany = ROLL && PULL && ((lw.x | lw.y) & ((1u << Q) - 1u)) != 0u;
+                // roller nodes store 0
+                auto msk = [&](float2 v) {
+                    if constexpr (ROLL) {
+                        if (lw.x & kLinkSolid) v.x = 0.f;
+                        if (lw.y & kLinkSolid) v.y = 0.f;
+                    }
+                    return v;
+                };
                 // FP32: start the lines of the off-axis stencil values (c_y and
                 // c_z both nonzero, read from global memory below) toward L1
                 // before the pull phase (measured 2% on the update; the
@@ -920,6 +998,15 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                                 fv = add2(fv, p2(float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw * rho0));
                             }
                         }
+                        if constexpr (ROLL && PULL) {
+                            // roller links (16-bit: deviations from w_i rho0,
+                            // the four-roller reference)
+                            if (lany && (((lw.x | lw.y) >> i) & 1u)) {
+                                if ((lw.x >> i) & 1u) fv.x = roll_link<Q, FMT>(L, 0, i, row + x0, x0, y, lw.x, rho0);
+                                if ((lw.y >> i) & 1u)
+                                    fv.y = roll_link<Q, FMT>(L, 0, i, row + x0 + 1, x0 + 1, y, lw.y, rho0);
+                            }
+                        }
                         f[i] = fv;
                     }
                 };
@@ -942,6 +1029,14 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                             const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
                             const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
                             gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
+                        }
+                        if constexpr (ROLL && PULL) {
+                            if (lany && (((lw.x | lw.y) >> i) & 1u)) {
+                                if ((lw.x >> i) & 1u)
+                                    gv.x = roll_link<Q, FMT>(L, 1, i, row + x0, x0, y, lw.x, php[row + x0]);
+                                if ((lw.y >> i) & 1u)
+                                    gv.y = roll_link<Q, FMT>(L, 1, i, row + x0 + 1, x0 + 1, y, lw.y, php[row + x0 + 1]);
+                            }
                         }
                         g[i] = gv;
                     }
@@ -1030,7 +1125,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                     const float2 wg = p2(og * w);
                     const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
                     const float2 Bg = mul2(mul2(wg, ph), cu3);
-                    const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
+                    const float2 gi = msk(fma2(omg, g[i], add2(Ag, Bg))), gj = msk(fma2(omg, g[j], sub2(Ag, Bg)));
                     if constexpr (DEV) {
                         // the rest population of g closes sum_i g*_i = phi on
                         // the values as they are stored
@@ -1080,7 +1175,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                         Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), GA));
                         Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
                     }
-                    const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
+                    const float2 fi = msk(fma2(omf, f[i], add2(Af, Bf))), fj = msk(fma2(omf, f[j], sub2(Af, Bf)));
                     if constexpr (DEV) {
                         fsum = add2(fsum, add2(st_pair(fp + (size_t)i * np, fi), st_pair(fp + (size_t)j * np, fj)));
                     } else {
@@ -1092,7 +1187,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 }
                 // f*_0: rho - sum, or for deviations (sum_i fr_i = rho0)
                 // (rho - rho0) - sum
-                st_pair(fp, sub2(sf, fsum));
+                st_pair(fp, msk(sub2(sf, fsum)));
 
                 if constexpr (TWO) {
                     if (walls) pull_g(std::true_type{});
@@ -1117,12 +1212,21 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                         collide_g(i, Lat<Q>::opp(i), float(Lat<Q>::w(i)), cu3, fma2(mul2(p2(1.5f), cu3), cu, m15usq));
                     }
                 }
-                if constexpr (DEV) st_pair(L.dst.g0 + off, sub2(ph, gsum));
-                else st_pair(gp, sub2(ph, gsum));
+                if constexpr (DEV) st_pair(L.dst.g0 + off, msk(sub2(ph, gsum)));
+                else st_pair(gp, msk(sub2(ph, gsum)));
             }
         }
     }
 }
+
+// The pulled phi pass and update of the four-roller device on the row
+// kernels (wall-link words staged with the rows); defined in
+// fre_rows_roller.cu, a translation unit of its own.
+template <int Q, int FMT>
+struct RollRows {
+    static void phi(const Launch &L);
+    static void update(const Launch &L);
+};
 
 template <int Q, int FMT>
 struct WsRowLaunchers {
@@ -1131,16 +1235,16 @@ struct WsRowLaunchers {
     // stages per block: the update takes up to three of those that fit (one
     // block per SM on long rows); the lighter phi and mu passes take two, so
     // that two blocks (two producer warps issuing bulk copies) share an SM
-    template <int KIND, int R>
+    template <int KIND, int R, bool ROLL = false>
     static int nst(int nx) {
-        const unsigned sb = RowsLayout<Q, FMT, KIND, R>::stage(nx);
+        const unsigned sb = RowsLayout<Q, FMT, KIND, R, ROLL>::stage(nx);
         const int lim = KIND == WS_UPDATE ? kMaxSmem : kMaxSmem / 2;
         const int n = (int)(lim / sb);
         if (KIND != WS_UPDATE) return n >= 2 ? 2 : n;
         return n >= 3 ? 3 : (n >= 2 ? 2 : n);
     }
     // two rows per unit where a staged row is shorter than 2 KB
-    template <int KIND>
+    template <int KIND, bool ROLL = false>
     static int rows_per_unit(const Geo &G, bool pull) {
         // the mu pass stages three copies per unit whatever R: four rows per
         // unit keep it off the copy engine's rate of operations
@@ -1149,10 +1253,13 @@ struct WsRowLaunchers {
         if (G.nx % 64 != 0) return 2;
         if (!pull || G.ny % 2 != 0) return 1;
         if (RowsLayout<Q, FMT, KIND, 1>::rowb(G.nx) >= 2048) return 1;
-        return nst<KIND, 2>(G.nx) >= 2 ? 2 : 1;
+        return nst<KIND, 2, ROLL>(G.nx) >= 2 ? 2 : 1;
     }
+    // the four-roller device takes the row kernels when its wall-link table
+    // is there (pulled steps; the first, in-place step runs per node)
     static bool usable(const Geo &G) {
-        if (G.device == FRE_FOUR_ROLLER) return false;
+        const bool roll = G.device == FRE_FOUR_ROLLER;
+        if (roll && !G.links) return false;
         if ((G.np * sizeof(S)) % 16 != 0 || (G.nx * sizeof(S)) % 16 != 0 || (G.nx * 4) % 16 != 0) return false;
         // rows of a whole number of warps' pairs (nx a multiple of 64), or of
         // an odd number of half warps taken two rows at a time (ny even)
@@ -1160,14 +1267,17 @@ struct WsRowLaunchers {
         if (G.nx % 64 != 0 && (G.ny % 2 != 0 || nst<WS_UPDATE, 2>(G.nx) < 2 || nst<WS_PHI, 2>(G.nx) < 2 ||
                                nst<WS_MU, 2>(G.nx) < 2 || nst<WS_MU, 4>(G.nx) < 2))
             return false;
+        if (roll && (nst<WS_UPDATE, 2, true>(G.nx) < 2 || nst<WS_PHI, 2, true>(G.nx) < 2 ||
+                     nst<WS_UPDATE, 1, true>(G.nx) < 2 || nst<WS_PHI, 1, true>(G.nx) < 1))
+            return false;
         return nst<WS_UPDATE, 1>(G.nx) >= 2 && nst<WS_PHI, 1>(G.nx) >= 1 && nst<WS_MU, 1>(G.nx) >= 1;
     }
-    template <int KIND, bool PULL, int NST, int R, int NXC, int RPX>
+    template <int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
     static void launch(const Launch &L) {
         const int nx = L.G.nx;
         const int nu = (L.G.ny / R) * L.G.nz;
-        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
-        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX>;
+        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R, ROLL>::stage(nx);
+        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX, ROLL>;
         LaunchShape::opt_in((const void *)fn, smem);
         const int threads = RPX * (nx / 2) + 32;
         const int g = std::min(nu, LaunchShape::sms() *
@@ -1175,24 +1285,24 @@ struct WsRowLaunchers {
         fn<<<g, threads, smem, L.stream>>>(L, nu);
     }
     // resident blocks per SM of one launch shape
-    template <int KIND, bool PULL, int NST, int R, int NXC, int RPX>
+    template <int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
     static int resident(const Launch &L) {
         const int nx = L.G.nx;
-        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
-        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX>;
+        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R, ROLL>::stage(nx);
+        auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX, ROLL>;
         LaunchShape::opt_in((const void *)fn, smem);
         return LaunchShape::blocks_per_sm((const void *)fn, RPX * (nx / 2) + 32, smem);
     }
     // a third stage deepens the copy pipeline, but on short rows (few
     // consumer warps per block) it can cost a resident block: keep it only
     // where the SM holds as many blocks with it as with two
-    template <int KIND, bool PULL, int R, int NXC, int RPX>
+    template <int KIND, bool PULL, int R, int NXC, int RPX, bool ROLL = false>
     static void run_n(const Launch &L) {
-        if (nst<KIND, R>(L.G.nx) >= 3 &&
-            resident<KIND, PULL, 3, R, NXC, RPX>(L) >= resident<KIND, PULL, 2, R, NXC, RPX>(L))
-            launch<KIND, PULL, 3, R, NXC, RPX>(L);
+        if (nst<KIND, R, ROLL>(L.G.nx) >= 3 &&
+            resident<KIND, PULL, 3, R, NXC, RPX, ROLL>(L) >= resident<KIND, PULL, 2, R, NXC, RPX, ROLL>(L))
+            launch<KIND, PULL, 3, R, NXC, RPX, ROLL>(L);
         else
-            launch<KIND, PULL, 2, R, NXC, RPX>(L);
+            launch<KIND, PULL, 2, R, NXC, RPX, ROLL>(L);
     }
     template <int KIND, bool PULL, int R>
     static void run_r(const Launch &L) {
@@ -1209,8 +1319,33 @@ struct WsRowLaunchers {
         if (PULL && L.G.nx == 512) run_n<KIND, PULL, R, 512, RPD>(L);
         else run_n<KIND, PULL, R, 0, RPD>(L);
     }
+    // four-roller device, pulled steps of the phi pass and the update (the
+    // kernels with the wall-link words; instantiated in fre_rows_roller.cu)
+    template <int KIND, int R>
+    static void run_r_roll(const Launch &L) {
+        constexpr int RPD = RowsPar<KIND, R>::V;
+        if constexpr (RPD == 1 && R % 2 == 0) {
+            if (L.G.nx % 64 != 0) {
+                run_n<KIND, true, R, 0, 2, true>(L);
+                return;
+            }
+        }
+        run_n<KIND, true, R, 0, RPD, true>(L);
+    }
+    template <int KIND>
+    static void run_roll(const Launch &L) {
+        if (rows_per_unit<KIND, true>(L.G, true) == 2) run_r_roll<KIND, 2>(L);
+        else run_r_roll<KIND, 1>(L);
+    }
     template <int KIND, bool PULL>
     static void run(const Launch &L) {
+        if constexpr (KIND != WS_MU && PULL) {
+            if (L.G.device == FRE_FOUR_ROLLER) {
+                if (KIND == WS_UPDATE) RollRows<Q, FMT>::update(L);
+                else RollRows<Q, FMT>::phi(L);
+                return;
+            }
+        }
         const int r = rows_per_unit<KIND>(L.G, PULL);
         if constexpr (KIND == WS_MU) {
             if (r == 4) {

@@ -166,3 +166,44 @@ def test_half_warp_rows_take_the_full_row_kernels(fre, precision):
     assert a.kernel_path == 2 and b.kernel_path == 1, (a.kernel_path, b.kernel_path)
     a.close()
     b.close()
+
+
+ROLL_CASES = [
+    # lattice, nx, ny, nz: square boxes, a 96-wide one (two rows side by
+    # side) and a 192 x 96 box of the serving workload's shape
+    ("d3q19", 64, 64, 8),
+    ("d3q19", 96, 96, 6),
+    ("d3q19", 192, 96, 4),
+    ("d2q9", 128, 128, 1),
+]
+
+
+@pytest.mark.parametrize("case", ROLL_CASES, ids=lambda c: f"{c[0]}-{c[1]}x{c[2]}x{c[3]}")
+@pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
+def test_four_roller_row_kernels(fre, orc, case, precision):
+    """The four-roller device on the row kernels (the wall links of every
+    node staged with its rows, the local opposite population and the
+    rollers' moving-wall term on each link, roller nodes stored as 0, ghost
+    fills between the passes) against the per-node kernels and the FP64
+    oracle after 200 steps, with the bounds of the shear rows above."""
+    lattice, nx, ny, nz = case
+    kw = dict(u_wall=0.01, tau_f=1.2, tau_g=1.0, gamma_mob=0.8)
+    rows = make(fre, lattice, "four_roller", nx, ny, nz, precision, **kw)
+    gen = make(fre, lattice, "four_roller", nx, ny, nz, precision, flags=1, **kw)
+    assert rows.kernel_path == 2 and gen.kernel_path == 0
+    a = dict(tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0, rho0=1.0)
+    a.update(kw)
+    o = orc.Oracle({"d2q9": 0, "d3q19": 1}[lattice], 1, nx, ny, nz, a["tau_f"], a["tau_g"], a["A"], a["kappa"],
+                   a["gamma_mob"], a["u_wall"], a["rho0"])
+    c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, nx / 10)
+    for s in (rows, gen, o):
+        s.init_droplet(*c)
+        s.step(200)
+    ref = o.fields()
+    tol = {"fp32": 1e-5, "fp16dev": 3e-3, "bf16dev": 2e-2}[precision]
+    utol = 1e-4 if precision == "fp32" else tol
+    res = {name: errs(sim.fields(), ref, u_floor=0.01) for name, sim in (("rows", rows), ("per-node", gen))}
+    for name, e in res.items():
+        assert all(v < (utol if k.startswith("u") else tol) for k, v in e.items()), (name, res)
+    rows.close()
+    gen.close()
