@@ -219,6 +219,7 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.W = c->row_w;
     L.err = c->err_dev;
     L.stall = (c->p.flags & FRE_FLAG_TEST_PIPELINE_STALL) ? 1 : 0;
+    L.reflect = (c->fullrow && c->G.device == FRE_FOUR_ROLLER) ? 1 : 0;
     L.wait_ns = L.stall ? 5000000ull : 2000000000ull;
     return L;
 }

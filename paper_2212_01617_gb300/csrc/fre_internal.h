@@ -68,6 +68,8 @@ struct Launch {
     int *err;              // device error word (pipeline wait timed out)
     unsigned long long wait_ns;  // limit of every pipeline wait
     int stall;             // FRE_FLAG_TEST_PIPELINE_STALL: producers issue no copies
+    int reflect;           // four-roller on the row kernels: per-node updates also
+                           // reflect their wall links into the roller nodes' slots
     double *staging;       // FP64 staging of host I/O (n doubles per field)
     cudaStream_t stream;
 };

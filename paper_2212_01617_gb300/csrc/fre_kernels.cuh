@@ -500,6 +500,23 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
         else
             fsum += P::stf_back(L.dst, L.G.np, i, n, fs, T(L.P.rho0), U);
         gsum += P::stg_back(L.dst, L.G.np, i, n, gs);
+        if (L.reflect) {
+            // four-roller device run by the row kernels: when x + c_i is a
+            // roller node, the next step pulls population opp(i) at x from
+            // it; leave there f*_i(x) plus the moving-wall term of that link
+            // (the row kernels read it as from any other source)
+            const int nb = site_nb<Q>(s, i);
+            const int k = L.G.solid[nb];
+            if (k) {
+                const int o = Lat<Q>::opp(i);
+                // c_opp(i) . u_w = -(c_i . u_w), u_w = omega_k z x (x - c_k)
+                const T cu = -T(L.G.om[k]) * (T(Lat<Q>::cy(i)) * (T(s.x) - T(L.G.rcx[k])) -
+                                               T(Lat<Q>::cx(i)) * (T(s.y) - T(L.G.rcy[k])));
+                const T wi6 = T(6.0 * Lat<Q>::w(i));
+                P::stf(L.dst, L.G.np, o, nb, fs + wi6 * T(L.P.rho0) * cu, T(L.P.rho0), T(0));
+                P::stg(L.dst, L.G.np, o, nb, gs + wi6 * m.phi * cu);
+            }
+        }
     }
     // rest populations close the collision invariants on the values as
     // stored: sum f* = rho, sum g* = phi (in the 16-bit formats up to the

@@ -1,14 +1,10 @@
-// Row kernels of the four-roller device (pulled phi pass and update, with
-// the per-node wall-link words staged beside the rows): a translation unit
-// of its own so that these instantiations compile alongside the others.
+// Row update of the four-roller device (pulled steps, with the per-node
+// wall-link words staged beside the rows): a translation unit of its own so
+// that these instantiations compile alongside the others.
 #include "fre_ws.cuh"
 
 namespace fre {
 
-template <int Q, int FMT>
-void RollRows<Q, FMT>::phi(const Launch &L) {
-    WsRowLaunchers<Q, FMT>::template run_roll<WS_PHI>(L);
-}
 template <int Q, int FMT>
 void RollRows<Q, FMT>::update(const Launch &L) {
     WsRowLaunchers<Q, FMT>::template run_roll<WS_UPDATE>(L);

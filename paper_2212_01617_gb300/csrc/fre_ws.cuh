@@ -504,33 +504,6 @@ __device__ __forceinline__ float2 acc_c(float2 acc, float2 a, int c) {
 __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-// A wall link of the four-roller device in the row kernels: the node's own
-// opposite population (read from global memory: the stage holds the pulled
-// rows) plus the moving-wall term 2 w_i dens (c_i . u_w) / cs^2 of the
-// roller's rigid rotation, c_i . u_w = omega_k (c_iy (x - X_k) - c_ix (y -
-// Y_k)) (the wall point along the link does not change it).  lat 0: f
-// (dens = rho0; 16-bit: the deviation from w_i rho0), 1: g (dens = phi of
-// the previous step).  idx: the node's index.
-template <int Q, int FMT>
-__device__ __forceinline__ float roll_link(const Launch &L, int lat, int i, size_t idx, int x, int y, unsigned lw,
-                                           float dens) {
-    using S = typename Fmt<FMT>::S;
-    constexpr bool DEV = Fmt<FMT>::DEV;
-    const int o = Lat<Q>::opp(i);
-    const size_t np = (size_t)L.G.np;
-    float v;
-    if (!lat) {
-        v = to_f(static_cast<const S *>(L.src.f)[(size_t)o * np + idx]);
-    } else if (DEV && o == 0) {
-        v = L.src.g0[idx];
-    } else {
-        v = to_f(static_cast<const S *>(L.src.g)[(size_t)(DEV ? o - 1 : o) * np + idx]);
-    }
-    const int k = (int)((lw >> 24) & 7u);
-    const float cu =
-        L.F.rom[k] * (float(Lat<Q>::cy(i)) * (float(x) - L.F.rcx[k]) - float(Lat<Q>::cx(i)) * (float(y) - L.F.rcy[k]));
-    return fmaf(float(6.0 * Lat<Q>::w(i)) * dens, cu, v);
-}
 
 // row[x], row[x + 1] for even x (one aligned vector load)
 __device__ __forceinline__ float2 ld_pair(const float *row, int x) { return *reinterpret_cast<const float2 *>(row + x); }
@@ -566,6 +539,33 @@ __device__ __forceinline__ float2 st_pair(__nv_bfloat16 *p, float2 v) {
     const __nv_bfloat162 h = __float22bfloat162_rn(v);
     *reinterpret_cast<__nv_bfloat162 *>(p) = h;
     return __bfloat1622float2(h);
+}
+
+// one FP32 value in the storage type
+template <typename S>
+__device__ __forceinline__ S from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+// a pair store that skips the roller (solid) nodes of the pair (bit 30 of
+// their wall-link words); returns the stored values (rounded), 0 for rollers
+template <typename S>
+__device__ __forceinline__ float2 st_fluid(S *p, float2 v, uint2 lw) {
+    float2 out = make_float2(0.f, 0.f);
+    if (!(lw.x & (1u << 30))) {
+        const S a = from_f<S>(v.x);
+        p[0] = a;
+        out.x = to_f(a);
+    }
+    if (!(lw.y & (1u << 30))) {
+        const S b = from_f<S>(v.y);
+        p[1] = b;
+        out.y = to_f(b);
+    }
+    return out;
 }
 
 // populations whose c_y has the sign of sy, as a bit mask
@@ -860,9 +860,6 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 const int r = rg + q * RP;
                 const unsigned wall = wall_s[s][r];
                 const size_t row = ((size_t)z * ny + y0 + r) * nx;
-                // four-roller: the wall-link words of the pair's nodes
-                const uint2 lw = ROLL ? *reinterpret_cast<const uint2 *>(cur + FL::lnk_off(nx) + ((size_t)r * nx + x0) * 4)
-                                      : make_uint2(0u, 0u);
                 // rows without wall links (all but the first and last of the
                 // shear device) take every shift as a compile-time constant
                 auto pull_sum = [&](auto walls) {
@@ -880,25 +877,11 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                             const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
                             gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
                         }
-                        if constexpr (ROLL && PULL) {
-                            if (((lw.x | lw.y) >> i) & 1u) {
-                                const int y = y0 + r;
-                                if ((lw.x >> i) & 1u)
-                                    gv.x = roll_link<Q, FMT>(L, 1, i, row + x0, x0, y, lw.x, php[row + x0]);
-                                if ((lw.y >> i) & 1u)
-                                    gv.y = roll_link<Q, FMT>(L, 1, i, row + x0 + 1, x0 + 1, y, lw.y, php[row + x0 + 1]);
-                            }
-                        }
                         sum = add2(sum, gv);
                     }
                     return sum;
                 };
                 out[q] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
-                if constexpr (ROLL) {
-                    // roller nodes hold 0 (their stencil values come from the ghost fill)
-                    if (lw.x & kLinkSolid) out[q].x = 0.f;
-                    if (lw.y & kLinkSolid) out[q].y = 0.f;
-                }
             }
             __syncwarp();
             if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -946,14 +929,53 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 // four-roller: the wall-link words of the pair's nodes
                 const uint2 lw = ROLL ? *reinterpret_cast<const uint2 *>(cur + FL::lnk_off(nx) + ((size_t)r * nx + x0) * 4)
                                       : make_uint2(0u, 0u);
-                const bool lany = ROLL && PULL && ((lw.x | lw.y) & ((1u << Q) - 1u)) != 0u;
-                // roller nodes store 0
-                auto msk = [&](float2 v) {
+                const bool lany = ROLL && ((lw.x | lw.y) & ((1u << Q) - 1u)) != 0u;
+                // store a pair; the four-roller device leaves the slots of
+                // its roller nodes alone (they hold the populations its wall
+                // links reflect, below).  Returns the values as stored
+                // (16-bit: rounded; 0 for roller nodes)
+                auto stp = [&](S *p, float2 v) -> float2 {
                     if constexpr (ROLL) {
-                        if (lw.x & kLinkSolid) v.x = 0.f;
-                        if (lw.y & kLinkSolid) v.y = 0.f;
+                        if ((lw.x | lw.y) & kLinkSolid) return st_fluid(p, v, lw);
                     }
-                    return v;
+                    if constexpr (DEV) {
+                        return st_pair(p, v);
+                    } else {
+                        st_pair(p, v);
+                        return v;
+                    }
+                };
+                // Four-roller wall links, reflected ahead of the next step:
+                // for a link of population i at node x (source x - c_i a
+                // roller node), the value the next step pulls there is
+                // f*_opp(i)(x) plus the moving-wall term 2 w_i dens (c_i . u_w)
+                // / cs^2; it is stored into slot i of that roller node, so the
+                // pull reads it as from any other source (each roller slot
+                // has at most one such writer).  v: f*_opp(i) (16-bit f: its
+                // deviation from w_i rho0), dens: rho0 (f) or phi(x, t) (g).
+                auto reflect = [&](int lat, int i, int a, float v, float dens) {
+                    const int xa = x0 + a;
+                    const int xs = wrapi(xa - Lat<Q>::cx(i), nx), ysr = wrapi(y - Lat<Q>::cy(i), ny),
+                              zs = wrapi(z - Lat<Q>::cz(i), nz);
+                    const size_t src = ((size_t)zs * ny + ysr) * nx + xs;
+                    const int k = L.G.solid[src];
+                    const float cu = L.F.rom[k] * (float(Lat<Q>::cy(i)) * (float(xa) - L.F.rcx[k]) -
+                                                   float(Lat<Q>::cx(i)) * (float(y) - L.F.rcy[k]));
+                    const float val = fmaf(float(6.0 * Lat<Q>::w(i)) * dens, cu, v);
+                    if (!lat) {
+                        static_cast<S *>(L.dst.f)[(size_t)i * np + src] = from_f<S>(val);
+                    } else if (DEV && i == 0) {
+                        L.dst.g0[src] = val;
+                    } else {
+                        static_cast<S *>(L.dst.g)[(size_t)(DEV ? i - 1 : i) * np + src] = from_f<S>(val);
+                    }
+                };
+                // the reflections of opposite pair (i, j) of this pair of nodes
+                auto reflect_pair = [&](int lat, int i, int j, float2 vi, float2 vj, float2 dens) {
+                    if ((lw.x >> i) & 1u) reflect(lat, i, 0, vj.x, dens.x);
+                    if ((lw.y >> i) & 1u) reflect(lat, i, 1, vj.y, dens.y);
+                    if ((lw.x >> j) & 1u) reflect(lat, j, 0, vi.x, dens.x);
+                    if ((lw.y >> j) & 1u) reflect(lat, j, 1, vi.y, dens.y);
                 };
                 // FP32: start the lines of the off-axis stencil values (c_y and
                 // c_z both nonzero, read from global memory below) toward L1
@@ -998,15 +1020,6 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                                 fv = add2(fv, p2(float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw * rho0));
                             }
                         }
-                        if constexpr (ROLL && PULL) {
-                            // roller links (16-bit: deviations from w_i rho0,
-                            // the four-roller reference)
-                            if (lany && (((lw.x | lw.y) >> i) & 1u)) {
-                                if ((lw.x >> i) & 1u) fv.x = roll_link<Q, FMT>(L, 0, i, row + x0, x0, y, lw.x, rho0);
-                                if ((lw.y >> i) & 1u)
-                                    fv.y = roll_link<Q, FMT>(L, 0, i, row + x0 + 1, x0 + 1, y, lw.y, rho0);
-                            }
-                        }
                         f[i] = fv;
                     }
                 };
@@ -1029,14 +1042,6 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                             const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
                             const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
                             gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
-                        }
-                        if constexpr (ROLL && PULL) {
-                            if (lany && (((lw.x | lw.y) >> i) & 1u)) {
-                                if ((lw.x >> i) & 1u)
-                                    gv.x = roll_link<Q, FMT>(L, 1, i, row + x0, x0, y, lw.x, php[row + x0]);
-                                if ((lw.y >> i) & 1u)
-                                    gv.y = roll_link<Q, FMT>(L, 1, i, row + x0 + 1, x0 + 1, y, lw.y, php[row + x0 + 1]);
-                            }
                         }
                         g[i] = gv;
                     }
@@ -1125,16 +1130,16 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                     const float2 wg = p2(og * w);
                     const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
                     const float2 Bg = mul2(mul2(wg, ph), cu3);
-                    const float2 gi = msk(fma2(omg, g[i], add2(Ag, Bg))), gj = msk(fma2(omg, g[j], sub2(Ag, Bg)));
+                    const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
+                    if constexpr (ROLL) {
+                        if (lany) reflect_pair(1, i, j, gi, gj, ph);
+                    }
                     if constexpr (DEV) {
                         // the rest population of g closes sum_i g*_i = phi on
                         // the values as they are stored
-                        gsum = add2(gsum, add2(st_pair(gp + (size_t)(i - 1) * np, gi),
-                                               st_pair(gp + (size_t)(j - 1) * np, gj)));
+                        gsum = add2(gsum, add2(stp(gp + (size_t)(i - 1) * np, gi), stp(gp + (size_t)(j - 1) * np, gj)));
                     } else {
-                        st_pair(gp + (size_t)i * np, gi);
-                        st_pair(gp + (size_t)j * np, gj);
-                        gsum = add2(gsum, add2(gi, gj));
+                        gsum = add2(gsum, add2(stp(gp + (size_t)i * np, gi), stp(gp + (size_t)j * np, gj)));
                     }
                 };
 
@@ -1175,19 +1180,16 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                         Af = fma2(wr, fma2(rho, E, sf), mul2(p2(kf * w), GA));
                         Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
                     }
-                    const float2 fi = msk(fma2(omf, f[i], add2(Af, Bf))), fj = msk(fma2(omf, f[j], sub2(Af, Bf)));
-                    if constexpr (DEV) {
-                        fsum = add2(fsum, add2(st_pair(fp + (size_t)i * np, fi), st_pair(fp + (size_t)j * np, fj)));
-                    } else {
-                        st_pair(fp + (size_t)i * np, fi);
-                        st_pair(fp + (size_t)j * np, fj);
-                        fsum = add2(fsum, add2(fi, fj));
+                    const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
+                    if constexpr (ROLL) {
+                        if (lany) reflect_pair(0, i, j, fi, fj, p2(rho0));
                     }
+                    fsum = add2(fsum, add2(stp(fp + (size_t)i * np, fi), stp(fp + (size_t)j * np, fj)));
                     if constexpr (!TWO) collide_g(i, j, w, cu3, E);
                 }
                 // f*_0: rho - sum, or for deviations (sum_i fr_i = rho0)
                 // (rho - rho0) - sum
-                st_pair(fp, msk(sub2(sf, fsum)));
+                stp(fp, sub2(sf, fsum));
 
                 if constexpr (TWO) {
                     if (walls) pull_g(std::true_type{});
@@ -1212,19 +1214,29 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                         collide_g(i, Lat<Q>::opp(i), float(Lat<Q>::w(i)), cu3, fma2(mul2(p2(1.5f), cu3), cu, m15usq));
                     }
                 }
-                if constexpr (DEV) st_pair(L.dst.g0 + off, msk(sub2(ph, gsum)));
-                else st_pair(gp, msk(sub2(ph, gsum)));
+                if constexpr (DEV) {
+                    const float2 g0v = sub2(ph, gsum);
+                    if (ROLL && ((lw.x | lw.y) & kLinkSolid)) {
+                        if (!(lw.x & kLinkSolid)) L.dst.g0[off] = g0v.x;
+                        if (!(lw.y & kLinkSolid)) L.dst.g0[off + 1] = g0v.y;
+                    } else {
+                        st_pair(L.dst.g0 + off, g0v);
+                    }
+                } else {
+                    stp(gp, sub2(ph, gsum));
+                }
             }
         }
     }
 }
 
-// The pulled phi pass and update of the four-roller device on the row
-// kernels (wall-link words staged with the rows); defined in
-// fre_rows_roller.cu, a translation unit of its own.
+// The pulled update of the four-roller device on the row kernels (wall-link
+// words staged with the rows, wall links reflected into the roller nodes'
+// slots); defined in fre_rows_roller.cu, a translation unit of its own.  Its
+// phi and mu passes are the plain row kernels: the pull reads the reflected
+// populations from the roller slots like any other source.
 template <int Q, int FMT>
 struct RollRows {
-    static void phi(const Launch &L);
     static void update(const Launch &L);
 };
 
@@ -1267,9 +1279,7 @@ struct WsRowLaunchers {
         if (G.nx % 64 != 0 && (G.ny % 2 != 0 || nst<WS_UPDATE, 2>(G.nx) < 2 || nst<WS_PHI, 2>(G.nx) < 2 ||
                                nst<WS_MU, 2>(G.nx) < 2 || nst<WS_MU, 4>(G.nx) < 2))
             return false;
-        if (roll && (nst<WS_UPDATE, 2, true>(G.nx) < 2 || nst<WS_PHI, 2, true>(G.nx) < 2 ||
-                     nst<WS_UPDATE, 1, true>(G.nx) < 2 || nst<WS_PHI, 1, true>(G.nx) < 1))
-            return false;
+        if (roll && (nst<WS_UPDATE, 2, true>(G.nx) < 2 || nst<WS_UPDATE, 1, true>(G.nx) < 2)) return false;
         return nst<WS_UPDATE, 1>(G.nx) >= 2 && nst<WS_PHI, 1>(G.nx) >= 1 && nst<WS_MU, 1>(G.nx) >= 1;
     }
     template <int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
@@ -1339,10 +1349,9 @@ struct WsRowLaunchers {
     }
     template <int KIND, bool PULL>
     static void run(const Launch &L) {
-        if constexpr (KIND != WS_MU && PULL) {
+        if constexpr (KIND == WS_UPDATE && PULL) {
             if (L.G.device == FRE_FOUR_ROLLER) {
-                if (KIND == WS_UPDATE) RollRows<Q, FMT>::update(L);
-                else RollRows<Q, FMT>::phi(L);
+                RollRows<Q, FMT>::update(L);
                 return;
             }
         }
