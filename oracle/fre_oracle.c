@@ -96,6 +96,7 @@ struct orc_state {
     double *f, *g;         /* pre-collision populations [q][n] */
     double *fs, *gs;       /* post-collision populations [q][n] */
     double *rho, *phi, *mu, *ux, *uy, *uz, *Fx, *Fy, *Fz;
+    double *mu_rho;        /* full functional: mu_rho (mu holds mu_phi) */
     signed char *solid;    /* 0 fluid, k in 1..4: inside roller k */
     double rc[5][2];       /* roller centres (index 1..4) */
     double omega[5];       /* roller angular velocities, counter-clockwise > 0 */
@@ -305,6 +306,7 @@ orc_state *orc_create(const orc_params *p)
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
     if (p->lattice == ORC_D2Q9 && p->nz != 1) return NULL;
     if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) return NULL;
+    if (p->model != 0 && p->model != 1) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     if (!s) return NULL;
     s->p = *p;
@@ -321,11 +323,11 @@ orc_state *orc_create(const orc_params *p)
     s->fs = calloc(qn, sizeof(double));
     s->gs = calloc(qn, sizeof(double));
     double **fields[] = {&s->rho, &s->phi, &s->mu, &s->ux, &s->uy, &s->uz,
-                         &s->Fx, &s->Fy, &s->Fz};
-    for (int k = 0; k < 9; ++k) *fields[k] = calloc((size_t)s->n, sizeof(double));
+                         &s->Fx, &s->Fy, &s->Fz, &s->mu_rho};
+    for (int k = 0; k < 10; ++k) *fields[k] = calloc((size_t)s->n, sizeof(double));
     s->solid = calloc((size_t)s->n, 1);
     int ok = s->f && s->g && s->fs && s->gs && s->solid;
-    for (int k = 0; k < 9; ++k) ok = ok && *fields[k];
+    for (int k = 0; k < 10; ++k) ok = ok && *fields[k];
     if (!ok) { orc_destroy(s); return NULL; }
     if (p->device == ORC_FOUR_ROLLER) {
         double cx = 0.5 * (p->nx - 1), cy = 0.5 * (p->ny - 1);
@@ -350,7 +352,7 @@ void orc_destroy(orc_state *s)
     if (!s) return;
     free(s->f); free(s->g); free(s->fs); free(s->gs);
     free(s->rho); free(s->phi); free(s->mu); free(s->ux); free(s->uy); free(s->uz);
-    free(s->Fx); free(s->Fy); free(s->Fz);
+    free(s->Fx); free(s->Fy); free(s->Fz); free(s->mu_rho);
     free(s->solid);
     free(s);
 }
@@ -360,22 +362,46 @@ long long orc_nodes(const orc_state *s) { return s->n; }
 
 /* ------------------------------------------------------ macroscopic fields */
 
-/* Step 2: mu at fluid nodes from phi (phi ghosts must be filled). */
+/* isotropic Laplacian of a field at fluid node n (ghosts filled) */
+static double laplacian(const orc_state *s, const double *a, long long n)
+{
+    int x, y, z;
+    coords(s, n, &x, &y, &z);
+    double lap = 0.0;
+    for (int i = 1; i < s->q; ++i)
+        lap += s->w[i] * (a[stencil_nb(s, x, y, z, i)] - a[n]);
+    return lap * (2.0 / CS2);
+}
+
+/* Step 2: mu at fluid nodes from phi (phi ghosts must be filled).
+ * Reduced functional (model 0): mu = A(phi^3 - phi) - kappa lap(phi).
+ * Full functional (model 1, Eq. mu_rho and Eq. mu_phi; rho ghosts filled
+ * too), with a = rho + phi, b = rho - phi:
+ *   mu_rho = k1/8 a(a-2)(a-1) + k2/8 b(b-2)(b-1)
+ *            + alpha^2/4 [-(k1 + k2) lap(rho) + (k2 - k1) lap(phi)],
+ *   mu_phi = k1/8 a(a-2)(a-1) - k2/8 b(b-2)(b-1)
+ *            + alpha^2/4 [-(k1 + k2) lap(phi) + (k2 - k1) lap(rho)]. */
 static void compute_mu(orc_state *s)
 {
     #pragma omp parallel for schedule(static)
     for (long long n = 0; n < s->n; ++n) {
         if (s->solid[n]) continue;
-        int x, y, z;
-        coords(s, n, &x, &y, &z);
-        double lap = 0.0;
-        for (int i = 1; i < s->q; ++i)
-            lap += s->w[i] * (s->phi[stencil_nb(s, x, y, z, i)] - s->phi[n]);
-        lap *= 2.0 / CS2;
         double ph = s->phi[n];
-        s->mu[n] = s->p.A * (ph * ph * ph - ph) - s->p.kappa * lap;
+        double lphi = laplacian(s, s->phi, n);
+        if (s->p.model == 0) {
+            s->mu[n] = s->p.A * (ph * ph * ph - ph) - s->p.kappa * lphi;
+            continue;
+        }
+        double lrho = laplacian(s, s->rho, n);
+        double k1 = s->p.kappa1, k2 = s->p.kappa2, al2 = s->p.alpha * s->p.alpha;
+        double a = s->rho[n] + ph, b = s->rho[n] - ph;
+        double ta = k1 / 8.0 * a * (a - 2.0) * (a - 1.0);
+        double tb = k2 / 8.0 * b * (b - 2.0) * (b - 1.0);
+        s->mu_rho[n] = ta + tb + al2 / 4.0 * (-(k1 + k2) * lrho + (k2 - k1) * lphi);
+        s->mu[n] = ta - tb + al2 / 4.0 * (-(k1 + k2) * lphi + (k2 - k1) * lrho);
     }
     fill_ghosts(s, s->mu);
+    if (s->p.model == 1) fill_ghosts(s, s->mu_rho);
 }
 
 /* Steps 1-4 from the pre-collision populations: rho, phi, mu, F, u. */
@@ -393,6 +419,7 @@ static void macro(orc_state *s)
         s->phi[n] = ph;
     }
     fill_ghosts(s, s->phi);
+    if (s->p.model == 1) fill_ghosts(s, s->rho);
     compute_mu(s);
     #pragma omp parallel for schedule(static)
     for (long long n = 0; n < s->n; ++n) {
@@ -405,16 +432,25 @@ static void macro(orc_state *s)
         coords(s, n, &x, &y, &z);
         /* grad(phi) and grad(phi mu) with the isotropic lattice gradient */
         double gp[3] = {0.0, 0.0, 0.0}, gpm[3] = {0.0, 0.0, 0.0};
+        double gr[3] = {0.0, 0.0, 0.0}, grm[3] = {0.0, 0.0, 0.0};
         for (int i = 1; i < s->q; ++i) {
             long long m = stencil_nb(s, x, y, z, i);
             for (int a = 0; a < 3; ++a) {
                 gp[a] += s->w[i] * s->c[i][a] * s->phi[m];
                 gpm[a] += s->w[i] * s->c[i][a] * (s->phi[m] * s->mu[m]);
+                if (s->p.model == 1) {
+                    gr[a] += s->w[i] * s->c[i][a] * s->rho[m];
+                    grm[a] += s->w[i] * s->c[i][a] * (s->rho[m] * s->mu_rho[m]);
+                }
             }
         }
-        /* F = -phi grad(mu) = mu grad(phi) - grad(phi mu) */
+        /* F = -phi grad(mu) = mu grad(phi) - grad(phi mu); the full
+         * functional adds -rho grad(mu_rho) = mu_rho grad(rho) - grad(rho mu_rho) */
         double F[3], j[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < 3; ++a) F[a] = s->mu[n] * (gp[a] / CS2) - gpm[a] / CS2;
+        for (int a = 0; a < 3; ++a) {
+            F[a] = s->mu[n] * (gp[a] / CS2) - gpm[a] / CS2;
+            if (s->p.model == 1) F[a] += s->mu_rho[n] * (gr[a] / CS2) - grm[a] / CS2;
+        }
         for (int i = 0; i < s->q; ++i) {
             double fi = s->f[(size_t)i * s->n + n];
             for (int a = 0; a < 3; ++a) j[a] += s->c[i][a] * fi;
@@ -491,6 +527,7 @@ int orc_step(orc_state *s, int nsteps)
 static void init_equilibrium(orc_state *s)
 {
     fill_ghosts(s, s->phi);
+    if (s->p.model == 1) fill_ghosts(s, s->rho);
     compute_mu(s);
     #pragma omp parallel for schedule(static)
     for (long long n = 0; n < s->n; ++n) {
@@ -532,8 +569,18 @@ int orc_init_fields(orc_state *s, const double *rho, const double *ux,
  * Couette profile of the moving walls for the shear device, 0 otherwise. */
 int orc_init_droplet(orc_state *s, double cx, double cy, double cz, double R)
 {
-    if (!s || !(s->p.A > 0.0) || !(s->p.kappa > 0.0) || !(R > 0.0)) return -1;
-    double xi = sqrt(s->p.kappa / s->p.A);
+    if (!s || !(R > 0.0)) return -1;
+    /* interface width: tanh(x / (sqrt(2) xi)) with xi = sqrt(kappa / A); the
+     * full functional's planar profile is tanh(x / (2 alpha)), xi = sqrt(2)
+     * alpha (each component's profile has width 2 alpha, whatever kappa_k) */
+    double xi;
+    if (s->p.model == 0) {
+        if (!(s->p.A > 0.0) || !(s->p.kappa > 0.0)) return -1;
+        xi = sqrt(s->p.kappa / s->p.A);
+    } else {
+        if (!(s->p.alpha > 0.0)) return -1;
+        xi = sqrt(2.0) * s->p.alpha;
+    }
     for (long long n = 0; n < s->n; ++n) {
         int x, y, z;
         coords(s, n, &x, &y, &z);
@@ -607,8 +654,16 @@ static double nval(const nsum *a) { return a->s + a->c; }
 static double pressure(const orc_state *s, long long n)
 {
     /* bulk thermodynamic pressure cs^2 rho + phi mu - psi(phi) with
-     * psi = (A/4)(phi^2-1)^2, the bulk part of the reduced functional */
+     * psi = (A/4)(phi^2-1)^2, the bulk part of the reduced functional; the
+     * full functional: cs^2 rho + rho mu_rho + phi mu_phi - psi(rho, phi),
+     * psi = k1/32 a^2 (a-2)^2 + k2/32 b^2 (b-2)^2, a = rho + phi, b = rho - phi */
     double ph = s->phi[n];
+    if (s->p.model == 1) {
+        double a = s->rho[n] + ph, b = s->rho[n] - ph;
+        double psi = s->p.kappa1 / 32.0 * a * a * (a - 2.0) * (a - 2.0) +
+                     s->p.kappa2 / 32.0 * b * b * (b - 2.0) * (b - 2.0);
+        return CS2 * s->rho[n] + s->rho[n] * s->mu_rho[n] + ph * s->mu[n] - psi;
+    }
     double psi = 0.25 * s->p.A * (ph * ph - 1.0) * (ph * ph - 1.0);
     return CS2 * s->rho[n] + ph * s->mu[n] - psi;
 }

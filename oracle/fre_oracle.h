@@ -38,6 +38,10 @@ typedef struct {
     double u_wall;    /* shear: walls at -u_wall (bottom) / +u_wall (top);
                          four-roller: roller surface speed */
     double rho0;      /* reference density, also the wall density */
+    int model;        /* 0: reduced functional (A, kappa; force -phi grad mu);
+                         1: the full functional of Eq. functional (kappa1,
+                         kappa2, alpha; force -rho grad mu_rho - phi grad mu_phi) */
+    double kappa1, kappa2, alpha;
 } orc_params;
 
 typedef struct {

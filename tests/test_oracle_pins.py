@@ -442,12 +442,15 @@ def _fit(c, w, target, fixed=None):
     return wm * (fixed * H[:, 0] + H[:, 1:] @ x[:-1]) + x[-1] * rest
 
 
+@pytest.mark.parametrize("model", [0, 1])
 @pytest.mark.parametrize("lattice,shape", [(0, (1, 4, 4)), (1, (4, 4, 4))])
-def test_brute_force_one_step(orc, lattice, shape):
+def test_brute_force_one_step(orc, lattice, shape, model):
     """One step on a tiny periodic lattice from random positive populations,
     recomputed by an independent route: equilibria and the Guo term from
     their moment conditions by linear solves, the stencils as Fourier
-    multipliers (FFT), streaming by array rolls.  Agreement to 1e-13."""
+    multipliers (FFT), streaming by array rolls.  Agreement to 1e-13.
+    model 1: the full functional (Eq. functional, Eq. mu_rho, Eq. mu_phi)
+    with the force -rho grad(mu_rho) - phi grad(mu_phi) of Eq. F."""
     nz, ny, nx = shape
     c, _ = _lat(orc, lattice)
     q, d = c.shape[0], (2 if lattice == 0 else 3)
@@ -456,11 +459,13 @@ def test_brute_force_one_step(orc, lattice, shape):
                   for v in (c ** 2).sum(1)])
     cd = c[:, :d]
     tau_f, tau_g, A, kappa, Gamma = 0.8, 1.3, 0.03, 0.05, 0.7
+    k1, k2, alpha = 0.03, 0.07, 0.9
     rng = np.random.default_rng(5)
     f = w[:, None, None, None] * (1.0 + 0.1 * rng.uniform(-1, 1, (q,) + shape))
     g = w[:, None, None, None] * rng.uniform(-0.9, 0.9, (q,) + shape)
 
-    o = orc.Oracle(lattice, orc.PERIODIC, nx, ny, nz, tau_f, tau_g, A, kappa, Gamma, 0.0, 1.0)
+    o = orc.Oracle(lattice, orc.PERIODIC, nx, ny, nz, tau_f, tau_g, A, kappa, Gamma, 0.0, 1.0,
+                   model=model, kappa1=k1, kappa2=k2, alpha=alpha)
     o.load_populations(f, g)
     o.step(1)
     fo, go = o.populations()
@@ -475,9 +480,18 @@ def test_brute_force_one_step(orc, lattice, shape):
     lap_sym = (2 / CS2) * sum(w[i] * (phase[i] - 1) for i in range(q))
     grad_sym = [(1 / CS2) * sum(w[i] * cd[i, a] * phase[i] for i in range(q)) for a in range(d)]
     lap = np.fft.ifftn(lap_sym * np.fft.fftn(phi)).real
-    mu = A * (phi ** 3 - phi) - kappa * lap
     grad = lambda field, a: np.fft.ifftn(grad_sym[a] * np.fft.fftn(field)).real  # noqa: E731
-    F = [mu * grad(phi, a) - grad(phi * mu, a) for a in range(d)]
+    if model == 0:
+        mu = A * (phi ** 3 - phi) - kappa * lap
+        F = [mu * grad(phi, a) - grad(phi * mu, a) for a in range(d)]
+    else:
+        lap_r = np.fft.ifftn(lap_sym * np.fft.fftn(rho)).real
+        ap, bm = rho + phi, rho - phi
+        ta = k1 / 8 * ap * (ap - 2) * (ap - 1)
+        tb = k2 / 8 * bm * (bm - 2) * (bm - 1)
+        mu_r = ta + tb + alpha ** 2 / 4 * (-(k1 + k2) * lap_r + (k2 - k1) * lap)
+        mu = ta - tb + alpha ** 2 / 4 * (-(k1 + k2) * lap + (k2 - k1) * lap_r)
+        F = [mu * grad(phi, a) - grad(phi * mu, a) + mu_r * grad(rho, a) - grad(rho * mu_r, a) for a in range(d)]
     u = [(sum(cd[i, a] * f[i] for i in range(q)) + 0.5 * F[a]) / rho for a in range(d)]
 
     f_new = np.empty_like(f)
@@ -507,6 +521,111 @@ def test_brute_force_one_step(orc, lattice, shape):
         g_new[i] = np.roll(post_g[i], shift, axis=(0, 1, 2))
     assert np.abs(fo - f_new).max() < 1e-13
     assert np.abs(go - g_new).max() < 1e-13
+
+
+# ---------------------------------------------- the full functional
+
+def test_full_functional_reduces_to_the_reduced_one(orc):
+    """Eq. mu_phi with kappa_1 = kappa_2 = kappa_p and rho = 1 is the reduced
+    chemical potential A(phi^3 - phi) - kappa lap(phi) with A = kappa_p / 4,
+    kappa = alpha^2 kappa_p / 2, and mu_rho vanishes, so the force of Eq. F
+    is the reduced one: on a random phi field with rho = 1 the two models
+    give the same mu and, one step later, the same populations."""
+    kp, alpha = 0.08, 0.9
+    shape = (1, 12, 16)
+    rng = np.random.default_rng(21)
+    phi = np.tanh(2.0 * rng.uniform(-1, 1, shape))
+    z = np.zeros(shape)
+    red = orc.Oracle(0, orc.PERIODIC, 16, 12, 1, 0.9, 1.1, kp / 4, alpha ** 2 * kp / 2, 0.6, 0.0, 1.0)
+    full = orc.Oracle(0, orc.PERIODIC, 16, 12, 1, 0.9, 1.1, 0.0, 0.0, 0.6, 0.0, 1.0, model=1, kappa1=kp,
+                      kappa2=kp, alpha=alpha)
+    for o in (red, full):
+        o.init_fields(np.ones(shape), z, z, z, phi)
+    assert np.abs(red.fields()["mu"] - full.fields()["mu"]).max() < 1e-15
+    for o in (red, full):
+        o.step(1)
+    (fr, gr), (ff, gf) = red.populations(), full.populations()
+    assert np.abs(fr - ff).max() < 1e-15 and np.abs(gr - gf).max() < 1e-15
+
+
+def _slab_full(orc, alpha, k1, k2, steps):
+    L = int(48 * alpha)
+    o = orc.Oracle(0, orc.PERIODIC, L, 1, 1, 1.0, 1.0, 0.0, 0.0, 1.0, 0.0, 1.0, model=1, kappa1=k1, kappa2=k2,
+                   alpha=alpha)
+    x = np.arange(L)
+    x1, x2 = L / 4 - 0.5, 3 * L / 4 - 0.5
+    prof = np.tanh((x - x1) / (2 * alpha)) * -np.tanh((x - x2) / (2 * alpha))
+    init = prof[None, None, :]
+    z = np.zeros_like(init)
+    o.init_fields(np.ones_like(init), z, z, z, init)
+    o.step(steps)
+    fl = o.fields()
+    ph, rho = fl["phi"][0, 0], fl["rho"][0, 0]
+    a, b = rho + ph, rho - ph
+    da = (np.roll(a, -1) - np.roll(a, 1)) / 2
+    db = (np.roll(b, -1) - np.roll(b, 1)) / 2
+    # excess free energy per interface of Eq. functional (its bulk states,
+    # C_k = 0 or 1, carry none)
+    dens = (k1 / 32 * a ** 2 * (a - 2) ** 2 + alpha ** 2 * k1 / 8 * da ** 2 +
+            k2 / 32 * b ** 2 * (b - 2) ** 2 + alpha ** 2 * k2 / 8 * db ** 2)
+    return np.abs(ph - prof).max(), np.abs(rho - 1).max(), dens.sum() / 2 / (alpha * (k1 + k2) / 6) - 1
+
+
+def test_full_functional_flat_interface(orc):
+    """Eq. functional splits into one term per component C_k = (rho +- phi)/2,
+    (kappa_k / 2)[C_k^2 (C_k - 1)^2 + alpha^2 |grad C_k|^2], each minimised
+    by C_k = (1 +- tanh(x / (2 alpha)))/2 whatever kappa_k: a planar
+    interface with kappa_1 != kappa_2 relaxes to phi = tanh(x / (2 alpha))
+    (xi = sqrt(2) alpha) with rho = 1, and its excess free energy is
+    sigma = alpha (kappa_1 + kappa_2) / 6.  kappa_2 = 3 kappa_1, alpha = 1, 2,
+    4 at fixed alpha^2 (kappa_1 + kappa_2) = 0.08: the profile error shrinks
+    like alpha^-2, sigma to within 0.5%."""
+    res = [_slab_full(orc, al, 0.02 / al ** 2, 0.06 / al ** 2, int(1500 * al * al)) for al in (1.0, 2.0, 4.0)]
+    errs = [r[0] for r in res]
+    assert errs[0] < 0.02 and errs[1] < errs[0] / 3.5 and errs[2] < errs[1] / 3.5
+    assert all(r[1] < 1e-4 for r in res)
+    assert abs(res[0][2]) < 0.05 and abs(res[2][2]) < 0.005
+
+
+def test_full_functional_laplace_law(orc):
+    """Static 2D droplets of the full functional (kappa_1 = 0.04, kappa_2 =
+    0.12, alpha = 1/sqrt 2, so xi = 1): the slope of dp against 1/R_eff is
+    sigma = alpha (kappa_1 + kappa_2) / 6 within 5%; dp is the bulk pressure
+    cs^2 rho + rho mu_rho + phi mu_phi - psi(rho, phi) at the centroid minus
+    far away."""
+    k1, k2, alpha = 0.04, 0.12, 0.5 ** 0.5
+    sig = alpha * (k1 + k2) / 6
+    inv_r, dps = [], []
+    for R in (12, 16, 20, 24):
+        N = max(48, 4 * R)
+        o = orc.Oracle(0, orc.PERIODIC, N, N, 1, 1.0, 1.0, 0.0, 0.0, 1.0, 0.0, 1.0, model=1, kappa1=k1, kappa2=k2,
+                       alpha=alpha)
+        o.init_droplet((N - 1) / 2, (N - 1) / 2, 0, R)
+        o.step(12000)
+        ob = o.observables()
+        ph = o.fields()["phi"]
+        out, inn = ph[0, 0, 0], ph[0, N // 2, N // 2]
+        inv_r.append(1 / np.sqrt(np.sum((ph - out) / (inn - out)) / np.pi))
+        dps.append(ob["dp"])
+        assert ob["status"] == 0 and ob["max_u"] < 1e-4
+    slope = np.polyfit(inv_r, dps, 1)[0]
+    assert abs(slope / sig - 1) < 0.05, slope / sig
+
+
+@pytest.mark.parametrize("lattice,shape,R", [(0, (1, 24, 48), 6.0), (1, (8, 12, 16), 3.5)])
+def test_full_functional_conservation(orc, lattice, shape, R):
+    """Sum rho and sum phi stay collision invariants with the full force:
+    relative drift < 1e-12 over 10^4 steps in the shear device."""
+    nz, ny, nx = shape
+    o = orc.Oracle(lattice, orc.SHEAR, nx, ny, nz, 1.0, 1.0, 0.0, 0.0, 1.0, 0.02, 1.0, model=1, kappa1=0.03,
+                   kappa2=0.09, alpha=0.8)
+    o.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, R)
+    a = o.observables()
+    o.step(10000)
+    b = o.observables()
+    assert b["status"] == 0
+    assert abs(b["mass"] - a["mass"]) / a["mass"] < 1e-12
+    assert abs(b["phi_sum"] - a["phi_sum"]) / (nx * ny * nz) < 1e-12
 
 
 # ------------------------------------------- four-roller links, one step
