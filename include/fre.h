@@ -91,6 +91,18 @@ typedef struct {
     double rho0;       /* reference density; also the wall density of the
                           moving bounce-back term */
     unsigned flags;    /* FRE_FLAG_* bits, 0 by default */
+    /* Free-energy model.  0 (default): the reduced functional of A and kappa
+     * above, mu = A(phi^3 - phi) - kappa lap(phi), force -phi grad(mu).
+     * 1: the paper's full functional (Eq. functional) of kappa1, kappa2 and
+     * alpha, with mu_rho and mu_phi (Eq. mu_rho, Eq. mu_phi) and the force
+     * -rho grad(mu_rho) - phi grad(mu_phi) (Eq. F); A and kappa are then
+     * unused.  Its planar interface is tanh(x / (2 alpha)) (xi = sqrt(2)
+     * alpha) and its interface tension alpha (kappa1 + kappa2) / 6; with
+     * kappa1 = kappa2 = kappa_p it reduces to model 0 with A = kappa_p / 4,
+     * kappa = alpha^2 kappa_p / 2 at rho = 1.  Model 1 runs on the per-node
+     * kernels and is not taken by batches and servers. */
+    int model;
+    double kappa1, kappa2, alpha;
 } fre_params;
 
 /* Force the per-node kernels even where the row kernels apply (the row
@@ -166,10 +178,11 @@ size_t fre_device_bytes(const fre_params *p);
 fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out);
 
 /* Initialise a droplet phi = tanh((R - |x - c|)/(sqrt(2) xi)), xi =
- * sqrt(kappa/A) (the planar profile of Sec. 2.2 applied radially), rho =
- * rho0, u = the Couette profile u_x = u_wall (2(y + 1/2)/ny - 1) for the
- * shear device and 0 otherwise, mu from phi, and f = f_eq, g = g_eq
- * (Sec. 2.3).  In 2D cz is ignored.  Needs A > 0, kappa > 0, R > 0. */
+ * sqrt(kappa/A) (model 1: sqrt(2) alpha; the planar profile of Sec. 2.2
+ * applied radially), rho = rho0, u = the Couette profile u_x = u_wall (2(y +
+ * 1/2)/ny - 1) for the shear device and 0 otherwise, mu from phi, and f =
+ * f_eq, g = g_eq (Sec. 2.3).  In 2D cz is ignored.  Needs R > 0 and A > 0,
+ * kappa > 0 (model 1: alpha > 0). */
 fre_status fre_init_droplet(fre_ctx *c, double cx, double cy, double cz, double R);
 
 /* Initialise from host FP64 fields (n values each; uz may be NULL in 2D):

@@ -55,7 +55,8 @@ class fre_params(C.Structure):
                 ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("tau_f", C.c_double), ("tau_g", C.c_double), ("A", C.c_double),
                 ("kappa", C.c_double), ("gamma_mob", C.c_double), ("u_wall", C.c_double),
-                ("rho0", C.c_double), ("flags", C.c_uint)]
+                ("rho0", C.c_double), ("flags", C.c_uint),
+                ("model", C.c_int), ("kappa1", C.c_double), ("kappa2", C.c_double), ("alpha", C.c_double)]
 
 
 class fre_obs(C.Structure):
@@ -212,12 +213,13 @@ def current_stream_handle():
 
 def make_params(lattice="d2q9", precision="fp64", device="shear", nx=16, ny=8, nz=1,
                 tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0,
-                rho0=1.0, flags=0) -> fre_params:
+                rho0=1.0, flags=0, model=0, kappa1=0.0, kappa2=0.0, alpha=0.0) -> fre_params:
     lat = LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     dev = DEVICES[device] if isinstance(device, str) else int(device)
     return fre_params(lat, prec, dev, int(nx), int(ny), int(nz), float(tau_f), float(tau_g),
-                      float(A), float(kappa), float(gamma_mob), float(u_wall), float(rho0), int(flags))
+                      float(A), float(kappa), float(gamma_mob), float(u_wall), float(rho0), int(flags),
+                      int(model), float(kappa1), float(kappa2), float(alpha))
 
 
 # --------------------------------------------------- one call per C entry point

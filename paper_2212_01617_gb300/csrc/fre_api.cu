@@ -41,6 +41,7 @@ struct Sizes {
     int q, sz_store, sz_comp;
     long long n, np;
     size_t buf_bytes, field_bytes, solid_bytes;
+    int model;  // 1: two more fields (rho, mu_rho)
 };
 
 bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
@@ -60,6 +61,10 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
     if (!(p->A >= 0.0) || !(p->kappa >= 0.0)) return bad("A and kappa must be >= 0");
     if (!std::isfinite(p->gamma_mob) || !std::isfinite(p->u_wall) || !(p->rho0 > 0.0))
         return bad("gamma_mob and u_wall must be finite, rho0 > 0");
+    if (p->model != 0 && p->model != 1) return bad("unknown free-energy model (0 or 1)");
+    if (p->model == 1 && !(p->kappa1 >= 0.0 && p->kappa2 >= 0.0 && p->alpha >= 0.0 && std::isfinite(p->kappa1) &&
+                           std::isfinite(p->kappa2) && std::isfinite(p->alpha)))
+        return bad("model 1 needs finite kappa1, kappa2, alpha >= 0");
     if (p->device == FRE_FOUR_ROLLER && (p->nx < 8 || p->ny < 8)) return bad("four-roller needs nx, ny >= 8");
     long long n = (long long)p->nx * p->ny * p->nz;
     if (n > (1LL << 30)) return bad("too many nodes (limit 2^30)");
@@ -80,7 +85,8 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
         s.buf_bytes = (size_t)s.q * plane + (size_t)(s.q - 1) * plane + (size_t)s.np * 4;
     }
     s.field_bytes = (size_t)s.np * s.sz_comp;
-    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) + 4 * (size_t)p->nx * p->ny : 0;
+    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) + 8 * (size_t)p->nx * p->ny : 0;
+    s.model = p->model;
     return true;
 }
 
@@ -92,8 +98,8 @@ constexpr int kCclCap = 4096;
 size_t ccl_bytes(const Sizes &s) { return 2 * sizeof(int) * (size_t)s.n + 16 * (size_t)kCclCap + 256; }
 
 size_t total_bytes(const Sizes &s) {
-    return 2 * s.buf_bytes + 3 * s.field_bytes + s.solid_bytes + sizeof(double) * fre::kRedDoublesHost +
-           sizeof(fre_obs) + ccl_bytes(s);
+    return 2 * s.buf_bytes + (3 + 2 * s.model) * s.field_bytes + s.solid_bytes +
+           sizeof(double) * fre::kRedDoublesHost + sizeof(fre_obs) + ccl_bytes(s);
 }
 
 fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
@@ -151,20 +157,30 @@ void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<in
                                    {-1, 0, -1}, {0, 1, 1},  {0, -1, -1}, {1, -1, 0}, {-1, 1, 0},
                                    {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1}};
     auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
-    links.assign((size_t)p.nx * p.ny, 0u);
+    links.assign(2 * (size_t)p.nx * p.ny, 0u);
     for (int y = 0; y < p.ny; ++y)
         for (int x = 0; x < p.nx; ++x) {
-            unsigned w = 0;
+            unsigned w = 0, sel = 0;
+            int ka = 0, kb = 0;
             if (solid[(size_t)y * p.nx + x]) {
                 w = 1u << 30;
             } else {
                 for (int i = 1; i < q; ++i) {
                     const int *ci = q == 9 ? c9[i] : c19[i];
                     const int k = solid[(size_t)wrap(y - ci[1], p.ny) * p.nx + wrap(x - ci[0], p.nx)];
-                    if (k) w |= (1u << i) | ((unsigned)k << 24);
+                    if (!k) continue;
+                    w |= 1u << i;
+                    if (!ka || k == ka) {
+                        ka = k;
+                    } else {
+                        kb = k;  // a node's links reach at most two rollers
+                        sel |= 1u << i;
+                    }
                 }
             }
-            links[(size_t)y * p.nx + x] = w;
+            const size_t m = 2 * ((size_t)y * p.nx + x);
+            links[m] = w;
+            links[m + 1] = sel | ((unsigned)ka << 24) | ((unsigned)kb << 28);
         }
     ghost.clear();
     for (int z = 0; z < p.nz; ++z)
@@ -209,6 +225,8 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.phi_prev = c->phi[c->pp];
     L.phi = c->phi[1 - c->pp];
     L.mu = c->mu;
+    L.rhof = c->rhof;
+    L.murho = c->murho;
     L.ghost = c->ghost;
     L.n_ghost = c->n_ghost;
     L.red = c->red;
@@ -244,9 +262,9 @@ void fre::ctx_launch_step(fre_ctx *c) {
         c->ks->update_rows(L, pull);
     } else {
         c->ks->phi(L, pull);
-        if (c->n_ghost) c->ks->ghost(L, L.phi);
+        if (c->n_ghost) fre::ghost_fields(c, L, false);
         c->ks->mu(L);
-        if (c->n_ghost) c->ks->ghost(L, L.mu);
+        if (c->n_ghost) fre::ghost_fields(c, L, true);
         c->ks->update(L, pull);
     }
     c->cur ^= 1;
@@ -255,9 +273,16 @@ void fre::ctx_launch_step(fre_ctx *c) {
     c->step++;
 }
 
+// Stencil values at the roller solids: phi (and rho, model 1) after the phi
+// pass, mu (and mu_rho) after the mu pass.
+void fre::ghost_fields(fre_ctx *c, const Launch &L, bool mu_pass) {
+    c->ks->ghost(L, mu_pass ? L.mu : L.phi);
+    if (c->P.model == 1) c->ks->ghost(L, mu_pass ? L.murho : L.rhof);
+}
+
 bool fre::same_geometry(const fre_params *p, const fre_params *q) {
     return p->lattice == q->lattice && p->precision == q->precision && p->device == q->device && p->nx == q->nx &&
-           p->ny == q->ny && p->nz == q->nz && p->flags == q->flags;
+           p->ny == q->ny && p->nz == q->nz && p->flags == q->flags && p->model == q->model;
 }
 
 fre_status fre::ctx_reparam(fre_ctx *c, const fre_params *p) {
@@ -268,7 +293,7 @@ fre_status fre::ctx_reparam(fre_ctx *c, const fre_params *p) {
     if (!sizes_of(p, s, &why)) return fail(FRE_ERR_ARG, "ctx_reparam: %s", why.c_str());
     c->p = *p;
     c->G.uwall = p->u_wall;
-    c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0};
+    c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0, p->model, p->kappa1, p->kappa2, p->alpha};
     c->initialised = false;
     return FRE_OK;
 }
@@ -280,9 +305,9 @@ fre::Launch launch_of(fre_ctx *c) { return fre::ctx_launch(c); }
 // phi and mu of the current state into phi[1 - pp] and mu.
 void current_phi_mu(fre_ctx *c, const fre::Launch &L) {
     c->ks->phi(L, !c->local);
-    if (c->n_ghost) c->ks->ghost(L, L.phi);
+    if (c->n_ghost) fre::ghost_fields(c, L, false);
     c->ks->mu(L);
-    if (c->n_ghost) c->ks->ghost(L, L.mu);
+    if (c->n_ghost) fre::ghost_fields(c, L, true);
 }
 
 fre_status check_launch(const char *where) {
@@ -338,9 +363,9 @@ fre_status finish_init(fre_ctx *c, int from_staging) {
     c->cur = 0;
     c->pp = 1;
     fre::Launch L = launch_of(c);  // phi = phi[0], src = buf[0]
-    if (c->n_ghost) c->ks->ghost(L, L.phi);
+    if (c->n_ghost) fre::ghost_fields(c, L, false);
     c->ks->mu(L);
-    if (c->n_ghost) c->ks->ghost(L, L.mu);
+    if (c->n_ghost) fre::ghost_fields(c, L, true);
     c->ks->init_eq(L, from_staging);
     fre_status s = check_launch("init");
     if (s != FRE_OK) return s;
@@ -400,7 +425,7 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     c->G.n = s.n;
     c->G.np = s.np;
     c->G.uwall = p->u_wall;
-    c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0};
+    c->P = {p->tau_f, p->tau_g, p->A, p->kappa, p->gamma_mob, p->rho0, p->model, p->kappa1, p->kappa2, p->alpha};
 
     const bool dev16 = p->precision == FRE_FP16DEV || p->precision == FRE_BF16DEV;
     const size_t plane = (size_t)s.np * s.sz_store;
@@ -420,6 +445,12 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     {
         fre_status st = dev_alloc(c, &c->mu, s.field_bytes);
         if (st != FRE_OK) return bail(st);
+        if (p->model == 1) {
+            st = dev_alloc(c, &c->rhof, s.field_bytes);
+            if (st != FRE_OK) return bail(st);
+            st = dev_alloc(c, &c->murho, s.field_bytes);
+            if (st != FRE_OK) return bail(st);
+        }
         void *r;
         st = dev_alloc(c, &r, sizeof(double) * fre::kRedDoublesHost);
         if (st != FRE_OK) return bail(st);
@@ -472,13 +503,14 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     }
     c->G.solid = c->solid;
     c->G.links = c->links;
-    if (!(p->flags & FRE_FLAG_GENERIC_KERNELS) && c->ks->row_width) {
+    // the full functional (model 1) runs on the per-node kernels
+    if (!(p->flags & FRE_FLAG_GENERIC_KERNELS) && p->model == 0 && c->ks->row_width) {
         const unsigned sh = (p->flags >> FRE_FLAG_CHUNK_SHIFT) & 0xffu;
         c->row_w = c->ks->row_width(c->G, sh ? (1 << sh) : 0);
         c->rows = c->row_w > 0;
     }
     // the four-roller device has no chunked row kernels, only full rows
-    c->fullrow = !(p->flags & FRE_FLAG_GENERIC_KERNELS) && (c->rows || p->device == FRE_FOUR_ROLLER) &&
+    c->fullrow = !(p->flags & FRE_FLAG_GENERIC_KERNELS) && p->model == 0 && (c->rows || p->device == FRE_FOUR_ROLLER) &&
                  !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable && c->ks->fullrow_usable(c->G);
     cudaGetLastError();
     *out = c;
@@ -488,7 +520,9 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
 fre_status fre_init_droplet(fre_ctx *c, double cx, double cy, double cz, double R) {
     fre_status s = enter(c);
     if (s != FRE_OK) return s;
-    if (!(c->p.A > 0.0) || !(c->p.kappa > 0.0)) return fail(FRE_ERR_ARG, "fre_init_droplet needs A > 0, kappa > 0");
+    if (c->p.model == 0 && (!(c->p.A > 0.0) || !(c->p.kappa > 0.0)))
+        return fail(FRE_ERR_ARG, "fre_init_droplet needs A > 0, kappa > 0");
+    if (c->p.model == 1 && !(c->p.alpha > 0.0)) return fail(FRE_ERR_ARG, "fre_init_droplet needs alpha > 0");
     if (!(R > 0.0) || !std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(cz))
         return fail(FRE_ERR_ARG, "fre_init_droplet: R must be > 0 and the centre finite");
     c->cur = 0;
@@ -636,12 +670,12 @@ fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launche
         else c->ks->phi(L, pull);
         ++nl;
         cudaEventRecord(ev[3 * t + 1], c->stream);
-        if (c->n_ghost) { c->ks->ghost(L, L.phi); ++nl; }
+        if (c->n_ghost) { fre::ghost_fields(c, L, false); nl += 1 + c->P.model; }
         if (full) c->ks->mu_fullrow(L);
         else if (c->rows) c->ks->mu_rows(L);
         else c->ks->mu(L);
         ++nl;
-        if (c->n_ghost) { c->ks->ghost(L, L.mu); ++nl; }
+        if (c->n_ghost) { fre::ghost_fields(c, L, true); nl += 1 + c->P.model; }
         cudaEventRecord(ev[3 * t + 2], c->stream);
         if (full) c->ks->update_fullrow(L, pull);
         else if (c->rows) c->ks->update_rows(L, pull);

@@ -18,6 +18,7 @@ struct fre_ctx {
     fre::Buf buf[2]{};
     void *phi[2]{};
     void *mu = nullptr;
+    void *rhof = nullptr, *murho = nullptr;  // model 1: rho and mu_rho fields
     unsigned char *solid = nullptr;
     unsigned *links = nullptr;  // four-roller: wall-link words per (x, y)
     int *ghost = nullptr;
@@ -45,6 +46,9 @@ namespace fre {
 Launch ctx_launch(fre_ctx *c);
 // the kernels of one time step on the context stream; advances the state
 void ctx_launch_step(fre_ctx *c);
+// roller ghost fills of the stencil fields after the phi pass (mu_pass
+// false) or the mu pass
+void ghost_fields(fre_ctx *c, const Launch &L, bool mu_pass);
 // give a context new physical parameters of the same geometry (lattice,
 // precision, device, sizes and flags equal); the state must be
 // re-initialised before the next step

@@ -17,7 +17,7 @@ struct Geo {
     long long n;              // nodes
     long long np;             // plane stride of the population arrays (elements)
     const unsigned char *solid;  // roller id per node (0 = fluid); four-roller only
-    const unsigned *links;    // four-roller: wall-link word per (x, y) for the row kernels
+    const unsigned *links;    // four-roller: wall-link word pair per (x, y) for the row kernels
     double rcx[5], rcy[5], om[5];  // roller centres and angular velocities (1..4)
     double uwall;             // shear wall speed
 };
@@ -25,6 +25,8 @@ struct Geo {
 // Physical parameters of the scheme (Sec. 2.2).
 struct Phys {
     double tau_f, tau_g, A, kappa, Gamma, rho0;
+    int model;  // 0 reduced functional; 1 the full functional of kappa1, kappa2, alpha
+    double kappa1, kappa2, alpha;
 };
 
 // FP32 copies of the per-launch constants of the FP32-compute kernels,
@@ -57,7 +59,9 @@ struct Launch {
     Buf src, dst;
     const void *phi_prev;  // phi at the previous step (moving-wall term of g)
     void *phi;             // phi at the current step
-    void *mu;              // mu at the current step
+    void *mu;              // mu at the current step (model 1: mu_phi)
+    void *rhof;            // model 1: rho at the current step
+    void *murho;           // model 1: mu_rho at the current step
     const int *ghost;      // roller solid nodes with fluid neighbours
     int n_ghost;
     double *red;           // reduction scratch

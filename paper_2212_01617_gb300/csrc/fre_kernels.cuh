@@ -373,6 +373,26 @@ __device__ __forceinline__ Macro<typename Fmt<FMT>::T> macro_of(const Launch &L,
     m.Fx = T(3) * (mu * gpx - gqx);
     m.Fy = T(3) * (mu * gpy - gqy);
     m.Fz = T(3) * (mu * gpz - gqz);
+    if (L.P.model == 1) {
+        // full functional: -rho grad(mu_rho) = mu_rho grad(rho) - grad(rho mu_rho)
+        const T *__restrict__ rf = static_cast<const T *>(L.rhof);
+        const T *__restrict__ mr = static_cast<const T *>(L.murho);
+        T grx = T(0), gry = T(0), grz = T(0), gsx = T(0), gsy = T(0), gsz = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int k = site_nb<Q>(s, i);
+            const T r = rf[k];
+            const T rm = r * mr[k];
+            const T w = T(Lat<Q>::w(i));
+            if (Lat<Q>::cx(i)) { grx += w * T(Lat<Q>::cx(i)) * r; gsx += w * T(Lat<Q>::cx(i)) * rm; }
+            if (Lat<Q>::cy(i)) { gry += w * T(Lat<Q>::cy(i)) * r; gsy += w * T(Lat<Q>::cy(i)) * rm; }
+            if (Lat<Q>::cz(i)) { grz += w * T(Lat<Q>::cz(i)) * r; gsz += w * T(Lat<Q>::cz(i)) * rm; }
+        }
+        const T mur = mr[s.n];
+        m.Fx += T(3) * (mur * grx - gsx);
+        m.Fy += T(3) * (mur * gry - gsy);
+        m.Fz += T(3) * (mur * grz - gsz);
+    }
     const T inv = T(1) / rho;
     m.ux = (jx + T(0.5) * m.Fx) * inv;
     m.uy = (jy + T(0.5) * m.Fy) * inv;
@@ -400,11 +420,21 @@ static_assert(kBX * kBY == kBlock, "block shape");
     const Site s = make_site((L).G, x_, y_, z_)
 
 // phi = sum of the pulled g at one node
+// (the full functional, model 1, also writes rho = sum of the pulled f)
 template <int Q, int FMT, bool PULL>
 __device__ __forceinline__ void node_phi(const Launch &L, const Site &s) {
     using T = typename Fmt<FMT>::T;
     T g[Q];
-    gather<Q, FMT, PULL, false>(L, s, nullptr, g);
+    if (L.P.model == 1) {
+        T f[Q];
+        gather<Q, FMT, PULL, true>(L, s, f, g);
+        T r = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) r += f[i];
+        static_cast<T *>(L.rhof)[s.n] = r;
+    } else {
+        gather<Q, FMT, PULL, false>(L, s, nullptr, g);
+    }
     T ph = T(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) ph += g[i];
@@ -443,6 +473,13 @@ __global__ void __launch_bounds__(kBlock) k_ghost(Launch L, T *field) {
 }
 
 // mu = A (phi^3 - phi) - kappa lap(phi), lap = (2/cs^2) sum w_i (phi(x+c_i) - phi(x))
+// Full functional (model 1, Eq. mu_rho and Eq. mu_phi), a = rho + phi,
+// b = rho - phi:
+//   mu_rho = k1/8 a(a-2)(a-1) + k2/8 b(b-2)(b-1)
+//            + alpha^2/4 [-(k1 + k2) lap(rho) + (k2 - k1) lap(phi)],
+//   mu_phi = k1/8 a(a-2)(a-1) - k2/8 b(b-2)(b-1)
+//            + alpha^2/4 [-(k1 + k2) lap(phi) + (k2 - k1) lap(rho)];
+// mu_phi goes to L.mu, mu_rho to L.murho.
 template <int Q, typename T>
 __device__ __forceinline__ void node_mu(const Launch &L, const Site &s) {
     const T *__restrict__ phi = static_cast<const T *>(L.phi);
@@ -451,6 +488,21 @@ __device__ __forceinline__ void node_mu(const Launch &L, const Site &s) {
 #pragma unroll
     for (int i = 1; i < Q; ++i) lap += T(Lat<Q>::w(i)) * (phi[site_nb<Q>(s, i)] - p0);
     lap *= T(6);
+    if (L.P.model == 1) {
+        const T *__restrict__ rho = static_cast<const T *>(L.rhof);
+        const T r0 = rho[s.n];
+        T lapr = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) lapr += T(Lat<Q>::w(i)) * (rho[site_nb<Q>(s, i)] - r0);
+        lapr *= T(6);
+        const T k1 = T(L.P.kappa1), k2 = T(L.P.kappa2), al2 = T(L.P.alpha * L.P.alpha);
+        const T a = r0 + p0, b = r0 - p0;
+        const T ta = k1 / T(8) * a * (a - T(2)) * (a - T(1));
+        const T tb = k2 / T(8) * b * (b - T(2)) * (b - T(1));
+        static_cast<T *>(L.murho)[s.n] = ta + tb + al2 / T(4) * (-(k1 + k2) * lapr + (k2 - k1) * lap);
+        static_cast<T *>(L.mu)[s.n] = ta - tb + al2 / T(4) * (-(k1 + k2) * lap + (k2 - k1) * lapr);
+        return;
+    }
     const T A = sizeof(T) == 4 ? T(L.F.A) : T(L.P.A), kappa = sizeof(T) == 4 ? T(L.F.kappa) : T(L.P.kappa);
     static_cast<T *>(L.mu)[s.n] = A * (p0 * p0 * p0 - p0) - kappa * lap;
 }
@@ -613,13 +665,17 @@ __global__ void __launch_bounds__(kBlock) k_set_phi(Launch L, int analytic, doub
         phi[s.n] = T(0);
         return;
     }
+    if (L.P.model == 1)
+        static_cast<T *>(L.rhof)[s.n] = analytic ? T(L.P.rho0) : T(L.staging[s.n]);
     if (!analytic) {
         phi[s.n] = T(L.staging[4 * L.G.n + s.n]);
         return;
     }
     double dx = s.x - cx, dy = s.y - cy, dz = (Lat<Q>::D == 3) ? s.z - cz : 0.0;
     double r = sqrt(dx * dx + dy * dy + dz * dz);
-    double xi = sqrt(L.P.kappa / L.P.A);
+    // interface width: xi = sqrt(kappa / A); the full functional's planar
+    // profile tanh(x / (2 alpha)) has xi = sqrt(2) alpha
+    double xi = L.P.model == 1 ? sqrt(2.0) * L.P.alpha : sqrt(L.P.kappa / L.P.A);
     phi[s.n] = T(tanh((R - r) / (sqrt(2.0) * xi)));
 }
 
@@ -923,6 +979,15 @@ __device__ double pressure_at(const Launch &L, int x, int y, int z) {
     for (int i = 0; i < Q; ++i) rho += (double)f[i];
     const double ph = static_cast<const T *>(L.phi)[s.n];
     const double mu = static_cast<const T *>(L.mu)[s.n];
+    if (L.P.model == 1) {
+        // cs^2 rho + rho mu_rho + phi mu_phi - psi, psi the bulk part of
+        // Eq. functional: k1/32 a^2 (a-2)^2 + k2/32 b^2 (b-2)^2
+        const double mur = static_cast<const T *>(L.murho)[s.n];
+        const double a = rho + ph, b = rho - ph;
+        const double psi = L.P.kappa1 / 32.0 * a * a * (a - 2.0) * (a - 2.0) +
+                           L.P.kappa2 / 32.0 * b * b * (b - 2.0) * (b - 2.0);
+        return rho / 3.0 + rho * mur + ph * mu - psi;
+    }
     return rho / 3.0 + ph * mu - 0.25 * L.P.A * (ph * ph - 1.0) * (ph * ph - 1.0);
 }
 

@@ -212,7 +212,8 @@ fre_status fre_server_submit(fre_server *s, const fre_params *p, double cx, doub
     if (!s || !p || !id) return sfail(FRE_ERR_ARG, "fre_server_submit: NULL argument");
     if (p->lattice != s->lattice || p->precision != s->precision)
         return sfail(FRE_ERR_ARG, "fre_server_submit: lattice and precision must match the server");
-    const size_t bytes = (R > 0.0 && std::isfinite(cx) && std::isfinite(cy) && std::isfinite(cz))
+    // a request of the full functional (model 1) is rejected: the batch runs model 0
+    const size_t bytes = (R > 0.0 && std::isfinite(cx) && std::isfinite(cy) && std::isfinite(cz) && p->model == 0)
                              ? fre_device_bytes(p) : 0;
     const long long nodes = (long long)p->nx * p->ny * p->nz;
     *id = s->policy.submit(nodes, bytes, s->now());

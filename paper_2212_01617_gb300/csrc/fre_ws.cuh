@@ -469,10 +469,10 @@ struct RowsLayout {
         if (KIND == WS_UPDATE) return fld_off(nx) + 2 * NFIELD * fldb(nx);
         return base_tx(nx);
     }
-    // four-roller device: the wall-link words (one uint32 per node) of the
+    // four-roller device: the wall-link words (two uint32 per node) of the
     // unit's R rows, after everything else
     __host__ __device__ static unsigned lnk_off(int nx) { return (base_bytes(nx) + 15u) / 16u * 16u; }
-    __host__ __device__ static unsigned lnk_bytes(int nx) { return ROLL ? (unsigned)(R * nx * 4) : 0u; }
+    __host__ __device__ static unsigned lnk_bytes(int nx) { return ROLL ? (unsigned)(R * nx * 8) : 0u; }
     __host__ __device__ static unsigned tx_bytes(int nx) { return base_tx(nx) + lnk_bytes(nx); }
     __host__ __device__ static unsigned bytes(int nx) { return ROLL ? lnk_off(nx) + lnk_bytes(nx) : base_bytes(nx); }
     __host__ __device__ static unsigned stage(int nx) { return (bytes(nx) + 127u) / 128u * 128u; }
@@ -482,11 +482,13 @@ struct RowsLayout {
     }
 };
 
-// Wall-link word of a node of the four-roller device (host-built table
-// [ny][nx], the same in every z plane since the rollers are extruded
-// along z): bit i (i < q) is set when the source x - c_i of population i
-// is a roller node; bits 24..26 hold that roller's number (one roller
-// borders a node); bit 30 marks a roller (solid) node itself.
+// Wall-link words of a node of the four-roller device (host-built table
+// [ny][nx] of word pairs, the same in every z plane since the rollers are
+// extruded along z).  Word 0: bit i (i < q) is set when the source x - c_i
+// of population i is a roller node; bit 30 marks a roller (solid) node
+// itself.  Word 1: the rollers a node's links reach (at most two, where
+// rollers nearly touch): bits 24..26 roller A, 28..30 roller B, and bit i
+// set when link i reaches B rather than A.
 constexpr unsigned kLinkSolid = 1u << 30;
 
 
@@ -759,7 +761,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
             for (int gi = lane; gi < FL::ngroups(); gi += 32) {
                 if (ROLL && gi == FL::ngroups() - 1) {
                     // the link words of the unit's rows (contiguous in the table)
-                    bulk_load(buf + FL::lnk_off(nx), L.G.links + (size_t)y0 * nx, FL::lnk_bytes(nx), bar);
+                    bulk_load(buf + FL::lnk_off(nx), L.G.links + 2 * (size_t)y0 * nx, FL::lnk_bytes(nx), bar);
                     continue;
                 }
                 if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q)) {
@@ -927,8 +929,9 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 const size_t row = ((size_t)z * ny + y) * nx;
                 const Site st = make_site(L.G, x0, y, z);
                 // four-roller: the wall-link words of the pair's nodes
-                const uint2 lw = ROLL ? *reinterpret_cast<const uint2 *>(cur + FL::lnk_off(nx) + ((size_t)r * nx + x0) * 4)
-                                      : make_uint2(0u, 0u);
+                const uint4 lk = ROLL ? *reinterpret_cast<const uint4 *>(cur + FL::lnk_off(nx) + ((size_t)r * nx + x0) * 8)
+                                      : make_uint4(0u, 0u, 0u, 0u);
+                const uint2 lw = make_uint2(lk.x, lk.z);
                 const bool lany = ROLL && ((lw.x | lw.y) & ((1u << Q) - 1u)) != 0u;
                 // store a pair; the four-roller device leaves the slots of
                 // its roller nodes alone (they hold the populations its wall
@@ -952,21 +955,23 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 // / cs^2; it is stored into slot i of that roller node, so the
                 // pull reads it as from any other source (each roller slot
                 // has at most one such writer).  v: f*_opp(i) (16-bit f: its
-                // deviation from w_i rho0), dens: rho0 (f) or phi(x, t) (g).
+                // deviation from w_i rho0), dens: rho0 (f) or phi(x, t) (g);
+                // the roller comes from the staged link words.
                 auto reflect = [&](int lat, int i, int a, float v, float dens) {
                     const int xa = x0 + a;
                     const int xs = wrapi(xa - Lat<Q>::cx(i), nx), ysr = wrapi(y - Lat<Q>::cy(i), ny),
                               zs = wrapi(z - Lat<Q>::cz(i), nz);
                     const size_t src = ((size_t)zs * ny + ysr) * nx + xs;
-                    const int k = L.G.solid[src];
+                    const unsigned sel = a ? lk.w : lk.y;
+                    const int k = (int)(((sel >> i) & 1u) ? (sel >> 28) & 7u : (sel >> 24) & 7u);
                     const float cu = L.F.rom[k] * (float(Lat<Q>::cy(i)) * (float(xa) - L.F.rcx[k]) -
                                                    float(Lat<Q>::cx(i)) * (float(y) - L.F.rcy[k]));
                     const float val = fmaf(float(6.0 * Lat<Q>::w(i)) * dens, cu, v);
                     if (!lat) {
                         static_cast<S *>(L.dst.f)[(size_t)i * np + src] = from_f<S>(val);
-                    } else if (DEV && i == 0) {
-                        L.dst.g0[src] = val;
                     } else {
+                        // g: i >= 1 (a link has c_i != 0), a 16-bit plane
+                        // or an FP32 one
                         static_cast<S *>(L.dst.g)[(size_t)(DEV ? i - 1 : i) * np + src] = from_f<S>(val);
                     }
                 };
@@ -1225,6 +1230,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 } else {
                     stp(gp, sub2(ph, gsum));
                 }
+
             }
         }
     }

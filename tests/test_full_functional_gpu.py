@@ -1,0 +1,70 @@
+"""The paper's full free-energy functional on the GPU (model 1: Eq.
+functional with kappa_1, kappa_2, alpha; mu_rho and mu_phi of Eq. mu_rho and
+Eq. mu_phi; the force -rho grad(mu_rho) - phi grad(mu_phi) of Eq. F) against
+the oracle's: FP64 relative L-inf < 1e-12 on rho, u, phi, mu after 500
+steps on both lattices and every device, FP32 1e-5 (rho, phi) and 1e-4 on u
+against max(|u|, 0.01); the observables (the Laplace pressure from the full
+functional's bulk pressure) to 1e-10."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+DEV = {"shear": 0, "four_roller": 1, "periodic": 2}
+FULL = dict(model=1, kappa1=0.03, kappa2=0.09, alpha=0.8)
+CASES = [  # lattice, device, (nx, ny, nz), droplet, overrides
+    ("d2q9", "shear", (80, 40, 1), (39.5, 19.5, 0.0, 9.0), dict(u_wall=0.01)),
+    ("d2q9", "four_roller", (64, 64, 1), (31.5, 31.5, 0.0, 7.0), dict(u_wall=0.01)),
+    ("d3q19", "periodic", (27, 21, 19), (13.0, 10.0, 9.0, 5.0), dict(tau_g=1.3)),
+    ("d3q19", "shear", (32, 20, 16), (15.5, 9.5, 7.5, 5.0), dict(u_wall=0.02, tau_f=0.8)),
+    ("d3q19", "four_roller", (32, 32, 6), (15.5, 15.5, 2.5, 5.0), dict(u_wall=0.01)),
+]
+BASE = dict(tau_f=1.0, tau_g=1.0, A=0.0, kappa=0.0, gamma_mob=1.0, u_wall=0.0, rho0=1.0)
+
+
+@pytest.fixture(scope="module")
+def fre():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_01617_gb300 import build
+    build.build()
+    import paper_2212_01617_gb300 as fre
+    return fre
+
+
+def errs(a, b, u_floor):
+    uscale = max(max(np.abs(b[k]).max() for k in ("ux", "uy", "uz")), u_floor)
+    return {k: np.abs(a[k] - b[k]).max() / (uscale if k.startswith("u") else np.abs(b[k]).max())
+            for k in ("rho", "ux", "uy", "uz", "phi", "mu")}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}-{c[1]}")
+def test_full_functional_matches_oracle(fre, orc, case, precision):
+    lattice, device, (nx, ny, nz), drop, kw = case
+    a = dict(BASE, **kw)
+    sim = fre.Simulation(lattice=lattice, precision=precision, device=device, nx=nx, ny=ny, nz=nz, **a, **FULL)
+    assert sim.kernel_path == 0  # the full functional runs on the per-node kernels
+    o = orc.Oracle({"d2q9": 0, "d3q19": 1}[lattice], DEV[device], nx, ny, nz, a["tau_f"], a["tau_g"], a["A"],
+                   a["kappa"], a["gamma_mob"], a["u_wall"], a["rho0"], **FULL)
+    for s in (sim, o):
+        s.init_droplet(*drop)
+        s.step(500)
+    e = errs(sim.fields(), o.fields(), 0.0 if precision == "fp64" else 0.01)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    utol = tol if precision == "fp64" else 1e-4
+    assert all(v < (utol if k.startswith("u") else tol) for k, v in e.items() if k != "mu"), e
+    if precision == "fp64":
+        assert e["mu"] < 1e-12, e
+        ob, oo = sim.observables(), o.observables()
+        for key in ("mass", "phi_sum", "D", "dp", "p_centre"):
+            assert abs(ob[key] - oo[key]) <= 1e-10 * max(abs(oo[key]), 1e-6), (key, ob[key], oo[key])
+    sim.close()
+
+
+def test_full_functional_not_in_batches(fre):
+    with fre.Batch("d2q9", "fp64") as b:
+        with pytest.raises(fre.FreError) as ei:
+            b.add(9.5, 9.5, 0.0, 4.0, lattice="d2q9", device="periodic", nx=20, ny=20, nz=1, **BASE, **FULL)
+        assert ei.value.status == fre.FRE_ERR_ARG
