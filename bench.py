@@ -316,6 +316,39 @@ def cpu_baseline(seconds=15.0):
             "parallel_speedup": v_all / v_one if v_one > 0 else None}
 
 
+SERVE_SIZES = [(64, 64, 64), (96, 96, 96), (128, 64, 64), (192, 96, 96)]
+
+
+def serving_size_rates(steps=50):
+    """Step rates (G node updates per second, device-timed) of the serving
+    workload's D3Q19 lattice sizes, shear and four-roller, FP32 and FP16-dev,
+    on the kernels each context picks (the row kernels where they apply)."""
+    import torch
+    import paper_2212_01617_gb300 as fre
+    out = {}
+    for dev in ("shear", "four_roller"):
+        for shape in SERVE_SIZES:
+            nx, ny, nz = shape
+            for prec in ("fp32", "fp16dev"):
+                sim = fre.Simulation(lattice="d3q19", precision=prec, device=dev, nx=nx, ny=ny, nz=nz,
+                                     **dict(SERVE_PHYS, u_wall=0.02))
+                sim.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, ny / 5)
+                sim.step(10)
+                torch.cuda.synchronize()
+                best = None
+                for _ in range(3):
+                    _, _, upd, tot, _ = sim.step_timed(steps)
+                    if best is None or tot < best[0]:
+                        best = (tot, upd)
+                out[f"{dev} {nx}x{ny}x{nz} {prec}"] = {
+                    "gnodes_per_s": nx * ny * nz * steps / (best[0] * 1e-3) / 1e9,
+                    "update_frac_of_measured_hbm": ALG_BYTES[prec] * nx * ny * nz * steps / (best[1] * 1e-3) / 1e9
+                    / measured_peak_gbs()[0],
+                    "kernel_path": sim.kernel_path}
+                sim.close()
+    return out
+
+
 def base_config(precision):
     return {"workload": "D3Q19 two-lattice FRE-LBM, parallel-band shear 512x256x256 (33.5M nodes), "
                         "droplet R=48, A=kappa=0.04, tau=2, Gamma=0.5, u_w=0.03",
@@ -682,6 +715,7 @@ def main():
         batch = {k: bl[k] for k in ("value", "unit", "ms_per_step", "sequential", "speedup_vs_sequential",
                                     "roofline", "tuning", "config")}
         serve = serve_summary(args.summary_requests, args.summary_max_steps, args.serve_target_nodes)
+        serve["step_rates_by_size"] = serving_size_rates()
 
     if rank == 0:
         variants = {}
