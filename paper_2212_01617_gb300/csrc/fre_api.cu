@@ -37,6 +37,90 @@ fre_status fail(fre_status s, const char *fmt, ...) {
         if (e_ != cudaSuccess) return fail(FRE_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
+// Four-roller geometry (Sec. 3): four cylinders of radius nx/8 along z,
+// centred at ((nx-1)/2 +- nx/4, (ny-1)/2 +- ny/4), top right and bottom left
+// turning counter-clockwise, the other two clockwise, at surface speed
+// u_wall; a node belongs to the first roller whose disc holds it.  One z
+// plane of roller ids (the rollers are extruded along z).
+struct RollerPlane {
+    double rcx[5], rcy[5], om[5];
+    std::vector<unsigned char> id;  // [ny][nx], 0 fluid
+};
+
+void roller_plane(const fre_params &p, RollerPlane &g) {
+    const double cx = 0.5 * (p.nx - 1), cy = 0.5 * (p.ny - 1);
+    const double ox = 0.25 * p.nx, oy = 0.25 * p.ny;
+    const double r = p.nx / 8.0;
+    const double om = p.u_wall / r;
+    const double xs[5] = {0, cx + ox, cx - ox, cx - ox, cx + ox};
+    const double ys[5] = {0, cy + oy, cy + oy, cy - oy, cy - oy};
+    const double ws[5] = {0, om, -om, om, -om};  // top right, top left, bottom left, bottom right
+    for (int k = 0; k < 5; ++k) {
+        g.rcx[k] = xs[k];
+        g.rcy[k] = ys[k];
+        g.om[k] = ws[k];
+    }
+    g.id.assign((size_t)p.nx * p.ny, 0);
+    for (int y = 0; y < p.ny; ++y)
+        for (int x = 0; x < p.nx; ++x)
+            for (int k = 1; k <= 4; ++k) {
+                const double dx = x - xs[k], dy = y - ys[k];
+                if (dx * dx + dy * dy <= r * r) {
+                    g.id[(size_t)y * p.nx + x] = (unsigned char)k;
+                    break;
+                }
+            }
+}
+
+const int kC9[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
+                       {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
+const int kC19[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                         {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, 0, 1},
+                         {-1, 0, -1}, {0, 1, 1},  {0, -1, -1}, {1, -1, 0}, {-1, 1, 0},
+                         {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1}};
+
+int wrap_host(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// The wall links of one plane: population i at fluid node (x, y) whose
+// source (x, y) - c_i is a roller node of roller k, as the table of
+// k_reflect (Geo::rlinks).  The moving-wall coefficient is
+// 2 w_i (c_i . u_w) / cs^2 with u_w = omega_k z x (p - c_k) at the link's
+// wall point p = x - c_i / 2; the shift along c_i drops out of c_i x (p - c_k),
+// so c_i . u_w = omega_k (c_iy (x - x_k) - c_ix (y - y_k)).  Returns the
+// number of links; fills `out` when it is not NULL.
+long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::vector<int4> *out) {
+    if (out) out->clear();
+    long long count = 0;
+    for (int y = 0; y < p.ny; ++y)
+        for (int x = 0; x < p.nx; ++x) {
+            if (g.id[(size_t)y * p.nx + x]) continue;
+            for (int i = 1; i < q; ++i) {
+                const int *ci = q == 9 ? kC9[i] : kC19[i];
+                const int xs = wrap_host(x - ci[0], p.nx), ys = wrap_host(y - ci[1], p.ny);
+                const int k = g.id[(size_t)ys * p.nx + xs];
+                if (!k) continue;
+                ++count;
+                if (!out) continue;
+                int o = 0;
+                for (int j = 0; j < q; ++j) {
+                    const int *cj = q == 9 ? kC9[j] : kC19[j];
+                    if (cj[0] == -ci[0] && cj[1] == -ci[1] && cj[2] == -ci[2]) o = j;
+                }
+                const int c2 = ci[0] * ci[0] + ci[1] * ci[1] + ci[2] * ci[2];
+                const double w = q == 9 ? (c2 == 1 ? 1.0 / 9 : 1.0 / 36) : (c2 == 1 ? 1.0 / 18 : 1.0 / 36);
+                const double cu = g.om[k] * (ci[1] * (x - g.rcx[k]) - ci[0] * (y - g.rcy[k]));
+                const float coef = float(6.0 * w * cu);
+                int4 e;
+                e.x = y * p.nx + x;
+                e.y = ys * p.nx + xs;
+                e.z = i | (o << 8) | ((ci[2] + 1) << 16);
+                std::memcpy(&e.w, &coef, sizeof(float));
+                out->push_back(e);
+            }
+        }
+    return count;
+}
+
 struct Sizes {
     int q, sz_store, sz_comp;
     long long n, np;
@@ -85,7 +169,12 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
         s.buf_bytes = (size_t)s.q * plane + (size_t)(s.q - 1) * plane + (size_t)s.np * 4;
     }
     s.field_bytes = (size_t)s.np * s.sz_comp;
-    s.solid_bytes = p->device == FRE_FOUR_ROLLER ? (size_t)(s.np) + 8 * (size_t)p->nx * p->ny : 0;
+    s.solid_bytes = 0;
+    if (p->device == FRE_FOUR_ROLLER) {
+        RollerPlane g;
+        roller_plane(*p, g);
+        s.solid_bytes = (size_t)s.np + sizeof(int4) * (size_t)roller_links(*p, s.q, g, nullptr);
+    }
     s.model = p->model;
     return true;
 }
@@ -117,71 +206,27 @@ fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
     return FRE_OK;
 }
 
-// Four-roller geometry: roller id of every node, the solid nodes that have
-// a fluid stencil neighbour, and the wall-link word of every (x, y) for the
-// row kernels (bit i: the source (x, y) - c_i lies in a roller; bits 24..26
-// that roller; bit 30: the node itself is a roller node).  The rollers are
-// extruded along z, so one plane of words serves every z.
+// Four-roller geometry of a context: roller id of every node, the solid
+// nodes that have a fluid stencil neighbour, and the wall links of a plane.
 void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<int> &ghost,
-                   std::vector<unsigned> &links) {
+                   std::vector<int4> &links) {
     const fre_params &p = c->p;
     fre::Geo &G = c->G;
-    const double cx = 0.5 * (p.nx - 1), cy = 0.5 * (p.ny - 1);
-    const double ox = 0.25 * p.nx, oy = 0.25 * p.ny;
-    const double r = p.nx / 8.0;
-    const double om = p.u_wall / r;
-    const double xs[5] = {0, cx + ox, cx - ox, cx - ox, cx + ox};
-    const double ys[5] = {0, cy + oy, cy + oy, cy - oy, cy - oy};
-    const double ws[5] = {0, om, -om, om, -om};  // top right, top left, bottom left, bottom right
+    RollerPlane g;
+    roller_plane(p, g);
     for (int k = 0; k < 5; ++k) {
-        G.rcx[k] = xs[k];
-        G.rcy[k] = ys[k];
-        G.om[k] = ws[k];
+        G.rcx[k] = g.rcx[k];
+        G.rcy[k] = g.rcy[k];
+        G.om[k] = g.om[k];
     }
-    solid.assign((size_t)G.n, 0);
-    for (int z = 0; z < p.nz; ++z)
-        for (int y = 0; y < p.ny; ++y)
-            for (int x = 0; x < p.nx; ++x)
-                for (int k = 1; k <= 4; ++k) {
-                    double dx = x - xs[k], dy = y - ys[k];
-                    if (dx * dx + dy * dy <= r * r) {
-                        solid[((size_t)z * p.ny + y) * p.nx + x] = (unsigned char)k;
-                        break;
-                    }
-                }
+    const size_t plane = (size_t)p.nx * p.ny;
+    solid.resize((size_t)G.n);
+    for (int z = 0; z < p.nz; ++z) std::memcpy(solid.data() + (size_t)z * plane, g.id.data(), plane);
     const int q = c->q;
-    static const int c9[9][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {-1, 0, 0}, {0, -1, 0},
-                                 {1, 1, 0}, {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}};
-    static const int c19[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
-                                   {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, 0, 1},
-                                   {-1, 0, -1}, {0, 1, 1},  {0, -1, -1}, {1, -1, 0}, {-1, 1, 0},
-                                   {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1}};
-    auto wrap = [](int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); };
-    links.assign(2 * (size_t)p.nx * p.ny, 0u);
-    for (int y = 0; y < p.ny; ++y)
-        for (int x = 0; x < p.nx; ++x) {
-            unsigned w = 0, sel = 0;
-            int ka = 0, kb = 0;
-            if (solid[(size_t)y * p.nx + x]) {
-                w = 1u << 30;
-            } else {
-                for (int i = 1; i < q; ++i) {
-                    const int *ci = q == 9 ? c9[i] : c19[i];
-                    const int k = solid[(size_t)wrap(y - ci[1], p.ny) * p.nx + wrap(x - ci[0], p.nx)];
-                    if (!k) continue;
-                    w |= 1u << i;
-                    if (!ka || k == ka) {
-                        ka = k;
-                    } else {
-                        kb = k;  // a node's links reach at most two rollers
-                        sel |= 1u << i;
-                    }
-                }
-            }
-            const size_t m = 2 * ((size_t)y * p.nx + x);
-            links[m] = w;
-            links[m + 1] = sel | ((unsigned)ka << 24) | ((unsigned)kb << 28);
-        }
+    const auto &c9 = kC9;
+    const auto &c19 = kC19;
+    auto wrap = wrap_host;
+    roller_links(p, q, g, &links);
     ghost.clear();
     for (int z = 0; z < p.nz; ++z)
         for (int y = 0; y < p.ny; ++y)
@@ -248,7 +293,8 @@ void fre::ctx_launch_step(fre_ctx *c) {
     fre::Launch L = ctx_launch(c);
     const bool pull = !c->local;
     // the four-roller device takes its in-place first step on the per-node
-    // kernels (its row kernels stage wall links for pulled steps)
+    // kernels (which reflect their wall links themselves); its pulled row
+    // update leaves the wall links to the reflection pass
     const bool roll = c->G.device == FRE_FOUR_ROLLER;
     if (c->fullrow && (pull || !roll)) {
         c->ks->phi_fullrow(L, pull);
@@ -256,6 +302,7 @@ void fre::ctx_launch_step(fre_ctx *c) {
         c->ks->mu_fullrow(L);
         if (c->n_ghost) c->ks->ghost(L, L.mu);
         c->ks->update_fullrow(L, pull);
+        if (roll) c->ks->reflect(L);
     } else if (c->rows) {
         c->ks->phi_rows(L, pull);
         c->ks->mu_rows(L);
@@ -474,7 +521,7 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     if (p->device == FRE_FOUR_ROLLER) {
         std::vector<unsigned char> solid;
         std::vector<int> ghost;
-        std::vector<unsigned> links;
+        std::vector<int4> links;
         build_rollers(c, solid, ghost, links);
         void *d;
         fre_status st = dev_alloc(c, &d, s.solid_bytes);
@@ -492,17 +539,21 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
                                 c->stream) != cudaSuccess)
                 return bail(fail(FRE_ERR_CUDA, "upload of the ghost list failed"));
         }
-        st = dev_alloc(c, &d, sizeof(unsigned) * links.size());
-        if (st != FRE_OK) return bail(st);
-        c->links = static_cast<unsigned *>(d);
-        if (cudaMemcpyAsync(c->links, links.data(), sizeof(unsigned) * links.size(), cudaMemcpyHostToDevice,
-                            c->stream) != cudaSuccess)
-            return bail(fail(FRE_ERR_CUDA, "upload of the roller links failed"));
+        c->n_rlinks = (int)links.size();
+        if (c->n_rlinks) {
+            st = dev_alloc(c, &d, sizeof(int4) * links.size());
+            if (st != FRE_OK) return bail(st);
+            c->rlinks = static_cast<int4 *>(d);
+            if (cudaMemcpyAsync(c->rlinks, links.data(), sizeof(int4) * links.size(), cudaMemcpyHostToDevice,
+                                c->stream) != cudaSuccess)
+                return bail(fail(FRE_ERR_CUDA, "upload of the roller links failed"));
+        }
         if (cudaStreamSynchronize(c->stream) != cudaSuccess)
             return bail(fail(FRE_ERR_CUDA, "geometry upload: %s", cudaGetErrorString(cudaGetLastError())));
     }
     c->G.solid = c->solid;
-    c->G.links = c->links;
+    c->G.rlinks = c->rlinks;
+    c->G.n_rlinks = c->n_rlinks;
     // the full functional (model 1) runs on the per-node kernels
     if (!(p->flags & FRE_FLAG_GENERIC_KERNELS) && p->model == 0 && c->ks->row_width) {
         const unsigned sh = (p->flags >> FRE_FLAG_CHUNK_SHIFT) & 0xffu;
@@ -681,6 +732,10 @@ fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launche
         else if (c->rows) c->ks->update_rows(L, pull);
         else c->ks->update(L, pull);
         ++nl;
+        if (full && c->G.device == FRE_FOUR_ROLLER) {
+            c->ks->reflect(L);
+            ++nl;
+        }
         cudaEventRecord(ev[3 * t + 3], c->stream);
         c->cur ^= 1;
         c->pp ^= 1;

@@ -20,7 +20,8 @@ struct fre_ctx {
     void *mu = nullptr;
     void *rhof = nullptr, *murho = nullptr;  // model 1: rho and mu_rho fields
     unsigned char *solid = nullptr;
-    unsigned *links = nullptr;  // four-roller: wall-link words per (x, y)
+    int4 *rlinks = nullptr;     // four-roller: the wall links of a plane (Geo::rlinks)
+    int n_rlinks = 0;
     int *ghost = nullptr;
     int n_ghost = 0;
     double *red = nullptr;

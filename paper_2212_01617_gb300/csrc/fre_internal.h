@@ -17,7 +17,13 @@ struct Geo {
     long long n;              // nodes
     long long np;             // plane stride of the population arrays (elements)
     const unsigned char *solid;  // roller id per node (0 = fluid); four-roller only
-    const unsigned *links;    // four-roller: wall-link word pair per (x, y) for the row kernels
+    // four-roller: the wall links of one z plane (every plane has the same,
+    // the rollers being extruded along z), for the reflection pass of the
+    // row kernels (k_reflect): {fluid node y nx + x, its link's roller
+    // source (wrapped) y' nx + x', i | opp(i) << 8 | (c_iz + 1) << 16,
+    // float bits of 2 w_i (c_i . u_w) / cs^2}
+    const int4 *rlinks;
+    int n_rlinks;
     double rcx[5], rcy[5], om[5];  // roller centres and angular velocities (1..4)
     double uwall;             // shear wall speed
 };
@@ -74,6 +80,7 @@ struct Launch {
     int stall;             // FRE_FLAG_TEST_PIPELINE_STALL: producers issue no copies
     int reflect;           // four-roller on the row kernels: per-node updates also
                            // reflect their wall links into the roller nodes' slots
+                           // (the row update leaves that to k_reflect)
     double *staging;       // FP64 staging of host I/O (n doubles per field)
     cudaStream_t stream;
 };
@@ -109,6 +116,9 @@ struct KernelSet {
     void (*update_fullrow)(const Launch &, bool pull);
     void (*phi_fullrow)(const Launch &, bool pull);
     void (*mu_fullrow)(const Launch &);
+    // four-roller device on the row kernels: after the update, the wall
+    // links of the step reflected into the roller nodes' slots of dst
+    void (*reflect)(const Launch &);
 };
 
 // Many contexts of one lattice and storage format advanced by one launch

@@ -581,6 +581,43 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
     P::stg(L.dst, L.G.np, 0, n, m.phi - gsum);
 }
 
+// Four-roller device on the row kernels: the wall links of the step just
+// taken, reflected ahead of the next one (half-way bounce-back with the
+// moving-wall term).  For population i at a fluid node x whose source x - c_i
+// is a roller node, the next step pulls slot i of that roller node; leave
+// there f*_opp(i)(x) + c rho0 and g*_opp(i)(x) + c phi(x, t), with
+// c = 2 w_i (c_i . u_w) / cs^2 from the link table.  One thread per link
+// and z plane.  Reads touch fluid nodes only, each roller slot has a single
+// writer.  16-bit f holds deviations from w_i rho0 on this device, and
+// w_opp(i) = w_i, so a deviation carries over; 16-bit g keeps i >= 1 in
+// plane i - 1 (a link has c_i != 0).
+template <int FMT>
+__global__ void __launch_bounds__(kBlock) k_reflect(Launch L) {
+    static_assert(FMT != FRE_FP64, "the row kernels compute in FP32");
+    using S = typename Fmt<FMT>::S;
+    constexpr bool DEV = Fmt<FMT>::DEV;
+    const int nl = L.G.n_rlinks;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nl * L.G.nz) return;
+    const int z = (int)(t / nl);
+    const int4 e = __ldg(L.G.rlinks + (t - (long long)z * nl));
+    const int i = e.z & 0xff, o = (e.z >> 8) & 0xff, cz = ((e.z >> 16) & 0xff) - 1;
+    const float c = __int_as_float(e.w);
+    const size_t plane = (size_t)L.G.nx * L.G.ny, np = (size_t)L.G.np;
+    const size_t n = (size_t)z * plane + (size_t)e.x;
+    const size_t src = (size_t)wrapi(z - cz, L.G.nz) * plane + (size_t)e.y;
+    S *f = static_cast<S *>(L.dst.f);
+    S *g = static_cast<S *>(L.dst.g);
+    const float ph = static_cast<const float *>(L.phi)[n];
+    if constexpr (DEV) {
+        f[(size_t)i * np + src] = from_float<S>(fmaf(c, L.F.rho0, to_float(f[(size_t)o * np + n])));
+        g[(size_t)(i - 1) * np + src] = from_float<S>(fmaf(c, ph, to_float(g[(size_t)(o - 1) * np + n])));
+    } else {
+        f[(size_t)i * np + src] = fmaf(c, L.F.rho0, f[(size_t)o * np + n]);
+        g[(size_t)i * np + src] = fmaf(c, ph, g[(size_t)o * np + n]);
+    }
+}
+
 template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock) k_update(Launch L) {
     FRE_SITE_OR_RETURN(L, s);
@@ -1109,6 +1146,12 @@ struct Launchers {
     }
     static void init_eq(const Launch &L, int from_staging) {
         k_init_eq<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L, from_staging);
+    }
+    static void reflect(const Launch &L) {
+        if constexpr (FMT != FRE_FP64) {
+            const long long nt = (long long)L.G.n_rlinks * L.G.nz;
+            if (nt > 0) k_reflect<FMT><<<(unsigned)((nt + kBlock - 1) / kBlock), kBlock, 0, L.stream>>>(L);
+        }
     }
     static void mei_prep(const Launch &L) { k_mei_prep<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L); }
     static void mei_iter(const Launch &L, bool pull) {

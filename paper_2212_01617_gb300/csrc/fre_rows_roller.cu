@@ -1,6 +1,6 @@
-// Row update of the four-roller device (pulled steps, with the per-node
-// wall-link words staged beside the rows): a translation unit of its own so
-// that these instantiations compile alongside the others.
+// Row update of the four-roller device (pulled steps; roller nodes stored
+// as 0): a translation unit of its own so that these instantiations compile
+// alongside the others.
 #include "fre_ws.cuh"
 
 namespace fre {

@@ -424,7 +424,7 @@ namespace fre {
 // memory and staged by one copy unless the pull offset wraps or meets a
 // wall; the phi / mu stencil rows of one z plane are one copy of R + 2 rows
 // (y0 - 1 .. y0 + R) unless they wrap or are clamped at a wall.
-template <int Q, int FMT, int KIND, int R, bool ROLL = false>
+template <int Q, int FMT, int KIND, int R>
 struct RowsLayout {
     using S = typename Fmt<FMT>::S;
     static constexpr bool DEV = Fmt<FMT>::DEV;
@@ -469,27 +469,15 @@ struct RowsLayout {
         if (KIND == WS_UPDATE) return fld_off(nx) + 2 * NFIELD * fldb(nx);
         return base_tx(nx);
     }
-    // four-roller device: the wall-link words (two uint32 per node) of the
-    // unit's R rows, after everything else
-    __host__ __device__ static unsigned lnk_off(int nx) { return (base_bytes(nx) + 15u) / 16u * 16u; }
-    __host__ __device__ static unsigned lnk_bytes(int nx) { return ROLL ? (unsigned)(R * nx * 8) : 0u; }
-    __host__ __device__ static unsigned tx_bytes(int nx) { return base_tx(nx) + lnk_bytes(nx); }
-    __host__ __device__ static unsigned bytes(int nx) { return ROLL ? lnk_off(nx) + lnk_bytes(nx) : base_bytes(nx); }
+    __host__ __device__ static unsigned tx_bytes(int nx) { return base_tx(nx); }
+    __host__ __device__ static unsigned bytes(int nx) { return base_bytes(nx); }
     __host__ __device__ static unsigned stage(int nx) { return (bytes(nx) + 127u) / 128u * 128u; }
-    // copy groups issued by the producer lanes (the last one: the link words)
+    // copy groups issued by the producer lanes
     __host__ __device__ static constexpr int ngroups() {
-        return (KIND == WS_UPDATE ? 2 * Q + 2 * NGRP : (KIND == WS_PHI ? Q : NGRP)) + (ROLL ? 1 : 0);
+        return KIND == WS_UPDATE ? 2 * Q + 2 * NGRP : (KIND == WS_PHI ? Q : NGRP);
     }
 };
 
-// Wall-link words of a node of the four-roller device (host-built table
-// [ny][nx] of word pairs, the same in every z plane since the rollers are
-// extruded along z).  Word 0: bit i (i < q) is set when the source x - c_i
-// of population i is a roller node; bit 30 marks a roller (solid) node
-// itself.  Word 1: the rollers a node's links reach (at most two, where
-// rollers nearly touch): bits 24..26 roller A, 28..30 roller B, and bit i
-// set when link i reaches B rather than A.
-constexpr unsigned kLinkSolid = 1u << 30;
 
 
 // Two adjacent nodes per consumer thread: FP32 arithmetic on packed pairs
@@ -543,32 +531,6 @@ __device__ __forceinline__ float2 st_pair(__nv_bfloat16 *p, float2 v) {
     return __bfloat1622float2(h);
 }
 
-// one FP32 value in the storage type
-template <typename S>
-__device__ __forceinline__ S from_f(float v);
-template <>
-__device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-// a pair store that skips the roller (solid) nodes of the pair (bit 30 of
-// their wall-link words); returns the stored values (rounded), 0 for rollers
-template <typename S>
-__device__ __forceinline__ float2 st_fluid(S *p, float2 v, uint2 lw) {
-    float2 out = make_float2(0.f, 0.f);
-    if (!(lw.x & (1u << 30))) {
-        const S a = from_f<S>(v.x);
-        p[0] = a;
-        out.x = to_f(a);
-    }
-    if (!(lw.y & (1u << 30))) {
-        const S b = from_f<S>(v.y);
-        p[1] = b;
-        out.y = to_f(b);
-    }
-    return out;
-}
 
 // populations whose c_y has the sign of sy, as a bit mask
 template <int Q>
@@ -684,12 +646,12 @@ struct RowsPar {
 
 // NXC: the row length as a compile-time constant (every shared-memory
 // offset then folds into the instruction), or 0 to take it from the launch.
-// ROLL: the four-roller device (wall links per node from the staged link
-// words, roller nodes stored as 0).
+// ROLL: the four-roller device (roller nodes stored as 0; its wall links
+// are reflected into the roller nodes' slots by k_reflect after the update).
 template <int Q, int FMT, int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
 __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_wsrow(Launch L, int nunits) {
     using S = typename Fmt<FMT>::S;
-    using FL = RowsLayout<Q, FMT, KIND, R, ROLL>;
+    using FL = RowsLayout<Q, FMT, KIND, R>;
     constexpr bool DEV = Fmt<FMT>::DEV;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) unsigned long long full[NST], empty[NST];
@@ -759,11 +721,6 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
             }
             __syncwarp();
             for (int gi = lane; gi < FL::ngroups(); gi += 32) {
-                if (ROLL && gi == FL::ngroups() - 1) {
-                    // the link words of the unit's rows (contiguous in the table)
-                    bulk_load(buf + FL::lnk_off(nx), L.G.links + 2 * (size_t)y0 * nx, FL::lnk_bytes(nx), bar);
-                    continue;
-                }
                 if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q)) {
                     // ---- phi / mu stencil rows of one z plane
                     const int j = KIND == WS_MU ? gi : gi - 2 * Q;
@@ -928,59 +885,24 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                 const int y = y0 + r;
                 const size_t row = ((size_t)z * ny + y) * nx;
                 const Site st = make_site(L.G, x0, y, z);
-                // four-roller: the wall-link words of the pair's nodes
-                const uint4 lk = ROLL ? *reinterpret_cast<const uint4 *>(cur + FL::lnk_off(nx) + ((size_t)r * nx + x0) * 8)
-                                      : make_uint4(0u, 0u, 0u, 0u);
-                const uint2 lw = make_uint2(lk.x, lk.z);
-                const bool lany = ROLL && ((lw.x | lw.y) & ((1u << Q) - 1u)) != 0u;
-                // store a pair; the four-roller device leaves the slots of
-                // its roller nodes alone (they hold the populations its wall
-                // links reflect, below).  Returns the values as stored
-                // (16-bit: rounded; 0 for roller nodes)
+                // four-roller: the roller (solid) nodes of the pair store 0
+                // in every slot (a select, no branch); k_reflect then fills
+                // the slots the next step pulls through a wall link
+                const uchar2 sol = ROLL ? __ldg(reinterpret_cast<const uchar2 *>(L.G.solid + row + x0))
+                                        : make_uchar2(0, 0);
+                auto zs2 = [&](float2 v) -> float2 {
+                    if constexpr (ROLL) return make_float2(sol.x ? 0.f : v.x, sol.y ? 0.f : v.y);
+                    return v;
+                };
+                // store a pair; returns the values as stored (16-bit: rounded)
                 auto stp = [&](S *p, float2 v) -> float2 {
-                    if constexpr (ROLL) {
-                        if ((lw.x | lw.y) & kLinkSolid) return st_fluid(p, v, lw);
-                    }
+                    v = zs2(v);
                     if constexpr (DEV) {
                         return st_pair(p, v);
                     } else {
                         st_pair(p, v);
                         return v;
                     }
-                };
-                // Four-roller wall links, reflected ahead of the next step:
-                // for a link of population i at node x (source x - c_i a
-                // roller node), the value the next step pulls there is
-                // f*_opp(i)(x) plus the moving-wall term 2 w_i dens (c_i . u_w)
-                // / cs^2; it is stored into slot i of that roller node, so the
-                // pull reads it as from any other source (each roller slot
-                // has at most one such writer).  v: f*_opp(i) (16-bit f: its
-                // deviation from w_i rho0), dens: rho0 (f) or phi(x, t) (g);
-                // the roller comes from the staged link words.
-                auto reflect = [&](int lat, int i, int a, float v, float dens) {
-                    const int xa = x0 + a;
-                    const int xs = wrapi(xa - Lat<Q>::cx(i), nx), ysr = wrapi(y - Lat<Q>::cy(i), ny),
-                              zs = wrapi(z - Lat<Q>::cz(i), nz);
-                    const size_t src = ((size_t)zs * ny + ysr) * nx + xs;
-                    const unsigned sel = a ? lk.w : lk.y;
-                    const int k = (int)(((sel >> i) & 1u) ? (sel >> 28) & 7u : (sel >> 24) & 7u);
-                    const float cu = L.F.rom[k] * (float(Lat<Q>::cy(i)) * (float(xa) - L.F.rcx[k]) -
-                                                   float(Lat<Q>::cx(i)) * (float(y) - L.F.rcy[k]));
-                    const float val = fmaf(float(6.0 * Lat<Q>::w(i)) * dens, cu, v);
-                    if (!lat) {
-                        static_cast<S *>(L.dst.f)[(size_t)i * np + src] = from_f<S>(val);
-                    } else {
-                        // g: i >= 1 (a link has c_i != 0), a 16-bit plane
-                        // or an FP32 one
-                        static_cast<S *>(L.dst.g)[(size_t)(DEV ? i - 1 : i) * np + src] = from_f<S>(val);
-                    }
-                };
-                // the reflections of opposite pair (i, j) of this pair of nodes
-                auto reflect_pair = [&](int lat, int i, int j, float2 vi, float2 vj, float2 dens) {
-                    if ((lw.x >> i) & 1u) reflect(lat, i, 0, vj.x, dens.x);
-                    if ((lw.y >> i) & 1u) reflect(lat, i, 1, vj.y, dens.y);
-                    if ((lw.x >> j) & 1u) reflect(lat, j, 0, vi.x, dens.x);
-                    if ((lw.y >> j) & 1u) reflect(lat, j, 1, vi.y, dens.y);
                 };
                 // FP32: start the lines of the off-axis stencil values (c_y and
                 // c_z both nonzero, read from global memory below) toward L1
@@ -1136,9 +1058,6 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                     const float2 Ag = mul2(wg, fma2(ph, E, gmu3));
                     const float2 Bg = mul2(mul2(wg, ph), cu3);
                     const float2 gi = fma2(omg, g[i], add2(Ag, Bg)), gj = fma2(omg, g[j], sub2(Ag, Bg));
-                    if constexpr (ROLL) {
-                        if (lany) reflect_pair(1, i, j, gi, gj, ph);
-                    }
                     if constexpr (DEV) {
                         // the rest population of g closes sum_i g*_i = phi on
                         // the values as they are stored
@@ -1186,9 +1105,6 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                         Bf = fma2(mul2(wr, rho), cu3, mul2(p2(3.f * kf * w), cF));
                     }
                     const float2 fi = fma2(omf, f[i], add2(Af, Bf)), fj = fma2(omf, f[j], sub2(Af, Bf));
-                    if constexpr (ROLL) {
-                        if (lany) reflect_pair(0, i, j, fi, fj, p2(rho0));
-                    }
                     fsum = add2(fsum, add2(stp(fp + (size_t)i * np, fi), stp(fp + (size_t)j * np, fj)));
                     if constexpr (!TWO) collide_g(i, j, w, cu3, E);
                 }
@@ -1220,13 +1136,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
                     }
                 }
                 if constexpr (DEV) {
-                    const float2 g0v = sub2(ph, gsum);
-                    if (ROLL && ((lw.x | lw.y) & kLinkSolid)) {
-                        if (!(lw.x & kLinkSolid)) L.dst.g0[off] = g0v.x;
-                        if (!(lw.y & kLinkSolid)) L.dst.g0[off + 1] = g0v.y;
-                    } else {
-                        st_pair(L.dst.g0 + off, g0v);
-                    }
+                    st_pair(L.dst.g0 + off, zs2(sub2(ph, gsum)));
                 } else {
                     stp(gp, sub2(ph, gsum));
                 }
@@ -1236,11 +1146,11 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
     }
 }
 
-// The pulled update of the four-roller device on the row kernels (wall-link
-// words staged with the rows, wall links reflected into the roller nodes'
-// slots); defined in fre_rows_roller.cu, a translation unit of its own.  Its
-// phi and mu passes are the plain row kernels: the pull reads the reflected
-// populations from the roller slots like any other source.
+// The pulled update of the four-roller device on the row kernels (roller
+// nodes stored as 0; k_reflect then writes the wall links into the roller
+// nodes' slots); defined in fre_rows_roller.cu, a translation unit of its
+// own.  Its phi and mu passes are the plain row kernels: the pull reads the
+// reflected populations from the roller slots like any other source.
 template <int Q, int FMT>
 struct RollRows {
     static void update(const Launch &L);
@@ -1253,16 +1163,16 @@ struct WsRowLaunchers {
     // stages per block: the update takes up to three of those that fit (one
     // block per SM on long rows); the lighter phi and mu passes take two, so
     // that two blocks (two producer warps issuing bulk copies) share an SM
-    template <int KIND, int R, bool ROLL = false>
+    template <int KIND, int R>
     static int nst(int nx) {
-        const unsigned sb = RowsLayout<Q, FMT, KIND, R, ROLL>::stage(nx);
+        const unsigned sb = RowsLayout<Q, FMT, KIND, R>::stage(nx);
         const int lim = KIND == WS_UPDATE ? kMaxSmem : kMaxSmem / 2;
         const int n = (int)(lim / sb);
         if (KIND != WS_UPDATE) return n >= 2 ? 2 : n;
         return n >= 3 ? 3 : (n >= 2 ? 2 : n);
     }
     // two rows per unit where a staged row is shorter than 2 KB
-    template <int KIND, bool ROLL = false>
+    template <int KIND>
     static int rows_per_unit(const Geo &G, bool pull) {
         // the mu pass stages three copies per unit whatever R: four rows per
         // unit keep it off the copy engine's rate of operations
@@ -1271,13 +1181,12 @@ struct WsRowLaunchers {
         if (G.nx % 64 != 0) return 2;
         if (!pull || G.ny % 2 != 0) return 1;
         if (RowsLayout<Q, FMT, KIND, 1>::rowb(G.nx) >= 2048) return 1;
-        return nst<KIND, 2, ROLL>(G.nx) >= 2 ? 2 : 1;
+        return nst<KIND, 2>(G.nx) >= 2 ? 2 : 1;
     }
     // the four-roller device takes the row kernels when its wall-link table
     // is there (pulled steps; the first, in-place step runs per node)
     static bool usable(const Geo &G) {
-        const bool roll = G.device == FRE_FOUR_ROLLER;
-        if (roll && !G.links) return false;
+        if (G.device == FRE_FOUR_ROLLER && !G.rlinks) return false;
         if ((G.np * sizeof(S)) % 16 != 0 || (G.nx * sizeof(S)) % 16 != 0 || (G.nx * 4) % 16 != 0) return false;
         // rows of a whole number of warps' pairs (nx a multiple of 64), or of
         // an odd number of half warps taken two rows at a time (ny even)
@@ -1285,14 +1194,13 @@ struct WsRowLaunchers {
         if (G.nx % 64 != 0 && (G.ny % 2 != 0 || nst<WS_UPDATE, 2>(G.nx) < 2 || nst<WS_PHI, 2>(G.nx) < 2 ||
                                nst<WS_MU, 2>(G.nx) < 2 || nst<WS_MU, 4>(G.nx) < 2))
             return false;
-        if (roll && (nst<WS_UPDATE, 2, true>(G.nx) < 2 || nst<WS_UPDATE, 1, true>(G.nx) < 2)) return false;
         return nst<WS_UPDATE, 1>(G.nx) >= 2 && nst<WS_PHI, 1>(G.nx) >= 1 && nst<WS_MU, 1>(G.nx) >= 1;
     }
     template <int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
     static void launch(const Launch &L) {
         const int nx = L.G.nx;
         const int nu = (L.G.ny / R) * L.G.nz;
-        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R, ROLL>::stage(nx);
+        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX, ROLL>;
         LaunchShape::opt_in((const void *)fn, smem);
         const int threads = RPX * (nx / 2) + 32;
@@ -1304,7 +1212,7 @@ struct WsRowLaunchers {
     template <int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
     static int resident(const Launch &L) {
         const int nx = L.G.nx;
-        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R, ROLL>::stage(nx);
+        const size_t smem = (size_t)NST * RowsLayout<Q, FMT, KIND, R>::stage(nx);
         auto fn = k_wsrow<Q, FMT, KIND, PULL, NST, R, NXC, RPX, ROLL>;
         LaunchShape::opt_in((const void *)fn, smem);
         return LaunchShape::blocks_per_sm((const void *)fn, RPX * (nx / 2) + 32, smem);
@@ -1314,7 +1222,7 @@ struct WsRowLaunchers {
     // where the SM holds as many blocks with it as with two
     template <int KIND, bool PULL, int R, int NXC, int RPX, bool ROLL = false>
     static void run_n(const Launch &L) {
-        if (nst<KIND, R, ROLL>(L.G.nx) >= 3 &&
+        if (nst<KIND, R>(L.G.nx) >= 3 &&
             resident<KIND, PULL, 3, R, NXC, RPX, ROLL>(L) >= resident<KIND, PULL, 2, R, NXC, RPX, ROLL>(L))
             launch<KIND, PULL, 3, R, NXC, RPX, ROLL>(L);
         else
@@ -1335,8 +1243,8 @@ struct WsRowLaunchers {
         if (PULL && L.G.nx == 512) run_n<KIND, PULL, R, 512, RPD>(L);
         else run_n<KIND, PULL, R, 0, RPD>(L);
     }
-    // four-roller device, pulled steps of the phi pass and the update (the
-    // kernels with the wall-link words; instantiated in fre_rows_roller.cu)
+    // four-roller device, pulled steps of the update (roller nodes stored
+    // as 0; instantiated in fre_rows_roller.cu)
     template <int KIND, int R>
     static void run_r_roll(const Launch &L) {
         constexpr int RPD = RowsPar<KIND, R>::V;
@@ -1350,7 +1258,7 @@ struct WsRowLaunchers {
     }
     template <int KIND>
     static void run_roll(const Launch &L) {
-        if (rows_per_unit<KIND, true>(L.G, true) == 2) run_r_roll<KIND, 2>(L);
+        if (rows_per_unit<KIND>(L.G, true) == 2) run_r_roll<KIND, 2>(L);
         else run_r_roll<KIND, 1>(L);
     }
     template <int KIND, bool PULL>
@@ -1399,7 +1307,7 @@ const KernelSet *kernel_set_ws() {
                                      GL::mei_final, WsEntry<Q, FMT>::width, WL::phi,
                                      WL::mu, WL::update, WsRowLaunchers<Q, FMT>::usable,
                                      WsRowLaunchers<Q, FMT>::update, WsRowLaunchers<Q, FMT>::phi,
-                                     WsRowLaunchers<Q, FMT>::mu};
+                                     WsRowLaunchers<Q, FMT>::mu, GL::reflect};
         return &ks;
     }
 }
