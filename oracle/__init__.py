@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("tau_f", C.c_double), ("tau_g", C.c_double),
                 ("A", C.c_double), ("kappa", C.c_double), ("Gamma", C.c_double),
                 ("u_wall", C.c_double), ("rho0", C.c_double),
-                ("model", C.c_int), ("kappa1", C.c_double), ("kappa2", C.c_double), ("alpha", C.c_double)]
+                ("model", C.c_int), ("kappa1", C.c_double), ("kappa2", C.c_double), ("alpha", C.c_double),
+                ("interp", C.c_int)]
 
 
 class Obs(C.Structure):
@@ -150,11 +151,12 @@ class Oracle:
 
     def __init__(self, lattice=D2Q9, device=SHEAR, nx=16, ny=8, nz=1, tau_f=1.0,
                  tau_g=1.0, A=0.04, kappa=0.04, Gamma=1.0, u_wall=0.0, rho0=1.0,
-                 model=0, kappa1=0.0, kappa2=0.0, alpha=0.0):
+                 model=0, kappa1=0.0, kappa2=0.0, alpha=0.0, interp=0):
         """model 0: the reduced functional (A, kappa); model 1: the full
-        functional of Eq. functional (kappa1, kappa2, alpha)."""
+        functional of Eq. functional (kappa1, kappa2, alpha).  interp: the
+        four-roller device's interpolated bounce-back at the rollers."""
         self.p = Params(lattice, device, nx, ny, nz, tau_f, tau_g, A, kappa, Gamma,
-                        u_wall, rho0, model, kappa1, kappa2, alpha)
+                        u_wall, rho0, model, kappa1, kappa2, alpha, interp)
         self._h = lib().orc_create(C.byref(self.p))
         if not self._h:
             raise ValueError("oracle: invalid parameters")

@@ -483,6 +483,24 @@ static void collide(orc_state *s)
     }
 }
 
+/* Fraction q in (0, 1] of the link from fluid node (x, y) toward its solid
+ * source (x, y) - c_i at which it crosses the surface of roller k (circle
+ * of radius rr about rc[k]), measured from the fluid node.  The source's
+ * wrapped coordinates place the circle; the fluid node is the source plus
+ * c_i. */
+static double link_fraction(const orc_state *s, int x, int y, int i, int k)
+{
+    int xs = wrap(x - s->c[i][0], s->p.nx), ys = wrap(y - s->c[i][1], s->p.ny);
+    double dx = xs + s->c[i][0] - s->rc[k][0], dy = ys + s->c[i][1] - s->rc[k][1];
+    double cx = s->c[i][0], cy = s->c[i][1];
+    double cc = cx * cx + cy * cy, dc = dx * cx + dy * cy, dd = dx * dx + dy * dy - s->rr * s->rr;
+    double disc = dc * dc - cc * dd;
+    double t = (dc - sqrt(disc > 0.0 ? disc : 0.0)) / cc; /* first crossing of |d - t c| = r */
+    if (t <= 0.0) t = 1e-12;
+    if (t > 1.0) t = 1.0;
+    return t;
+}
+
 static void stream(orc_state *s)
 {
     #pragma omp parallel for schedule(static)
@@ -501,8 +519,43 @@ static void stream(orc_state *s)
                 double cu = 0.0;
                 for (int a = 0; a < 3; ++a) cu += s->c[i][a] * uw[a];
                 size_t kb = (size_t)s->opp[i] * s->n + n;
-                s->f[k] = s->fs[kb] + 2.0 * s->w[i] * s->p.rho0 * cu / CS2;
-                s->g[k] = s->gs[kb] + 2.0 * s->w[i] * s->phi[n] * cu / CS2;
+                double lf = 2.0 * s->w[i] * s->p.rho0 * cu / CS2, lg = 2.0 * s->w[i] * s->phi[n] * cu / CS2;
+                if (s->p.interp && s->p.device == ORC_FOUR_ROLLER) {
+                    /* interpolated bounce-back (linear, after Bouzidi et al.):
+                     * the wall sits at x - q c_i; q < 1/2 interpolates the
+                     * opposite population between x and x + c_i before it
+                     * is reflected, q >= 1/2 between the reflected one and
+                     * the node's own population i; the moving-wall term
+                     * takes the matching weight (1 for q < 1/2, 1/(2q)) */
+                    long long src2 = node(s, wrap(x - s->c[i][0], s->p.nx), wrap(y - s->c[i][1], s->p.ny),
+                                          wrap(z - s->c[i][2], s->p.nz));
+                    int kr = s->solid[src2];
+                    double q = link_fraction(s, x, y, i, kr);
+                    /* the wall velocity at the wall point x - q c_i itself */
+                    double xw = wrap(x - s->c[i][0], s->p.nx) + (1.0 - q) * s->c[i][0];
+                    double yw = wrap(y - s->c[i][1], s->p.ny) + (1.0 - q) * s->c[i][1];
+                    cu = s->omega[kr] * (-(yw - s->rc[kr][1]) * s->c[i][0] + (xw - s->rc[kr][0]) * s->c[i][1]);
+                    lf = 2.0 * s->w[i] * s->p.rho0 * cu / CS2;
+                    lg = 2.0 * s->w[i] * s->phi[n] * cu / CS2;
+                    long long m = node(s, wrap(x + s->c[i][0], s->p.nx), wrap(y + s->c[i][1], s->p.ny),
+                                       wrap(z + s->c[i][2], s->p.nz));
+                    if (q < 0.5 && !s->solid[m]) {
+                        size_t km = (size_t)s->opp[i] * s->n + m;
+                        s->f[k] = 2.0 * q * s->fs[kb] + (1.0 - 2.0 * q) * s->fs[km] + lf;
+                        s->g[k] = 2.0 * q * s->gs[kb] + (1.0 - 2.0 * q) * s->gs[km] + lg;
+                    } else if (q >= 0.5) {
+                        size_t ki = (size_t)i * s->n + n;
+                        s->f[k] = (s->fs[kb] + (2.0 * q - 1.0) * s->fs[ki] + lf) / (2.0 * q);
+                        s->g[k] = (s->gs[kb] + (2.0 * q - 1.0) * s->gs[ki] + lg) / (2.0 * q);
+                    } else {
+                        /* no fluid node behind x: half-way bounce-back */
+                        s->f[k] = s->fs[kb] + lf;
+                        s->g[k] = s->gs[kb] + lg;
+                    }
+                } else {
+                    s->f[k] = s->fs[kb] + lf;
+                    s->g[k] = s->gs[kb] + lg;
+                }
             }
         }
     }

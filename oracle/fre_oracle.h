@@ -42,6 +42,9 @@ typedef struct {
                          1: the full functional of Eq. functional (kappa1,
                          kappa2, alpha; force -rho grad mu_rho - phi grad mu_phi) */
     double kappa1, kappa2, alpha;
+    int interp;       /* four-roller: 1 = interpolated bounce-back at the
+                         roller surfaces (link fraction q from the circles),
+                         0 = half-way bounce-back on the staircase */
 } orc_params;
 
 typedef struct {

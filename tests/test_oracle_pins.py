@@ -650,8 +650,25 @@ def _four_roller_geometry(nx, ny, u_w):
     return ident, rollers
 
 
+def _link_fraction_bisection(p_fluid, c, centre, r):
+    """Fraction t of the link from p_fluid toward p_fluid - c at which it
+    first enters the disc of radius r about centre, by bisection on the
+    inside test (independent of any closed form)."""
+    lo, hi = 0.0, 1.0
+    inside = lambda t: (p_fluid[0] - t * c[0] - centre[0]) ** 2 + (p_fluid[1] - t * c[1] - centre[1]) ** 2 <= r * r  # noqa: E731,E501
+    assert not inside(0.0) and inside(1.0)
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if inside(mid):
+            hi = mid
+        else:
+            lo = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("interp", [0, 1])
 @pytest.mark.parametrize("lattice,shape", [(0, (1, 16, 16)), (1, (3, 16, 16))])
-def test_brute_force_one_step_four_roller(orc, lattice, shape):
+def test_brute_force_one_step_four_roller(orc, lattice, shape, interp):
     """One step of the four-roller device on a small lattice from random
     populations, recomputed from the geometry alone: the staircase mask,
     stencil values at solids as the w-weighted mean of their fluid
@@ -661,7 +678,14 @@ def test_brute_force_one_step_four_roller(orc, lattice, shape):
     rotation at the link's wall point, u_w = omega_k z x (x - c_i / 2 - c_k).
     Every fluid population agrees with the oracle to 1e-13.  The link wall
     point and the ghost rule are readings (no closed form fixes them); this
-    pins their indices, signs and points."""
+    pins their indices, signs and points.  interp = 1: the linear
+    interpolated bounce-back of Bouzidi, Firdaouss and Lallemand (2001) with
+    the wall fraction q of each link found by bisection on the circle and
+    the wall velocity taken at x - q c_i: q < 1/2 uses
+    2q f*_ibar(x) + (1 - 2q) f*_ibar(x + c_i) (half-way bounce-back when
+    x + c_i is solid), q >= 1/2 uses
+    [f*_ibar(x) + (2q - 1) f*_i(x)] / (2q), with the moving-wall term
+    weighted 1 and 1/(2q) respectively."""
     nz, ny, nx = shape
     c, _ = _lat(orc, lattice)
     q, d = c.shape[0], (2 if lattice == 0 else 3)
@@ -681,7 +705,7 @@ def test_brute_force_one_step_four_roller(orc, lattice, shape):
     f[:, solid] = 0.0
     g[:, solid] = 0.0
 
-    o = orc.Oracle(lattice, orc.FOUR_ROLLER, nx, ny, nz, tau_f, tau_g, A, kappa, Gamma, u_w, rho0)
+    o = orc.Oracle(lattice, orc.FOUR_ROLLER, nx, ny, nz, tau_f, tau_g, A, kappa, Gamma, u_w, rho0, interp=interp)
     o.load_populations(f, g)
     o.step(1)
     fo, go = o.populations()
@@ -727,6 +751,7 @@ def test_brute_force_one_step_four_roller(orc, lattice, shape):
     f_new = np.zeros_like(f)
     g_new = np.zeros_like(g)
     links = 0
+    branches = [0, 0, 0]  # q >= 1/2; q < 1/2 with x + c_i solid; q < 1/2
     for (z, y, x) in zip(*np.nonzero(fluid)):
         for i in range(q):
             xs, ys, zs = (x - ci[i, 0]) % nx, (y - ci[i, 1]) % ny, (z - ci[i, 2]) % nz
@@ -737,12 +762,36 @@ def test_brute_force_one_step_four_roller(orc, lattice, shape):
                 continue
             links += 1
             x0, y0, om = rollers[k]
-            xw, yw = x - 0.5 * ci[i, 0], y - 0.5 * ci[i, 1]
+            if not interp:
+                xw, yw = x - 0.5 * ci[i, 0], y - 0.5 * ci[i, 1]
+                uw = np.array([-om * (yw - y0), om * (xw - x0), 0.0])[:d]
+                cu = float(cd[i] @ uw)
+                f_new[i, z, y, x] = post_f[opp[i], z, y, x] + 2 * w[i] * rho0 * cu / CS2
+                g_new[i, z, y, x] = post_g[opp[i], z, y, x] + 2 * w[i] * phi[z, y, x] * cu / CS2
+                continue
+            # the fluid node in the frame of the (wrapped) solid source
+            pf = (xs + ci[i, 0], ys + ci[i, 1])
+            qq = _link_fraction_bisection(pf, ci[i, :2], (x0, y0), nx / 8.0)
+            xw, yw = pf[0] - qq * ci[i, 0], pf[1] - qq * ci[i, 1]
             uw = np.array([-om * (yw - y0), om * (xw - x0), 0.0])[:d]
-            cu = float(cd[i] @ uw)
-            f_new[i, z, y, x] = post_f[opp[i], z, y, x] + 2 * w[i] * rho0 * cu / CS2
-            g_new[i, z, y, x] = post_g[opp[i], z, y, x] + 2 * w[i] * phi[z, y, x] * cu / CS2
+            lf = 2 * w[i] * rho0 * float(cd[i] @ uw) / CS2
+            lg = 2 * w[i] * phi[z, y, x] * float(cd[i] @ uw) / CS2
+            xm, ym, zm = (x + ci[i, 0]) % nx, (y + ci[i, 1]) % ny, (z + ci[i, 2]) % nz
+            ob, oi = (opp[i], z, y, x), (i, z, y, x)
+            branches[int(qq < 0.5) + int(qq < 0.5 and ident[zm, ym, xm] == 0)] += 1
+            if qq < 0.5 and ident[zm, ym, xm] == 0:
+                om_ = (opp[i], zm, ym, xm)
+                f_new[i, z, y, x] = 2 * qq * post_f[ob] + (1 - 2 * qq) * post_f[om_] + lf
+                g_new[i, z, y, x] = 2 * qq * post_g[ob] + (1 - 2 * qq) * post_g[om_] + lg
+            elif qq < 0.5:
+                f_new[i, z, y, x] = post_f[ob] + lf
+                g_new[i, z, y, x] = post_g[ob] + lg
+            else:
+                f_new[i, z, y, x] = (post_f[ob] + (2 * qq - 1) * post_f[oi] + lf) / (2 * qq)
+                g_new[i, z, y, x] = (post_g[ob] + (2 * qq - 1) * post_g[oi] + lg) / (2 * qq)
     assert links >= 40 * nz  # the step crosses many roller links
+    if interp:  # both interpolation branches are taken many times
+        assert branches[0] >= 10 * nz and branches[2] >= 10 * nz, branches
     assert np.abs(fo[:, fluid] - f_new[:, fluid]).max() < 1e-13
     assert np.abs(go[:, fluid] - g_new[:, fluid]).max() < 1e-13
 
