@@ -390,11 +390,20 @@ def run_reference(args, ws, rank):
 
 def profile_case(spec: str, precisions, steps: int = 3):
     """Small case of the benchmark kernels for ncu captures: a D3Q19 shear
-    lattice of the given size (e.g. 512x64x32), droplet, `steps` steps."""
+    lattice of the given size (e.g. 512x64x32), droplet, `steps` steps.  A
+    "four_roller:" prefix (e.g. four_roller:192x96x96) takes the four-roller
+    device instead, at the same physical parameters (u_wall 0.02)."""
     import torch
     import paper_2212_01617_gb300 as fre
-    nx, ny, nz = (int(v) for v in spec.split("x"))
+    device, _, size = spec.rpartition(":")
+    nx, ny, nz = (int(v) for v in size.split("x"))
     w = dict(WORKLOAD, nx=nx, ny=ny, nz=nz)
+    if device:
+        if device not in ("shear", "four_roller"):
+            raise SystemExit(f"unknown device {device!r} in --profile-case")
+        w["device"] = device
+        if device == "four_roller":
+            w["u_wall"] = 0.02
     for prec in precisions:
         base, flags = split_prec(prec)
         sim = fre.Simulation(precision=base, flags=flags, **w)
@@ -648,7 +657,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-case", default=None,
-                    help="NXxNYxNZ: run a few steps of a small case (ncu captures) and exit")
+                    help="[four_roller:]NXxNYxNZ: run a few steps of a small case (ncu captures) and exit")
     ap.add_argument("--workload", choices=["lattice", "batch", "serve"], default="lattice",
                     help="lattice: the 512x256x256 D3Q19 lattice (default); batch: 64 uneven D2Q9 cases; "
                          "serve: Poisson-arriving D3Q19 requests through the serving loop")

@@ -136,6 +136,21 @@ typedef struct {
  * FRE_ERR_CUDA; the GPU and other contexts are unaffected.  The populations
  * of such a context are left undefined: initialise it again before use. */
 #define FRE_FLAG_TEST_PIPELINE_STALL 16u
+/* Four-roller device only (an argument error elsewhere): bounce-back at the
+ * roller surfaces interpolated along each wall link instead of half-way
+ * bounce-back on the staircase of roller nodes.  The circle cuts the link
+ * from a fluid node x toward its roller source x - c_i at x - q c_i,
+ * 0 < q <= 1; the linear rule of Bouzidi, Firdaouss and Lallemand (Phys.
+ * Fluids 13, 2001) then gives the pulled population
+ *   q < 1/2:  2q f*_ibar(x) + (1 - 2q) f*_ibar(x + c_i) + m_i
+ *             (half-way bounce-back f*_ibar(x) + m_i where x + c_i is a
+ *             roller node too),
+ *   q >= 1/2: [f*_ibar(x) + (2q - 1) f*_i(x) + m_i] / (2q),
+ * with the moving-wall term m_i = 2 w_i rho0 (c_i . u_w) / cs^2 of the
+ * roller's rotation (g alike, with phi(x, t) in place of rho0).  The wall
+ * then sits on the circle to second order instead of on the staircase.
+ * Runs on the per-node kernels; batches and servers do not take it. */
+#define FRE_FLAG_INTERPOLATED_WALLS 32u
 /* Bits 8..15: log2 of the x-chunk width of the row kernels (0 = automatic:
  * 128 when nx allows it, else the whole row).  A tuning knob; every valid
  * width computes the same update. */

@@ -8,7 +8,8 @@ Python binding.  ``build.build()`` compiles the library in-tree.
 """
 from .binding import (  # noqa: F401
     EXPORTS, FRE_BF16DEV, FRE_D2Q9, FRE_D3Q19, FRE_ERR_ARG, FRE_ERR_BUDGET, FRE_ERR_CUDA, FRE_ERR_OOM,
-    FRE_ERR_STATE, FRE_ERR_UNSTABLE, FRE_FLAG_COUETTE_REFERENCE, FRE_FLAG_REST_REFERENCE, FRE_FOUR_ROLLER, FRE_FP16DEV, FRE_FP32, FRE_FP64, FRE_OK, FRE_PERIODIC,
+    FRE_ERR_STATE, FRE_ERR_UNSTABLE, FRE_FLAG_COUETTE_REFERENCE, FRE_FLAG_INTERPOLATED_WALLS,
+    FRE_FLAG_REST_REFERENCE, FRE_FOUR_ROLLER, FRE_FP16DEV, FRE_FP32, FRE_FP64, FRE_OK, FRE_PERIODIC,
     FRE_SHEAR, Batch, FreError, Server, Simulation, fre_copy_fields, fre_create, fre_destroy, fre_device_bytes,
     fre_components, fre_init_droplet, fre_init_fields, fre_kernel_path, fre_last_error, fre_load_populations,
     fre_moments_noalloc, fre_observables, fre_params, fre_step, fre_step_count, fre_step_timed,
@@ -17,7 +18,8 @@ from .binding import (  # noqa: F401
 
 __all__ = [
     "EXPORTS", "FRE_BF16DEV", "FRE_D2Q9", "FRE_D3Q19", "FRE_ERR_ARG", "FRE_ERR_BUDGET", "FRE_ERR_CUDA",
-    "FRE_ERR_OOM", "FRE_ERR_STATE", "FRE_ERR_UNSTABLE", "FRE_FLAG_COUETTE_REFERENCE", "FRE_FLAG_REST_REFERENCE", "FRE_FOUR_ROLLER", "FRE_FP16DEV", "FRE_FP32",
+    "FRE_ERR_OOM", "FRE_ERR_STATE", "FRE_ERR_UNSTABLE", "FRE_FLAG_COUETTE_REFERENCE", "FRE_FLAG_INTERPOLATED_WALLS",
+    "FRE_FLAG_REST_REFERENCE", "FRE_FOUR_ROLLER", "FRE_FP16DEV", "FRE_FP32",
     "FRE_FP64", "FRE_OK", "FRE_PERIODIC", "FRE_SHEAR", "Batch", "FreError", "Server", "Simulation", "fre_copy_fields",
     "fre_components", "fre_create", "fre_destroy", "fre_device_bytes", "fre_init_droplet", "fre_init_fields", "fre_kernel_path",
     "fre_last_error", "fre_load_populations", "fre_moments_noalloc", "fre_observables", "fre_params",

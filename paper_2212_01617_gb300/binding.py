@@ -42,6 +42,7 @@ FRE_FLAG_GENERIC_KERNELS = 1
 FRE_FLAG_COUETTE_REFERENCE = 4
 FRE_FLAG_REST_REFERENCE = 8
 FRE_FLAG_TEST_PIPELINE_STALL = 16
+FRE_FLAG_INTERPOLATED_WALLS = 32
 
 
 class FreError(RuntimeError):

@@ -150,6 +150,8 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
                            std::isfinite(p->kappa2) && std::isfinite(p->alpha)))
         return bad("model 1 needs finite kappa1, kappa2, alpha >= 0");
     if (p->device == FRE_FOUR_ROLLER && (p->nx < 8 || p->ny < 8)) return bad("four-roller needs nx, ny >= 8");
+    if ((p->flags & FRE_FLAG_INTERPOLATED_WALLS) && p->device != FRE_FOUR_ROLLER)
+        return bad("FRE_FLAG_INTERPOLATED_WALLS applies to the four-roller device only");
     long long n = (long long)p->nx * p->ny * p->nz;
     if (n > (1LL << 30)) return bad("too many nodes (limit 2^30)");
     s.q = p->lattice == FRE_D2Q9 ? 9 : 19;
@@ -219,6 +221,8 @@ void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<in
         G.rcy[k] = g.rcy[k];
         G.om[k] = g.om[k];
     }
+    G.rr = p.nx / 8.0;
+    G.interp = (p.flags & FRE_FLAG_INTERPOLATED_WALLS) ? 1 : 0;
     const size_t plane = (size_t)p.nx * p.ny;
     solid.resize((size_t)G.n);
     for (int z = 0; z < p.nz; ++z) std::memcpy(solid.data() + (size_t)z * plane, g.id.data(), plane);
@@ -554,14 +558,16 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     c->G.solid = c->solid;
     c->G.rlinks = c->rlinks;
     c->G.n_rlinks = c->n_rlinks;
-    // the full functional (model 1) runs on the per-node kernels
-    if (!(p->flags & FRE_FLAG_GENERIC_KERNELS) && p->model == 0 && c->ks->row_width) {
+    // the full functional (model 1) and the interpolated roller walls run
+    // on the per-node kernels
+    const bool per_node = (p->flags & (FRE_FLAG_GENERIC_KERNELS | FRE_FLAG_INTERPOLATED_WALLS)) || p->model != 0;
+    if (!per_node && c->ks->row_width) {
         const unsigned sh = (p->flags >> FRE_FLAG_CHUNK_SHIFT) & 0xffu;
         c->row_w = c->ks->row_width(c->G, sh ? (1 << sh) : 0);
         c->rows = c->row_w > 0;
     }
     // the four-roller device has no chunked row kernels, only full rows
-    c->fullrow = !(p->flags & FRE_FLAG_GENERIC_KERNELS) && p->model == 0 && (c->rows || p->device == FRE_FOUR_ROLLER) &&
+    c->fullrow = !per_node && (c->rows || p->device == FRE_FOUR_ROLLER) &&
                  !(p->flags & FRE_FLAG_CHUNKED_UPDATE) && c->ks->fullrow_usable && c->ks->fullrow_usable(c->G);
     cudaGetLastError();
     *out = c;

@@ -374,6 +374,8 @@ fre_status fre::batch_attach(fre_batch *b, fre_ctx *c, size_t bytes, int *slot) 
         return bfail(FRE_ERR_ARG, "batch_attach: lattice, precision and stream must match the batch%s");
     if (!c->initialised) return bfail(FRE_ERR_STATE, "batch_attach: context not initialised%s");
     if (c->p.model != 0) return bfail(FRE_ERR_ARG, "batch_attach: batches run the reduced functional (model 0)%s");
+    if (c->p.flags & FRE_FLAG_INTERPOLATED_WALLS)
+        return bfail(FRE_ERR_ARG, "batch_attach: batches run half-way bounce-back at the rollers%s");
     if (b->in_use + bytes > b->budget) return bfail(FRE_ERR_BUDGET, "batch_attach: device-memory budget exceeded%s");
     int k = 0;
     while (k < (int)b->slots.size() && b->slots[k]) ++k;
@@ -447,6 +449,8 @@ fre_status fre_batch_add(fre_batch *b, const fre_params *p, double cx, double cy
     if (p->lattice != b->lattice || p->precision != b->precision)
         return bfail(FRE_ERR_ARG, "fre_batch_add: lattice and precision must match the batch%s");
     if (p->model != 0) return bfail(FRE_ERR_ARG, "fre_batch_add: batches run the reduced functional (model 0)%s");
+    if (p->flags & FRE_FLAG_INTERPOLATED_WALLS)
+        return bfail(FRE_ERR_ARG, "fre_batch_add: batches run half-way bounce-back at the rollers%s");
     const size_t bytes = fre_device_bytes(p);
     if (bytes == 0) return bfail(FRE_ERR_ARG, "fre_batch_add: invalid parameters%s");
     if (b->in_use + bytes > b->budget) return bfail(FRE_ERR_BUDGET, "fre_batch_add: device-memory budget exceeded%s");

@@ -25,6 +25,8 @@ struct Geo {
     const int4 *rlinks;
     int n_rlinks;
     double rcx[5], rcy[5], om[5];  // roller centres and angular velocities (1..4)
+    double rr;                // roller radius
+    int interp;               // four-roller: interpolated bounce-back at the roller surfaces
     double uwall;             // shear wall speed
 };
 

@@ -298,6 +298,11 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
     const long long np = L.G.np;
     const int n = s.n;
     T ws = T(0);
+    // f_i - w_i rho0 (16-bit formats) or f_i as stored
+    auto ldW = [&](int i, int k, T Uk) -> T {
+        if constexpr (DEV) return P::ldw(L.src, np, i, k, rho0, Uk);
+        else return P::ldf(L.src, np, i, k, rho0, Uk);
+    };
     // f_i from W_i (16-bit formats) or as stored
     auto ldf = [&](int i, int k, T Uk, T extra) {
         if constexpr (DEV) {
@@ -324,9 +329,56 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
             const int o = Lat<Q>::opp(i);
             const T cu = T(Lat<Q>::cx(i)) * uwx + T(Lat<Q>::cy(i)) * uwy;
             const T wi2 = T(2.0 * Lat<Q>::w(i) * 3.0);
+            const T php = static_cast<const T *>(L.phi_prev)[n];
+            if (L.G.interp) {
+                // Four-roller, interpolated bounce-back (linear, Bouzidi,
+                // Firdaouss and Lallemand 2001): the roller surface cuts the
+                // link at x - q c_i.  q < 1/2: the opposite population
+                // interpolated between x and x + c_i before it is reflected,
+                // 2q f*_ibar(x) + (1 - 2q) f*_ibar(x + c_i) (half-way
+                // bounce-back where x + c_i is solid too); q >= 1/2: the
+                // reflected one interpolated with the node's own,
+                // [f*_ibar(x) + (2q - 1) f*_i(x)] / (2q).  The moving-wall
+                // term takes weight 1 and 1/(2q) respectively; c_i . u_w is
+                // the same at every point of the link (the rotation's
+                // c_i x (p - c_k) does not change along c_i).  The weights
+                // of each rule sum to 1, so 16-bit deviations combine alike.
+                const int k = L.G.solid[site_src<Q>(s, i)];
+                const double ex = Lat<Q>::cx(i), ey = Lat<Q>::cy(i);
+                const double dx = s.x - L.G.rcx[k], dy = s.y - L.G.rcy[k];
+                const double cc = ex * ex + ey * ey, dc = dx * ex + dy * ey;
+                const double dd = dx * dx + dy * dy - L.G.rr * L.G.rr;
+                const double disc = dc * dc - cc * dd;
+                double qd = (dc - sqrt(disc > 0.0 ? disc : 0.0)) / cc;  // first crossing
+                qd = qd <= 0.0 ? 1e-12 : (qd > 1.0 ? 1.0 : qd);
+                const T q2 = T(2.0 * qd);
+                const T lf = wi2 * rho0 * cu, lg = wi2 * php * cu;
+                const int nb = site_nb<Q>(s, i);
+                T Wv, gv;
+                if (qd < 0.5 && !L.G.solid[nb]) {
+                    const T Unb = DEV ? T(couette_u(L, s.y + Lat<Q>::cy(i))) : T(0);
+                    Wv = q2 * ldW(o, n, U) + (T(1) - q2) * ldW(o, nb, Unb) + lf;
+                    gv = q2 * P::ldg(L.src, np, o, n) + (T(1) - q2) * P::ldg(L.src, np, o, nb) + lg;
+                } else if (qd >= 0.5) {
+                    Wv = (ldW(o, n, U) + (q2 - T(1)) * ldW(i, n, U) + lf) / q2;
+                    gv = (P::ldg(L.src, np, o, n) + (q2 - T(1)) * P::ldg(L.src, np, i, n) + lg) / q2;
+                } else {
+                    Wv = ldW(o, n, U) + lf;
+                    gv = P::ldg(L.src, np, o, n) + lg;
+                }
+                if (WANT_F) {
+                    if constexpr (DEV) {
+                        ws += Wv;
+                        f[i] = Wv + T(Lat<Q>::w(i)) * rho0;
+                    } else {
+                        f[i] = Wv;
+                    }
+                }
+                g[i] = gv;
+                continue;
+            }
             // w_opp(i) = w_i: the opposite's deviation carries over
             if (WANT_F) f[i] = ldf(o, n, U, wi2 * rho0 * cu);
-            const T php = static_cast<const T *>(L.phi_prev)[n];
             g[i] = P::ldg(L.src, np, o, n) + wi2 * php * cu;
         }
     }
