@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256) k_batch(const Launch *__restrict__ cases,
         }
     }
     __syncthreads();
+    pdl_wait();
     const Launch &L = sL;
     const int x = corner[0] + (int)(threadIdx.x % BX), y = corner[1] + (int)(threadIdx.x / BX), z = corner[2];
     if (x >= L.G.nx || y >= L.G.ny || z >= L.G.nz) return;
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(256) k_batch_ghost(const Launch *__restrict__ 
     const int slot = batch_slot(start, nslots, blockIdx.x);
     const Launch &L = cases[slot];
     const int t = (blockIdx.x - __ldg(start + slot)) * 256 + threadIdx.x;
+    pdl_wait();
     if (t >= L.n_ghost) return;
     node_ghost<Q, T>(L, static_cast<T *>(field ? L.mu : L.phi), t);
 }
@@ -82,9 +84,9 @@ struct BatchLaunchers {
     static void run(const BatchLaunch &B, int bx) {
         if (B.total_blocks <= 0) return;
         switch (bx) {
-            case 32: k_batch<Q, FMT, 32, KIND><<<B.total_blocks, 256, 0, B.stream>>>(B.cases, B.block_start, B.nslots); break;
-            case 128: k_batch<Q, FMT, 128, KIND><<<B.total_blocks, 256, 0, B.stream>>>(B.cases, B.block_start, B.nslots); break;
-            default: k_batch<Q, FMT, 64, KIND><<<B.total_blocks, 256, 0, B.stream>>>(B.cases, B.block_start, B.nslots); break;
+            case 32: launch_pdl(k_batch<Q, FMT, 32, KIND>, dim3(B.total_blocks), dim3(256), 0, B.stream, B.cases, B.block_start, B.nslots); break;
+            case 128: launch_pdl(k_batch<Q, FMT, 128, KIND>, dim3(B.total_blocks), dim3(256), 0, B.stream, B.cases, B.block_start, B.nslots); break;
+            default: launch_pdl(k_batch<Q, FMT, 64, KIND>, dim3(B.total_blocks), dim3(256), 0, B.stream, B.cases, B.block_start, B.nslots); break;
         }
     }
     static void phi(const BatchLaunch &B, int bx) { run<B_PHI>(B, bx); }
@@ -92,7 +94,7 @@ struct BatchLaunchers {
     static void update(const BatchLaunch &B, int bx) { run<B_UPDATE>(B, bx); }
     static void ghost(const BatchLaunch &B, int field) {
         if (B.total_ghost_blocks > 0)
-            k_batch_ghost<Q, FMT><<<B.total_ghost_blocks, 256, 0, B.stream>>>(B.cases, B.ghost_start, B.nslots, field);
+            launch_pdl(k_batch_ghost<Q, FMT>, dim3(B.total_ghost_blocks), dim3(256), 0, B.stream, B.cases, B.ghost_start, B.nslots, field);
     }
     static const BatchKernels *set() {
         static const BatchKernels k = {phi, mu, ghost, update};

@@ -23,6 +23,35 @@
 
 namespace fre {
 
+// Programmatic dependent launch (sm_90 and later).  The kernels of a time
+// step are launched with launch_pdl: each may start (block scheduling,
+// shared-memory and barrier set-up, reads of launch tables) while the
+// kernel before it in the stream is still finishing, and waits for that
+// kernel's completion and memory (griddepcontrol.wait, pdl_wait) before it
+// reads or writes any field or population.  The persistent row kernels let
+// their successor start once a block is done with its units (pdl_trigger);
+// the others when they exit.  The wait is a no-op for a kernel launched
+// without the attribute, and a kernel launched normally after one of these
+// starts only when it ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       const Args &...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, fn, args...);
+}
+
 constexpr int kBlock = 256;
 
 template <int FMT>
@@ -495,6 +524,7 @@ __device__ __forceinline__ void node_phi(const Launch &L, const Site &s) {
 
 template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock) k_phi(Launch L) {
+    pdl_wait();
     FRE_SITE_OR_RETURN(L, s);
     if (is_solid(L.G, s.n)) return;
     node_phi<Q, FMT, PULL>(L, s);
@@ -519,6 +549,7 @@ __device__ __forceinline__ void node_ghost(const Launch &L, T *field, int t) {
 
 template <int Q, typename T>
 __global__ void __launch_bounds__(kBlock) k_ghost(Launch L, T *field) {
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L.n_ghost) return;
     node_ghost<Q, T>(L, field, t);
@@ -561,6 +592,7 @@ __device__ __forceinline__ void node_mu(const Launch &L, const Site &s) {
 
 template <int Q, typename T>
 __global__ void __launch_bounds__(kBlock) k_mu(Launch L) {
+    pdl_wait();
     FRE_SITE_OR_RETURN(L, s);
     if (is_solid(L.G, s.n)) return;
     node_mu<Q, T>(L, s);
@@ -648,6 +680,7 @@ __global__ void __launch_bounds__(kBlock) k_reflect(Launch L) {
     static_assert(FMT != FRE_FP64, "the row kernels compute in FP32");
     using S = typename Fmt<FMT>::S;
     constexpr bool DEV = Fmt<FMT>::DEV;
+    pdl_wait();
     const int nl = L.G.n_rlinks;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)nl * L.G.nz) return;
@@ -672,6 +705,7 @@ __global__ void __launch_bounds__(kBlock) k_reflect(Launch L) {
 
 template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock) k_update(Launch L) {
+    pdl_wait();
     FRE_SITE_OR_RETURN(L, s);
     if (is_solid(L.G, s.n)) return;
     node_update<Q, FMT, PULL>(L, s);
@@ -682,6 +716,7 @@ __global__ void __launch_bounds__(kBlock) k_update(Launch L) {
 // FP32 211 -> 198 us, FP16 283 -> 226 us).  D2Q9 fits five blocks unbounded.
 template <int Q, int FMT, bool PULL>
 __global__ void __launch_bounds__(kBlock, 4) k_update4(Launch L) {
+    pdl_wait();
     FRE_SITE_OR_RETURN(L, s);
     if (is_solid(L.G, s.n)) return;
     node_update<Q, FMT, PULL>(L, s);
@@ -1153,22 +1188,22 @@ struct Launchers {
     using T = typename Fmt<FMT>::T;
 
     static void phi(const Launch &L, bool pull) {
-        if (pull) k_phi<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
-        else k_phi<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+        if (pull) launch_pdl(k_phi<Q, FMT, true>, grid3(L.G), dim3(kBlock), 0, L.stream, L);
+        else launch_pdl(k_phi<Q, FMT, false>, grid3(L.G), dim3(kBlock), 0, L.stream, L);
     }
     static void ghost(const Launch &L, void *field) {
         if (L.n_ghost > 0)
-            k_ghost<Q, T><<<grid_for(L.n_ghost), kBlock, 0, L.stream>>>(L, static_cast<T *>(field));
+            launch_pdl(k_ghost<Q, T>, dim3(grid_for(L.n_ghost)), dim3(kBlock), 0, L.stream, L, static_cast<T *>(field));
     }
-    static void mu(const Launch &L) { k_mu<Q, T><<<grid3(L.G), kBlock, 0, L.stream>>>(L); }
+    static void mu(const Launch &L) { launch_pdl(k_mu<Q, T>, grid3(L.G), dim3(kBlock), 0, L.stream, L); }
     static void update(const Launch &L, bool pull) {
         if constexpr (Q == 19 && FMT != FRE_FP64) {
-            if (pull) k_update4<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
-            else k_update4<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+            if (pull) launch_pdl(k_update4<Q, FMT, true>, grid3(L.G), dim3(kBlock), 0, L.stream, L);
+            else launch_pdl(k_update4<Q, FMT, false>, grid3(L.G), dim3(kBlock), 0, L.stream, L);
             return;
         }
-        if (pull) k_update<Q, FMT, true><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
-        else k_update<Q, FMT, false><<<grid3(L.G), kBlock, 0, L.stream>>>(L);
+        if (pull) launch_pdl(k_update<Q, FMT, true>, grid3(L.G), dim3(kBlock), 0, L.stream, L);
+        else launch_pdl(k_update<Q, FMT, false>, grid3(L.G), dim3(kBlock), 0, L.stream, L);
     }
     static void obs(const Launch &L, bool pull) {
         const int nb = L.red_blocks;
@@ -1202,7 +1237,7 @@ struct Launchers {
     static void reflect(const Launch &L) {
         if constexpr (FMT != FRE_FP64) {
             const long long nt = (long long)L.G.n_rlinks * L.G.nz;
-            if (nt > 0) k_reflect<FMT><<<(unsigned)((nt + kBlock - 1) / kBlock), kBlock, 0, L.stream>>>(L);
+            if (nt > 0) launch_pdl(k_reflect<FMT>, dim3((unsigned)((nt + kBlock - 1) / kBlock)), dim3(kBlock), 0, L.stream, L);
         }
     }
     static void mei_prep(const Launch &L) { k_mei_prep<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L); }

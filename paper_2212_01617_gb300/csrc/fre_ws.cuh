@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
         fence_async_smem();
     }
     __syncthreads();
+    pdl_wait();
 
     if (producer) {
         // ------------------------------------------------------ producer warp
@@ -344,6 +345,8 @@ __global__ void __launch_bounds__(288) k_ws(Launch L, int W, int nunits) {
         }
     }
     if (KIND == WS_UPDATE && xl < 32) bulk_wait_all();
+    // this block is done with its units: the next kernel may start
+    pdl_trigger();
 }
 
 template <int Q, int FMT>
@@ -377,7 +380,7 @@ struct WsLaunchers {
         LaunchShape::opt_in((const void *)fn, kMaxSmem);
         const int g = std::min(nu, LaunchShape::sms() *
                                        LaunchShape::blocks_per_sm((const void *)fn, W + 32, smem));
-        fn<<<g, W + 32, smem, L.stream>>>(L, W, nu);
+        launch_pdl(fn, dim3(g), dim3(W + 32), smem, L.stream, L, W, nu);
     }
     template <int KIND, bool PULL>
     static void run(const Launch &L) {
@@ -684,6 +687,7 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
         fence_async_smem();
     }
     __syncthreads();
+    pdl_wait();
 
     if (producer) {
         // test of the timeout path: no copies are issued, so every consumer
@@ -1144,6 +1148,8 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
             }
         }
     }
+    // this block is done with its units: the next kernel may start
+    pdl_trigger();
 }
 
 // The pulled update of the four-roller device on the row kernels (roller
@@ -1206,7 +1212,7 @@ struct WsRowLaunchers {
         const int threads = RPX * (nx / 2) + 32;
         const int g = std::min(nu, LaunchShape::sms() *
                                        LaunchShape::blocks_per_sm((const void *)fn, threads, smem));
-        fn<<<g, threads, smem, L.stream>>>(L, nu);
+        launch_pdl(fn, dim3(g), dim3(threads), smem, L.stream, L, nu);
     }
     // resident blocks per SM of one launch shape
     template <int KIND, bool PULL, int NST, int R, int NXC, int RPX, bool ROLL = false>
