@@ -441,12 +441,12 @@ def run_batch_workload(args):
     (autotuned batched, per-slot or concurrent per-slot launches, CUDA-graph
     replays) against one context per case stepped on its own (one launch per
     kernel per case)."""
-    line = batch_summary(args.steps, max(args.warmup, 40))
+    line = batch_summary(args.steps, max(args.warmup, 40), args.batch_mode)
     print(json.dumps(line), flush=True)
     return 0
 
 
-def batch_summary(steps, warmup):
+def batch_summary(steps, warmup, mode=None):
     import torch
     import paper_2212_01617_gb300 as fre
     from paper_2212_01617_gb300 import inputs
@@ -456,14 +456,18 @@ def batch_summary(steps, warmup):
     # bracket all the work and the per-case launches run one after another
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        return _batch_workload(steps, warmup, fre, cases, nodes, stream)
+        return _batch_workload(steps, warmup, fre, cases, nodes, stream, mode)
 
 
-def _batch_workload(steps, warmup, fre, cases, nodes, stream):
+def _batch_workload(steps, warmup, fre, cases, nodes, stream, mode=None):
     import torch
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     b = fre.Batch("d2q9", "fp32")
+    if mode is not None:
+        # launch mode pinned (for profiling): no autotuning
+        m, _, bx = mode.partition(":")
+        b.set_mode(int(m), int(bx) if bx else 64)
     for p, d in cases:
         b.add(*d, **p)
     b.step(warmup)  # includes the autotuner's timed candidates
@@ -661,6 +665,8 @@ def main():
     ap.add_argument("--workload", choices=["lattice", "batch", "serve"], default="lattice",
                     help="lattice: the 512x256x256 D3Q19 lattice (default); batch: 64 uneven D2Q9 cases; "
                          "serve: Poisson-arriving D3Q19 requests through the serving loop")
+    ap.add_argument("--batch-mode", default=None,
+                    help="MODE[:BX] pins the batch's launch mode (0 batched, 1 per-slot, 2 concurrent) for profiling")
     ap.add_argument("--no-batch-serve", action="store_true",
                     help="leave the batch and serving summaries out of the default line")
     ap.add_argument("--summary-requests", type=int, default=12,
