@@ -927,3 +927,33 @@ def test_taylor_deformation_golden():
     taylor = 35.0 / 32.0 * g["Ca_end"]
     assert abs(g["D"] - taylor) < 0.05 * taylor, (g["D"], taylor)
     assert abs(g["theta_deg"] - 45.0) < 3.0
+
+
+def test_four_roller_taylor_golden():
+    """Steady deformation of a droplet at the stagnation point of the 3D
+    four-roller device (interpolated bounce-back at the rollers), viscosity
+    ratio 1: the small-deformation theory of planar extension,
+    D = (35/16) Ca with Ca = mu eps R / sigma (twice the shear value at the
+    same strain rate), within 10%; the long axis along the stretching
+    direction x; the centre flow a planar extension, du_y/dy = -du_x/dx.
+    The stored values are the oracle's, written by
+    tests/golden/make_four_roller.py (R = 10, Ca near 0.034, eps measured on
+    the droplet-free flow)."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_four_roller", os.path.join(here, "make_four_roller.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    with open(os.path.join(here, "four_roller_d3q19.json")) as fh:
+        g = json.load(fh)
+    assert g["case"] == mk.CASE and g["flow_steps"] == mk.FLOW_STEPS and g["drop_steps"] == mk.DROP_STEPS
+    assert g["eps"] > 0 and abs(g["eps"] + g["eps_y"]) < 1e-3 * g["eps"]
+    sigma = (8.0 * mk.CASE["kappa"] * mk.CASE["A"] / 9.0) ** 0.5
+    mu = mk.CASE["rho0"] * (mk.CASE["tau_f"] - 0.5) / 3.0
+    ca_end = mu * g["eps"] * g["R_end"] / sigma
+    assert abs(ca_end - g["Ca_end"]) < 1e-12
+    taylor = 35.0 / 16.0 * ca_end
+    assert abs(g["D"] - taylor) < 0.10 * taylor, (g["D"], taylor)
+    assert abs(g["theta_deg"]) < 3.0
