@@ -83,7 +83,10 @@ int wrap_host(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // The wall links of one plane: population i at fluid node (x, y) whose
 // source (x, y) - c_i is a roller node of roller k, as the table of
-// k_reflect (Geo::rlinks).  The moving-wall coefficient is
+// k_reflect (Geo::rlinks), ordered by i, then y, then x, so that the
+// neighbouring threads of a warp read and write the same population plane
+// at neighbouring boundary nodes (shared sectors where the boundary runs
+// along x).  The moving-wall coefficient is
 // 2 w_i (c_i . u_w) / cs^2 with u_w = omega_k z x (p - c_k) at the link's
 // wall point p = x - c_i / 2; the shift along c_i drops out of c_i x (p - c_k),
 // so c_i . u_w = omega_k (c_iy (x - x_k) - c_ix (y - y_k)).  Returns the
@@ -91,10 +94,10 @@ int wrap_host(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::vector<int4> *out) {
     if (out) out->clear();
     long long count = 0;
-    for (int y = 0; y < p.ny; ++y)
-        for (int x = 0; x < p.nx; ++x) {
-            if (g.id[(size_t)y * p.nx + x]) continue;
-            for (int i = 1; i < q; ++i) {
+    for (int i = 1; i < q; ++i)
+        for (int y = 0; y < p.ny; ++y)
+            for (int x = 0; x < p.nx; ++x) {
+                if (g.id[(size_t)y * p.nx + x]) continue;
                 const int *ci = q == 9 ? kC9[i] : kC19[i];
                 const int xs = wrap_host(x - ci[0], p.nx), ys = wrap_host(y - ci[1], p.ny);
                 const int k = g.id[(size_t)ys * p.nx + xs];
@@ -117,7 +120,6 @@ long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::ve
                 std::memcpy(&e.w, &coef, sizeof(float));
                 out->push_back(e);
             }
-        }
     return count;
 }
 
