@@ -9,8 +9,8 @@ Two oracle runs: the droplet-free flow, from which the strain rate eps =
 du_x/dx at the centre is measured once the flow is steady, and then a
 droplet placed in that flow, stepped until its deformation settles.
 
-Calls only oracle/.  Run from the repository root (about half an hour on
-eight cores):
+Calls only oracle/.  Run from the repository root (about an hour on eight
+cores):
     python tests/golden/make_four_roller.py
 """
 import json
@@ -35,8 +35,10 @@ import oracle  # noqa: E402
 # theory), Reynolds number eps R^2 / nu below 0.05.
 CASE = dict(nx=128, ny=128, nz=48, R=10.0, A=0.04, kappa=0.04, tau_f=2.0, tau_g=1.0, Gamma=0.02, rho0=1.0,
             u_wall=0.01, interp=1)
-FLOW_STEPS = 6000    # droplet-free run (eps within 0.1% of its value at 16000 steps)
-DROP_STEPS = 8000    # droplet run (D settles within 5000 steps), sampled every SAMPLE steps
+FLOW_STEPS = 4000    # droplet-free run (eps within 0.05% of its value at 16000 steps)
+DROP_STEPS = 16000   # droplet run, sampled every SAMPLE steps: D overshoots within
+                     # 5000 steps and relaxes over the box's viscous time
+                     # (N^2 / nu ~ 3e4 steps), a few percent more
 SAMPLE = 1000
 AVG = 4              # D: mean of the last AVG samples
 FIT = 8              # eps: slope of u_x over x within +-FIT nodes of the centre
