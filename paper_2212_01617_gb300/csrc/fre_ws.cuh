@@ -636,6 +636,164 @@ __device__ __forceinline__ void couette_consts(const Launch &L, const CoLane &c,
     }
 }
 
+// Producer: copy group gi (the phi / mu stencil rows of one z plane) of
+// the unit of rows y0 .. y0 + R - 1 of plane z into the stage buf, completing
+// on the mbarrier bar.
+template <int Q, int FMT, int KIND, int R>
+__device__ __forceinline__ void stage_field_group(const Launch &L, unsigned char *buf, unsigned bar, int gi,
+                                                  int y0, int z, int nx, int ny, int nz, bool shear) {
+    using FL = RowsLayout<Q, FMT, KIND, R>;
+    // ---- phi / mu stencil rows of one z plane
+    const int j = KIND == WS_MU ? gi : gi - 2 * Q;
+    const int fld = KIND == WS_MU ? 0 : j / (FL::NGRP > 0 ? FL::NGRP : 1);
+    const int grp = KIND == WS_MU ? j : j - fld * FL::NGRP;
+    // mu pass groups: cz = -1, 0, +1 (3D); update: cz = 0, +1, -1
+    const int cz = KIND == WS_MU ? (Lat<Q>::D == 3 ? grp - 1 : 0) : (grp == 0 ? 0 : (grp == 1 ? 1 : -1));
+    const bool full_y = KIND == WS_MU || cz == 0;  // R + 2 rows with y shifts
+    const int zn = wrapi(z + cz, nz);
+    const float *base = static_cast<const float *>(fld ? L.mu : L.phi) + (size_t)zn * ny * nx;
+    const int k0 = FL::fk(full_y ? -1 : 0, cz, 0);
+    unsigned char *dst = buf + FL::fld_row(nx, fld, k0);
+    if (!full_y) {
+        bulk_load(dst, base + (size_t)y0 * nx, (unsigned)R * FL::fldb(nx), bar);
+    } else if (y0 >= 1 && y0 + R <= ny - 1) {
+        bulk_load(dst, base + (size_t)(y0 - 1) * nx, (unsigned)(R + 2) * FL::fldb(nx), bar);
+    } else {
+        for (int q = 0; q < R + 2; ++q) {
+            int yn = y0 - 1 + q;
+            yn = shear ? (yn < 0 ? 0 : (yn >= ny ? ny - 1 : yn)) : wrapi(yn, ny);
+            bulk_load(dst + q * FL::fldb(nx), base + (size_t)yn * nx, FL::fldb(nx), bar);
+        }
+    }
+}
+
+// Producer: copy group gi (one population row set: lattice f or g, direction
+// i, pulled by -c_i in y and z; wall links of the shear device take the
+// local row of the opposite population) of the unit into the stage buf.
+template <int Q, int FMT, int KIND, int R, bool PULL>
+__device__ __forceinline__ void stage_pop_group(const Launch &L, unsigned char *buf, unsigned bar, int gi, int y0,
+                                                int z, int nx, int ny, int nz, bool shear) {
+    using S = typename Fmt<FMT>::S;
+    using FL = RowsLayout<Q, FMT, KIND, R>;
+    constexpr bool DEV = Fmt<FMT>::DEV;
+    // ---- population rows: lattice lat (0 f, 1 g), direction i
+    const int lat = KIND == WS_PHI ? 1 : (gi >= Q);
+    const int i = KIND == WS_PHI ? gi : gi - lat * Q;
+    const int cy = PULL ? Lat<Q>::cy(i) : 0, cz = PULL ? Lat<Q>::cz(i) : 0;
+    const int zs = wrapi(z - cz, nz);
+    // source plane of population p, its element size, smem row r
+    auto plane = [&](int p) -> const char * {
+        if (!lat) return static_cast<const char *>(L.src.f) + (size_t)p * L.G.np * sizeof(S);
+        if (DEV && p == 0) return reinterpret_cast<const char *>(L.src.g0);
+        return static_cast<const char *>(L.src.g) + (size_t)(DEV ? p - 1 : p) * L.G.np * sizeof(S);
+    };
+    const unsigned esz = (lat && DEV && i == 0) ? 4u : (unsigned)sizeof(S);
+    const unsigned rb = (unsigned)nx * esz;
+    auto smrow = [&](int r) -> unsigned { return lat ? FL::g_row(nx, i, r) : FL::f_row(nx, i, r); };
+    const int ys0 = y0 - cy;
+    const bool inside = ys0 >= 0 && ys0 + R - 1 <= ny - 1;
+    if (inside) {
+        bulk_load(buf + smrow(0), plane(i) + ((size_t)zs * ny + ys0) * nx * esz, (unsigned)R * rb, bar);
+    } else {
+        for (int r = 0; r < R; ++r) {
+            int ys = y0 + r - cy;
+            int pi = i, zr = zs;
+            if (ys < 0 || ys >= ny) {
+                if (shear) {
+                    // wall link: the local row of the opposite population
+                    ys = y0 + r;
+                    zr = z;
+                    pi = Lat<Q>::opp(i);
+                } else {
+                    ys = wrapi(ys, ny);
+                }
+            }
+            bulk_load(buf + smrow(r), plane(pi) + ((size_t)zr * ny + ys) * nx * esz, rb, bar);
+        }
+    }
+}
+
+// Consumers: phi = sum of the pulled g (with the moving-wall term on wall
+// links) of the rows of a unit from its stage cur; the warp releases the
+// stage (mbarrier empty_bar) before it stores phi.  wall_r[r]: bit i set when
+// population i of row r pulls through a shear wall.
+template <int Q, int FMT, int R, int RP, bool PULL>
+__device__ __forceinline__ void phi_unit(const Launch &L, const unsigned char *cur, const unsigned *wall_r, int nx,
+                                         int ny, int x0, int rg, int y0, int z, unsigned empty_bar) {
+    using S = typename Fmt<FMT>::S;
+    using FL = RowsLayout<Q, FMT, WS_PHI, R>;
+    constexpr bool DEV = Fmt<FMT>::DEV;
+    const float *__restrict__ php = static_cast<const float *>(L.phi_prev);
+    constexpr int RT = R / RP;  // rows of this thread's group
+    float2 out[RT];
+#pragma unroll
+    for (int q = 0; q < RT; ++q) {
+        const int r = rg + q * RP;
+        const unsigned wall = wall_r[r];
+        const size_t row = ((size_t)z * ny + y0 + r) * nx;
+        // rows without wall links (all but the first and last of the
+        // shear device) take every shift as a compile-time constant
+        auto pull_sum = [&](auto walls) {
+            constexpr bool WL = decltype(walls)::value;
+            float2 sum = p2(0.f);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const bool wl = WL && Lat<Q>::cy(i) != 0 && ((wall >> i) & 1u);
+                const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
+                float2 gv;
+                if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
+                else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
+                if (wl) {
+                    const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
+                    const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
+                    gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
+                }
+                sum = add2(sum, gv);
+            }
+            return sum;
+        };
+        out[q] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(empty_bar);
+#pragma unroll
+    for (int q = 0; q < RT; ++q)
+        st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
+}
+
+// Consumers: mu = A (phi^3 - phi) - kappa lap(phi) of the rows of a unit from
+// the staged phi stencil rows; the warp releases the stage before it stores.
+template <int Q, int FMT, int R, int RP>
+__device__ __forceinline__ void mu_unit(const Launch &L, const unsigned char *cur, int nx, int ny, int x0, int rg,
+                                        int y0, int z, unsigned empty_bar) {
+    using FL = RowsLayout<Q, FMT, WS_MU, R>;
+    constexpr int RT = R / RP;  // rows of this thread's group
+    float2 out[RT];
+#pragma unroll
+    for (int q = 0; q < RT; ++q) {
+        const int r = rg + q * RP;
+        const float *c0 = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(0, 0, r)));
+        const float2 p0 = ld_pair(c0, x0);
+        float2 lap = p2(0.f);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const float *rw = reinterpret_cast<const float *>(
+                cur + FL::fld_row(nx, 0, FL::fk(Lat<Q>::cy(i), Lat<Q>::cz(i), r)));
+            // stencil reads x + c, i.e. a shift by -c
+            lap = fma2(p2(float(Lat<Q>::w(i))), sub2(ld_shift(rw, x0, -Lat<Q>::cx(i), nx), p0), lap);
+        }
+        lap = mul2(p2(6.f), lap);
+        // A (phi^3 - phi) - kappa lap
+        out[q] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
+                      mul2(p2(L.F.kappa), lap));
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(empty_bar);
+#pragma unroll
+    for (int q = 0; q < RT; ++q)
+        st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
+}
+
 // Rows of a work unit run side by side, one consumer group of nx/2 threads
 // each (the kernel's RPX): the update takes all R rows of a unit at once;
 // the phi and mu passes loop over them, except on rows whose half length is
@@ -725,66 +883,10 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
             }
             __syncwarp();
             for (int gi = lane; gi < FL::ngroups(); gi += 32) {
-                if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q)) {
-                    // ---- phi / mu stencil rows of one z plane
-                    const int j = KIND == WS_MU ? gi : gi - 2 * Q;
-                    const int fld = KIND == WS_MU ? 0 : j / (FL::NGRP > 0 ? FL::NGRP : 1);
-                    const int grp = KIND == WS_MU ? j : j - fld * FL::NGRP;
-                    // mu pass groups: cz = -1, 0, +1 (3D); update: cz = 0, +1, -1
-                    const int cz = KIND == WS_MU ? (Lat<Q>::D == 3 ? grp - 1 : 0) : (grp == 0 ? 0 : (grp == 1 ? 1 : -1));
-                    const bool full_y = KIND == WS_MU || cz == 0;  // R + 2 rows with y shifts
-                    const int zn = wrapi(z + cz, nz);
-                    const float *base = static_cast<const float *>(fld ? L.mu : L.phi) + (size_t)zn * ny * nx;
-                    const int k0 = FL::fk(full_y ? -1 : 0, cz, 0);
-                    unsigned char *dst = buf + FL::fld_row(nx, fld, k0);
-                    if (!full_y) {
-                        bulk_load(dst, base + (size_t)y0 * nx, (unsigned)R * FL::fldb(nx), bar);
-                    } else if (y0 >= 1 && y0 + R <= ny - 1) {
-                        bulk_load(dst, base + (size_t)(y0 - 1) * nx, (unsigned)(R + 2) * FL::fldb(nx), bar);
-                    } else {
-                        for (int q = 0; q < R + 2; ++q) {
-                            int yn = y0 - 1 + q;
-                            yn = shear ? (yn < 0 ? 0 : (yn >= ny ? ny - 1 : yn)) : wrapi(yn, ny);
-                            bulk_load(dst + q * FL::fldb(nx), base + (size_t)yn * nx, FL::fldb(nx), bar);
-                        }
-                    }
-                    continue;
-                }
-                // ---- population rows: lattice lat (0 f, 1 g), direction i
-                const int lat = KIND == WS_PHI ? 1 : (gi >= Q);
-                const int i = KIND == WS_PHI ? gi : gi - lat * Q;
-                const int cy = PULL ? Lat<Q>::cy(i) : 0, cz = PULL ? Lat<Q>::cz(i) : 0;
-                const int zs = wrapi(z - cz, nz);
-                // source plane of population p, its element size, smem row r
-                auto plane = [&](int p) -> const char * {
-                    if (!lat) return static_cast<const char *>(L.src.f) + (size_t)p * L.G.np * sizeof(S);
-                    if (DEV && p == 0) return reinterpret_cast<const char *>(L.src.g0);
-                    return static_cast<const char *>(L.src.g) + (size_t)(DEV ? p - 1 : p) * L.G.np * sizeof(S);
-                };
-                const unsigned esz = (lat && DEV && i == 0) ? 4u : (unsigned)sizeof(S);
-                const unsigned rb = (unsigned)nx * esz;
-                auto smrow = [&](int r) -> unsigned { return lat ? FL::g_row(nx, i, r) : FL::f_row(nx, i, r); };
-                const int ys0 = y0 - cy;
-                const bool inside = ys0 >= 0 && ys0 + R - 1 <= ny - 1;
-                if (inside) {
-                    bulk_load(buf + smrow(0), plane(i) + ((size_t)zs * ny + ys0) * nx * esz, (unsigned)R * rb, bar);
-                } else {
-                    for (int r = 0; r < R; ++r) {
-                        int ys = y0 + r - cy;
-                        int pi = i, zr = zs;
-                        if (ys < 0 || ys >= ny) {
-                            if (shear) {
-                                // wall link: the local row of the opposite population
-                                ys = y0 + r;
-                                zr = z;
-                                pi = Lat<Q>::opp(i);
-                            } else {
-                                ys = wrapi(ys, ny);
-                            }
-                        }
-                        bulk_load(buf + smrow(r), plane(pi) + ((size_t)zr * ny + ys) * nx * esz, rb, bar);
-                    }
-                }
+                if (KIND != WS_PHI && (KIND == WS_MU || gi >= 2 * Q))
+                    stage_field_group<Q, FMT, KIND, R>(L, buf, bar, gi, y0, z, nx, ny, nz, shear);
+                else
+                    stage_pop_group<Q, FMT, KIND, R, PULL>(L, buf, bar, gi, y0, z, nx, ny, nz, shear);
             }
             if constexpr (CST) {
 #pragma unroll
@@ -816,67 +918,9 @@ __global__ void __launch_bounds__(RPX * 256 + 32, KIND == WS_UPDATE ? 1 : 2) k_w
         const int y0 = (unit % nyu) * R, z = unit / nyu;
 
         if constexpr (KIND == WS_PHI) {
-            constexpr int RT = R / RP;  // rows of this thread's group
-            float2 out[RT];
-#pragma unroll
-            for (int q = 0; q < RT; ++q) {
-                const int r = rg + q * RP;
-                const unsigned wall = wall_s[s][r];
-                const size_t row = ((size_t)z * ny + y0 + r) * nx;
-                // rows without wall links (all but the first and last of the
-                // shear device) take every shift as a compile-time constant
-                auto pull_sum = [&](auto walls) {
-                    constexpr bool WL = decltype(walls)::value;
-                    float2 sum = p2(0.f);
-#pragma unroll
-                    for (int i = 0; i < Q; ++i) {
-                        const bool wl = WL && Lat<Q>::cy(i) != 0 && ((wall >> i) & 1u);
-                        const int cx = (PULL && !wl) ? Lat<Q>::cx(i) : 0;
-                        float2 gv;
-                        if (DEV && i == 0) gv = ld_shift(reinterpret_cast<const float *>(cur + FL::g_row(nx, 0, r)), x0, cx, nx);
-                        else gv = ld_shift(reinterpret_cast<const S *>(cur + FL::g_row(nx, i, r)), x0, cx, nx);
-                        if (wl) {
-                            const float uw = Lat<Q>::cy(i) > 0 ? -L.F.uwall : L.F.uwall;
-                            const float w2cu = float(2.0 * Lat<Q>::w(i) * 3.0) * float(Lat<Q>::cx(i)) * uw;
-                            gv = fma2(p2(w2cu), ld_pair(php + row, x0), gv);
-                        }
-                        sum = add2(sum, gv);
-                    }
-                    return sum;
-                };
-                out[q] = (PULL && wall != 0u) ? pull_sum(std::true_type{}) : pull_sum(std::false_type{});
-            }
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-#pragma unroll
-            for (int q = 0; q < RT; ++q)
-                st_pair(static_cast<float *>(L.phi) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
+            phi_unit<Q, FMT, R, RP, PULL>(L, cur, wall_s[s], nx, ny, x0, rg, y0, z, smem_addr(&empty[s]));
         } else if constexpr (KIND == WS_MU) {
-            constexpr int RT = R / RP;  // rows of this thread's group
-            float2 out[RT];
-#pragma unroll
-            for (int q = 0; q < RT; ++q) {
-                const int r = rg + q * RP;
-                const float *c0 = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(0, 0, r)));
-                const float2 p0 = ld_pair(c0, x0);
-                float2 lap = p2(0.f);
-#pragma unroll
-                for (int i = 1; i < Q; ++i) {
-                    const float *rw = reinterpret_cast<const float *>(
-                        cur + FL::fld_row(nx, 0, FL::fk(Lat<Q>::cy(i), Lat<Q>::cz(i), r)));
-                    // stencil reads x + c, i.e. a shift by -c
-                    lap = fma2(p2(float(Lat<Q>::w(i))), sub2(ld_shift(rw, x0, -Lat<Q>::cx(i), nx), p0), lap);
-                }
-                lap = mul2(p2(6.f), lap);
-                // A (phi^3 - phi) - kappa lap
-                out[q] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
-                              mul2(p2(L.F.kappa), lap));
-            }
-            __syncwarp();
-            if ((threadIdx.x & 31) == 0) mbar_arrive(smem_addr(&empty[s]));
-#pragma unroll
-            for (int q = 0; q < RT; ++q)
-                st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
+            mu_unit<Q, FMT, R, RP>(L, cur, nx, ny, x0, rg, y0, z, smem_addr(&empty[s]));
         } else {
             // ---------------------------------------------------- update
             const float *__restrict__ phif = static_cast<const float *>(L.phi);
