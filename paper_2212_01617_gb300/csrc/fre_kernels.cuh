@@ -81,10 +81,13 @@ struct Fmt<FRE_BF16DEV> {
     static constexpr bool DEV = true;
 };
 
+__device__ __forceinline__ float to_float(float v) { return v; }
 __device__ __forceinline__ float to_float(__half h) { return __half2float(h); }
 __device__ __forceinline__ float to_float(__nv_bfloat16 h) { return __bfloat162float(h); }
 template <typename S>
 __device__ __forceinline__ S from_float(float v);
+template <>
+__device__ __forceinline__ float from_float<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ __half from_float<__half>(float v) { return __float2half_rn(v); }
 template <>
@@ -675,31 +678,50 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
 // writer.  16-bit f holds deviations from w_i rho0 on this device, and
 // w_opp(i) = w_i, so a deviation carries over; 16-bit g keeps i >= 1 in
 // plane i - 1 (a link has c_i != 0).
+constexpr int kReflectPlanes = 4;
 template <int FMT>
 __global__ void __launch_bounds__(kBlock) k_reflect(Launch L) {
     static_assert(FMT != FRE_FP64, "the row kernels compute in FP32");
     using S = typename Fmt<FMT>::S;
     constexpr bool DEV = Fmt<FMT>::DEV;
     pdl_wait();
-    const int nl = L.G.n_rlinks;
+    // kReflectPlanes planes of one link per thread: the table entry is read
+    // once and the loads of all planes are in flight together (the pass is
+    // bound by the latency of its scattered reads)
+    constexpr int PZ = kReflectPlanes;
+    const int nl = L.G.n_rlinks, nz = L.G.nz;
+    const int nzc = (nz + PZ - 1) / PZ;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (long long)nl * L.G.nz) return;
-    const int z = (int)(t / nl);
-    const int4 e = __ldg(L.G.rlinks + (t - (long long)z * nl));
+    if (t >= (long long)nl * nzc) return;
+    const int zc = (int)(t / nl);
+    const int4 e = __ldg(L.G.rlinks + (t - (long long)zc * nl));
     const int i = e.z & 0xff, o = (e.z >> 8) & 0xff, cz = ((e.z >> 16) & 0xff) - 1;
     const float c = __int_as_float(e.w);
     const size_t plane = (size_t)L.G.nx * L.G.ny, np = (size_t)L.G.np;
-    const size_t n = (size_t)z * plane + (size_t)e.x;
-    const size_t src = (size_t)wrapi(z - cz, L.G.nz) * plane + (size_t)e.y;
     S *f = static_cast<S *>(L.dst.f);
     S *g = static_cast<S *>(L.dst.g);
-    const float ph = static_cast<const float *>(L.phi)[n];
-    if constexpr (DEV) {
-        f[(size_t)i * np + src] = from_float<S>(fmaf(c, L.F.rho0, to_float(f[(size_t)o * np + n])));
-        g[(size_t)(i - 1) * np + src] = from_float<S>(fmaf(c, ph, to_float(g[(size_t)(o - 1) * np + n])));
-    } else {
-        f[(size_t)i * np + src] = fmaf(c, L.F.rho0, f[(size_t)o * np + n]);
-        g[(size_t)i * np + src] = fmaf(c, ph, g[(size_t)o * np + n]);
+    const float *phi = static_cast<const float *>(L.phi);
+    // 16-bit g keeps population i >= 1 in plane i - 1
+    const size_t gi = DEV ? (size_t)(i - 1) : (size_t)i, go = DEV ? (size_t)(o - 1) : (size_t)o;
+    float ph[PZ], fo[PZ], gq[PZ];
+#pragma unroll
+    for (int q = 0; q < PZ; ++q) {
+        const int z = zc * PZ + q;
+        if (z < nz) {
+            const size_t n = (size_t)z * plane + (size_t)e.x;
+            ph[q] = phi[n];
+            fo[q] = to_float(f[(size_t)o * np + n]);
+            gq[q] = to_float(g[go * np + n]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < PZ; ++q) {
+        const int z = zc * PZ + q;
+        if (z < nz) {
+            const size_t src = (size_t)wrapi(z - cz, nz) * plane + (size_t)e.y;
+            f[(size_t)i * np + src] = from_float<S>(fmaf(c, L.F.rho0, fo[q]));
+            g[gi * np + src] = from_float<S>(fmaf(c, ph[q], gq[q]));
+        }
     }
 }
 
@@ -1236,7 +1258,7 @@ struct Launchers {
     }
     static void reflect(const Launch &L) {
         if constexpr (FMT != FRE_FP64) {
-            const long long nt = (long long)L.G.n_rlinks * L.G.nz;
+            const long long nt = (long long)L.G.n_rlinks * ((L.G.nz + kReflectPlanes - 1) / kReflectPlanes);
             if (nt > 0) launch_pdl(k_reflect<FMT>, dim3((unsigned)((nt + kBlock - 1) / kBlock)), dim3(kBlock), 0, L.stream, L);
         }
     }
