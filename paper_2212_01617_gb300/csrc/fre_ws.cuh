@@ -763,32 +763,78 @@ __device__ __forceinline__ void phi_unit(const Launch &L, const unsigned char *c
 
 // Consumers: mu = A (phi^3 - phi) - kappa lap(phi) of the rows of a unit from
 // the staged phi stencil rows; the warp releases the stage before it stores.
+// With one row group (RP = 1) a thread takes all R rows of its node pair and
+// reads every staged value it needs once (the pair at x0 and the values at
+// x0 - 1 and x0 + 2 of each staged row), then sums the stencil per weight
+// class: lap = 6 (w_1 S_1 + w_2 S_2 - (1 - w_0) phi), S_k the sum over the
+// neighbours with |c|^2 = k.
 template <int Q, int FMT, int R, int RP>
 __device__ __forceinline__ void mu_unit(const Launch &L, const unsigned char *cur, int nx, int ny, int x0, int rg,
                                         int y0, int z, unsigned empty_bar) {
     using FL = RowsLayout<Q, FMT, WS_MU, R>;
     constexpr int RT = R / RP;  // rows of this thread's group
     float2 out[RT];
+    if constexpr (RP == 1) {
+        constexpr int NP = Lat<Q>::D == 3 ? 3 : 1;  // planes cz = -1, 0, +1 (3D)
+        const int xl = x0 == 0 ? nx - 1 : x0 - 1, xr = x0 + 2 == nx ? 0 : x0 + 2;
+        float2 pv[NP][R + 2];
+        float lv[NP][R + 2], rv[NP][R + 2];
 #pragma unroll
-    for (int q = 0; q < RT; ++q) {
-        const int r = rg + q * RP;
-        const float *c0 = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(0, 0, r)));
-        const float2 p0 = ld_pair(c0, x0);
-        float2 lap = p2(0.f);
+        for (int pz = 0; pz < NP; ++pz) {
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const float *rw = reinterpret_cast<const float *>(
-                cur + FL::fld_row(nx, 0, FL::fk(Lat<Q>::cy(i), Lat<Q>::cz(i), r)));
-            // stencil reads x + c, i.e. a shift by -c
-            lap = fma2(p2(float(Lat<Q>::w(i))), sub2(ld_shift(rw, x0, -Lat<Q>::cx(i), nx), p0), lap);
+            for (int k = 0; k < R + 2; ++k) {
+                const float *rw = reinterpret_cast<const float *>(
+                    cur + FL::fld_row(nx, 0, FL::fk(k - 1, NP == 3 ? pz - 1 : 0, 0)));
+                pv[pz][k] = ld_pair(rw, x0);
+                lv[pz][k] = rw[xl];
+                rv[pz][k] = rw[xr];
+            }
         }
-        lap = mul2(p2(6.f), lap);
-        // A (phi^3 - phi) - kappa lap
-        out[q] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
-                      mul2(p2(L.F.kappa), lap));
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(empty_bar);
+        constexpr float w1 = float(Lat<Q>::D == 3 ? 1.0 / 18.0 : 1.0 / 9.0), w2 = float(1.0 / 36.0);
+        constexpr float wm = float(1.0 - Lat<Q>::w(0));
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            float2 s1 = p2(0.f), s2 = p2(0.f);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+                const int pz = NP == 3 ? cz + 1 : 0, k = r + 1 + cy;
+                // phi at x + c_i for the pair
+                const float2 v = cx == 0 ? pv[pz][k]
+                                         : (cx > 0 ? make_float2(pv[pz][k].y, rv[pz][k])
+                                                   : make_float2(lv[pz][k], pv[pz][k].x));
+                if (cx * cx + cy * cy + cz * cz == 1) s1 = add2(s1, v);
+                else s2 = add2(s2, v);
+            }
+            const float2 p0 = pv[NP == 3 ? 1 : 0][r + 1];
+            const float2 lap = mul2(p2(6.f), fma2(p2(w1), s1, fma2(p2(w2), s2, mul2(p2(-wm), p0))));
+            // A (phi^3 - phi) - kappa lap
+            out[r] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))), mul2(p2(L.F.kappa), lap));
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < RT; ++q) {
+            const int r = rg + q * RP;
+            const float *c0 = reinterpret_cast<const float *>(cur + FL::fld_row(nx, 0, FL::fk(0, 0, r)));
+            const float2 p0 = ld_pair(c0, x0);
+            float2 lap = p2(0.f);
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const float *rw = reinterpret_cast<const float *>(
+                    cur + FL::fld_row(nx, 0, FL::fk(Lat<Q>::cy(i), Lat<Q>::cz(i), r)));
+                // stencil reads x + c, i.e. a shift by -c
+                lap = fma2(p2(float(Lat<Q>::w(i))), sub2(ld_shift(rw, x0, -Lat<Q>::cx(i), nx), p0), lap);
+            }
+            lap = mul2(p2(6.f), lap);
+            // A (phi^3 - phi) - kappa lap
+            out[q] = sub2(mul2(p2(L.F.A), fma2(mul2(p0, p0), p0, mul2(p2(-1.f), p0))),
+                          mul2(p2(L.F.kappa), lap));
+        }
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) mbar_arrive(empty_bar);
     }
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(empty_bar);
 #pragma unroll
     for (int q = 0; q < RT; ++q)
         st_pair(static_cast<float *>(L.mu) + ((size_t)z * ny + y0 + rg + q * RP) * nx + x0, out[q]);
