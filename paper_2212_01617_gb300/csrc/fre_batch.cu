@@ -43,7 +43,7 @@ struct fre_batch {
     int tuned_nslots = 0;  // slot count the tuning was measured on
     double tuned_ms[5] = {0, 0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128, per-slot, concurrent
     // streams and events of the concurrent mode (graph branches)
-    static constexpr int kBranches = 4;
+    static constexpr int kBranches = 8;
     cudaStream_t aux[kBranches] = {};
     cudaEvent_t fork = nullptr, join[kBranches] = {};
     cudaGraphExec_t graph = nullptr;
@@ -261,15 +261,24 @@ fre_status capture(fre_batch *b) {
         for (int s : b->order) fre::ctx_launch_step(b->slots[s]);
         for (int s : b->order) b->slots[s]->step -= 2;  // captured, not run
     } else {
-        // slot k's two steps on branch k mod kBranches: the slots' kernels
-        // may then run side by side
+        // each slot's two steps on one branch, so that the slots' kernels
+        // may run side by side; the largest slots first, each onto the
+        // branch with the fewest nodes so far, so that the branches end
+        // together
         cudaEventRecord(b->fork, b->stream);
         for (int j = 0; j < fre_batch::kBranches; ++j) cudaStreamWaitEvent(b->aux[j], b->fork, 0);
-        int k = 0;
-        for (int s : b->order) {
+        auto nodes = [&](int s) { return (long long)b->slots[s]->G.nx * b->slots[s]->G.ny * b->slots[s]->G.nz; };
+        std::vector<int> by_size(b->order);
+        std::stable_sort(by_size.begin(), by_size.end(), [&](int x, int y) { return nodes(x) > nodes(y); });
+        long long load[fre_batch::kBranches] = {};
+        for (int s : by_size) {
             fre_ctx *c = b->slots[s];
             const cudaStream_t own = c->stream;
-            c->stream = b->aux[k++ % fre_batch::kBranches];
+            int j = 0;
+            for (int q = 1; q < fre_batch::kBranches; ++q)
+                if (load[q] < load[j]) j = q;
+            load[j] += nodes(s);
+            c->stream = b->aux[j];
             fre::ctx_launch_step(c);
             fre::ctx_launch_step(c);
             c->stream = own;
