@@ -43,7 +43,7 @@ struct fre_batch {
     int tuned_nslots = 0;  // slot count the tuning was measured on
     double tuned_ms[5] = {0, 0, 0, 0, 0};  // ms/step of batched bx 32, 64, 128, per-slot, concurrent
     // streams and events of the concurrent mode (graph branches)
-    static constexpr int kBranches = 8;
+    static constexpr int kBranches = 16;
     cudaStream_t aux[kBranches] = {};
     cudaEvent_t fork = nullptr, join[kBranches] = {};
     cudaGraphExec_t graph = nullptr;
