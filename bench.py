@@ -363,6 +363,74 @@ def serving_size_rates(steps=50):
     return out
 
 
+def next_rows_summary(steps=100):
+    """Device-timed figures of the rows built after the hot path: the full
+    functional (model 1) and the interpolated roller walls (per-node
+    kernels: step rate and update-kernel fraction of HBM at the same
+    304 B/node of f and g), the consistent initialisation (time per
+    iteration) and the breakup detection (connected components of phi > 0,
+    time per call on the benchmark lattice)."""
+    import time
+    import torch
+    import paper_2212_01617_gb300 as fre
+    peak = measured_peak_gbs()[0]
+    out = {}
+
+    def step_rate(tag, **kw):
+        nx, ny, nz = kw["nx"], kw["ny"], kw["nz"]
+        sim = fre.Simulation(lattice="d3q19", precision="fp32", **kw)
+        sim.init_droplet((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, ny / 5)
+        sim.step(10)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            _, _, upd, tot, _ = sim.step_timed(steps)
+            if best is None or tot < best[0]:
+                best = (tot, upd)
+        n = nx * ny * nz
+        out[tag] = {"gnodes_per_s": n * steps / (best[0] * 1e-3) / 1e9, "ms_per_step": best[0] / steps,
+                    "update_frac_of_measured_hbm": ALG_BYTES["fp32"] * n * steps / (best[1] * 1e-3) / 1e9 / peak,
+                    "kernel_path": sim.kernel_path, "shape": [nx, ny, nz]}
+        return sim
+
+    phys = dict(tau_f=2.0, tau_g=2.0, A=0.04, kappa=0.04, gamma_mob=0.5, rho0=1.0)
+    step_rate("full_functional_shear_fp32", device="shear", nx=128, ny=64, nz=64, u_wall=0.03,
+              model=1, kappa1=0.03, kappa2=0.09, alpha=0.8, **phys).close()
+    step_rate("interpolated_walls_four_roller_fp32", device="four_roller", nx=192, ny=96, nz=96, u_wall=0.02,
+              flags=fre.FRE_FLAG_INTERPOLATED_WALLS, **phys).close()
+    # consistent initialisation, 128x64x64 FP32
+    sim = fre.Simulation(lattice="d3q19", precision="fp32", device="shear", nx=128, ny=64, nz=64, u_wall=0.03,
+                         **phys)
+    sim.init_droplet(63.5, 31.5, 31.5, 12.8)
+    sim.init_consistent(5)
+    torch.cuda.synchronize()
+    iters = 50
+    t0 = time.perf_counter()
+    sim.init_consistent(iters)
+    torch.cuda.synchronize()
+    out["consistent_init_shear_fp32"] = {"ms_per_iteration": (time.perf_counter() - t0) * 1e3 / iters,
+                                         "iterations": iters, "shape": [128, 64, 64]}
+    sim.close()
+    # breakup detection on the benchmark lattice
+    w = WORKLOAD
+    sim = fre.Simulation(precision="fp32", **w)
+    sim.init_droplet(*DROPLET)
+    sim.step(2)
+    sim.components()
+    torch.cuda.synchronize()
+    reps = 5
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        count, _, _ = sim.components()
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    n = w["nx"] * w["ny"] * w["nz"]
+    out["components_bench_lattice"] = {"ms_per_call": ms, "gnodes_per_s": n / (ms * 1e-3) / 1e9,
+                                       "components": count, "shape": [w["nx"], w["ny"], w["nz"]],
+                                       "what": "host-timed call (labels on the device, counts read back)"}
+    sim.close()
+    return out
+
+
 def base_config(precision):
     return {"workload": "D3Q19 two-lattice FRE-LBM, parallel-band shear 512x256x256 (33.5M nodes), "
                         "droplet R=48, A=kappa=0.04, tau=2, Gamma=0.5, u_w=0.03",
@@ -738,13 +806,14 @@ def main():
         cpu = cpu_baseline(args.cpu_seconds)
 
     # batch and serving summaries (one GPU, rank 0 of a single-rank run)
-    batch, serve = None, None
+    batch, serve, next_rows = None, None, None
     if rank == 0 and ws == 1 and not args.no_batch_serve:
         bl = batch_summary(200, 40)
         batch = {k: bl[k] for k in ("value", "unit", "ms_per_step", "sequential", "speedup_vs_sequential",
                                     "roofline", "tuning", "config")}
         serve = serve_summary(args.summary_requests, args.summary_max_steps, args.serve_target_nodes)
         serve["step_rates_by_size"] = serving_size_rates()
+        next_rows = next_rows_summary()
 
     if rank == 0:
         variants = {}
@@ -791,6 +860,8 @@ def main():
             line["batch"] = batch
         if serve is not None:
             line["serve"] = serve
+        if next_rows is not None:
+            line["next_rows"] = next_rows
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

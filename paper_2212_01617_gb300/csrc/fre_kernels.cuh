@@ -375,23 +375,29 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
                 // the same at every point of the link (the rotation's
                 // c_i x (p - c_k) does not change along c_i).  The weights
                 // of each rule sum to 1, so 16-bit deviations combine alike.
+                // The crossing in the arithmetic of the format (FP32 for
+                // FP32 and 16-bit storage: GB300's FP64 pipe is narrow and
+                // this branch diverges within warps)
                 const int k = L.G.solid[site_src<Q>(s, i)];
-                const double ex = Lat<Q>::cx(i), ey = Lat<Q>::cy(i);
-                const double dx = s.x - L.G.rcx[k], dy = s.y - L.G.rcy[k];
-                const double cc = ex * ex + ey * ey, dc = dx * ex + dy * ey;
-                const double dd = dx * dx + dy * dy - L.G.rr * L.G.rr;
-                const double disc = dc * dc - cc * dd;
-                double qd = (dc - sqrt(disc > 0.0 ? disc : 0.0)) / cc;  // first crossing
-                qd = qd <= 0.0 ? 1e-12 : (qd > 1.0 ? 1.0 : qd);
-                const T q2 = T(2.0 * qd);
+                const T ex = T(Lat<Q>::cx(i)), ey = T(Lat<Q>::cy(i));
+                const T dx = T(s.x) - T(L.G.rcx[k]), dy = T(s.y) - T(L.G.rcy[k]);
+                const T cc = ex * ex + ey * ey, dc = dx * ex + dy * ey;
+                const T dd = dx * dx + dy * dy - T(L.G.rr) * T(L.G.rr);
+                const T disc = dc * dc - cc * dd;
+                // first crossing (dc - sqrt(disc)) / cc, written as
+                // dd / (dc + sqrt(disc)): the roots' product dd/cc and sum
+                // 2 dc/cc are positive, so no cancellation for small q
+                T qd = dd / (dc + sqrt(disc > T(0) ? disc : T(0)));
+                qd = qd <= T(0) ? T(1e-12) : (qd > T(1) ? T(1) : qd);
+                const T q2 = T(2) * qd;
                 const T lf = wi2 * rho0 * cu, lg = wi2 * php * cu;
                 const int nb = site_nb<Q>(s, i);
                 T Wv, gv;
-                if (qd < 0.5 && !L.G.solid[nb]) {
+                if (qd < T(0.5) && !L.G.solid[nb]) {
                     const T Unb = DEV ? T(couette_u(L, s.y + Lat<Q>::cy(i))) : T(0);
                     Wv = q2 * ldW(o, n, U) + (T(1) - q2) * ldW(o, nb, Unb) + lf;
                     gv = q2 * P::ldg(L.src, np, o, n) + (T(1) - q2) * P::ldg(L.src, np, o, nb) + lg;
-                } else if (qd >= 0.5) {
+                } else if (qd >= T(0.5)) {
                     Wv = (ldW(o, n, U) + (q2 - T(1)) * ldW(i, n, U) + lf) / q2;
                     gv = (P::ldg(L.src, np, o, n) + (q2 - T(1)) * P::ldg(L.src, np, i, n) + lg) / q2;
                 } else {
