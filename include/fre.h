@@ -149,7 +149,10 @@ typedef struct {
  * with the moving-wall term m_i = 2 w_i rho0 (c_i . u_w) / cs^2 of the
  * roller's rotation (g alike, with phi(x, t) in place of rho0).  The wall
  * then sits on the circle to second order instead of on the staircase.
- * Runs on the per-node kernels; batches and servers do not take it. */
+ * FP64 runs it on the per-node kernels; FP32 and 16-bit storage on the row
+ * kernels, where a pass after each update writes every link's value into
+ * its roller source (link fractions computed once, in double, at create).
+ * Batches and servers do not take it. */
 #define FRE_FLAG_INTERPOLATED_WALLS 32u
 /* Bits 8..15: log2 of the x-chunk width of the row kernels (0 = automatic:
  * 128 when nx allows it, else the whole row).  A tuning knob; every valid

@@ -90,9 +90,16 @@ int wrap_host(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 // 2 w_i (c_i . u_w) / cs^2 with u_w = omega_k z x (p - c_k) at the link's
 // wall point p = x - c_i / 2; the shift along c_i drops out of c_i x (p - c_k),
 // so c_i . u_w = omega_k (c_iy (x - x_k) - c_ix (y - y_k)).  Returns the
-// number of links; fills `out` when it is not NULL.
-long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::vector<int4> *out) {
+// number of links; fills `out` when it is not NULL, and `outq` (the
+// interpolated walls' entries of Geo::rlinkq) when it is not NULL.  The
+// link from x toward x - c_i meets the circle of radius r about c_k at
+// x - q c_i with q the smaller root of |d - q c|^2 = r^2 (d = x - c_k, the
+// in-plane part of c_i): q = dd / (dc + sqrt(dc^2 - cc dd)), dc = d.c,
+// cc = c.c, dd = d.d - r^2 (both roots positive, no cancellation).
+long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::vector<int4> *out,
+                       std::vector<int4> *outq = nullptr) {
     if (out) out->clear();
+    if (outq) outq->clear();
     long long count = 0;
     for (int i = 1; i < q; ++i)
         for (int y = 0; y < p.ny; ++y)
@@ -119,6 +126,27 @@ long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::ve
                 e.z = i | (o << 8) | ((ci[2] + 1) << 16);
                 std::memcpy(&e.w, &coef, sizeof(float));
                 out->push_back(e);
+                if (outq) {
+                    // from the node's periodic image beside the roller (the
+                    // wrapped source plus c_i); the moving-wall coefficient
+                    // from the same image
+                    const double r = p.nx / 8.0;
+                    const double dx = xs + ci[0] - g.rcx[k], dy = ys + ci[1] - g.rcy[k];
+                    const float coefi = float(6.0 * w * g.om[k] * (ci[1] * dx - ci[0] * dy));
+                    std::memcpy(&out->back().w, &coefi, sizeof(float));
+                    const double cc = ci[0] * ci[0] + ci[1] * ci[1], dc = dx * ci[0] + dy * ci[1];
+                    const double dd = dx * dx + dy * dy - r * r, disc = dc * dc - cc * dd;
+                    double t = dd / (dc + std::sqrt(disc > 0.0 ? disc : 0.0));
+                    t = t <= 0.0 ? 1e-12 : (t > 1.0 ? 1.0 : t);
+                    const float qf = float(t);
+                    const int xn = wrap_host(x + ci[0], p.nx), yn = wrap_host(y + ci[1], p.ny);
+                    int4 a;
+                    std::memcpy(&a.x, &qf, sizeof(float));
+                    a.y = yn * p.nx + xn;
+                    a.z = g.id[(size_t)yn * p.nx + xn] ? 1 : 0;
+                    a.w = 0;
+                    outq->push_back(a);
+                }
             }
     return count;
 }
@@ -177,7 +205,8 @@ bool sizes_of(const fre_params *p, Sizes &s, std::string *why) {
     if (p->device == FRE_FOUR_ROLLER) {
         RollerPlane g;
         roller_plane(*p, g);
-        s.solid_bytes = (size_t)s.np + sizeof(int4) * (size_t)roller_links(*p, s.q, g, nullptr);
+        const size_t nl = (size_t)roller_links(*p, s.q, g, nullptr);
+        s.solid_bytes = (size_t)s.np + sizeof(int4) * nl * ((p->flags & FRE_FLAG_INTERPOLATED_WALLS) ? 2 : 1);
     }
     s.model = p->model;
     return true;
@@ -213,7 +242,7 @@ fre_status dev_alloc(fre_ctx *c, void **ptr, size_t bytes) {
 // Four-roller geometry of a context: roller id of every node, the solid
 // nodes that have a fluid stencil neighbour, and the wall links of a plane.
 void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<int> &ghost,
-                   std::vector<int4> &links) {
+                   std::vector<int4> &links, std::vector<int4> &linkq) {
     const fre_params &p = c->p;
     fre::Geo &G = c->G;
     RollerPlane g;
@@ -232,7 +261,7 @@ void build_rollers(fre_ctx *c, std::vector<unsigned char> &solid, std::vector<in
     const auto &c9 = kC9;
     const auto &c19 = kC19;
     auto wrap = wrap_host;
-    roller_links(p, q, g, &links);
+    roller_links(p, q, g, &links, G.interp ? &linkq : nullptr);
     ghost.clear();
     for (int z = 0; z < p.nz; ++z)
         for (int y = 0; y < p.ny; ++y)
@@ -288,7 +317,10 @@ fre::Launch fre::ctx_launch(fre_ctx *c) {
     L.W = c->row_w;
     L.err = c->err_dev;
     L.stall = (c->p.flags & FRE_FLAG_TEST_PIPELINE_STALL) ? 1 : 0;
-    L.reflect = (c->fullrow && c->G.device == FRE_FOUR_ROLLER) ? 1 : 0;
+    // the per-node update reflects half-way wall links itself where the row
+    // kernels run the context; interpolated links are left to the
+    // reflection pass, which follows every update then
+    L.reflect = (c->fullrow && c->G.device == FRE_FOUR_ROLLER && !c->G.interp) ? 1 : 0;
     L.wait_ns = L.stall ? 5000000ull : 2000000000ull;
     return L;
 }
@@ -319,6 +351,9 @@ void fre::ctx_launch_step(fre_ctx *c) {
         c->ks->mu(L);
         if (c->n_ghost) fre::ghost_fields(c, L, true);
         c->ks->update(L, pull);
+        // the in-place step of interpolated walls on the row kernels: the
+        // next (pulled, row) step reads its wall links from the roller slots
+        if (c->fullrow && roll && c->G.interp) c->ks->reflect(L);
     }
     c->cur ^= 1;
     c->pp ^= 1;
@@ -527,8 +562,8 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
     if (p->device == FRE_FOUR_ROLLER) {
         std::vector<unsigned char> solid;
         std::vector<int> ghost;
-        std::vector<int4> links;
-        build_rollers(c, solid, ghost, links);
+        std::vector<int4> links, linkq;
+        build_rollers(c, solid, ghost, links, linkq);
         void *d;
         fre_status st = dev_alloc(c, &d, s.solid_bytes);
         if (st != FRE_OK) return bail(st);
@@ -554,15 +589,25 @@ fre_status fre_create(const fre_params *p, void *cuda_stream, fre_ctx **out) {
                                 c->stream) != cudaSuccess)
                 return bail(fail(FRE_ERR_CUDA, "upload of the roller links failed"));
         }
+        if (!linkq.empty()) {
+            st = dev_alloc(c, &d, sizeof(int4) * linkq.size());
+            if (st != FRE_OK) return bail(st);
+            c->rlinkq = static_cast<int4 *>(d);
+            if (cudaMemcpyAsync(c->rlinkq, linkq.data(), sizeof(int4) * linkq.size(), cudaMemcpyHostToDevice,
+                                c->stream) != cudaSuccess)
+                return bail(fail(FRE_ERR_CUDA, "upload of the roller link fractions failed"));
+        }
         if (cudaStreamSynchronize(c->stream) != cudaSuccess)
             return bail(fail(FRE_ERR_CUDA, "geometry upload: %s", cudaGetErrorString(cudaGetLastError())));
     }
     c->G.solid = c->solid;
     c->G.rlinks = c->rlinks;
     c->G.n_rlinks = c->n_rlinks;
-    // the full functional (model 1) and the interpolated roller walls run
-    // on the per-node kernels
-    const bool per_node = (p->flags & (FRE_FLAG_GENERIC_KERNELS | FRE_FLAG_INTERPOLATED_WALLS)) || p->model != 0;
+    c->G.rlinkq = c->rlinkq;
+    // the full functional (model 1) runs on the per-node kernels; the
+    // interpolated roller walls take the row kernels with the interpolating
+    // reflection pass (FP32 and 16-bit storage)
+    const bool per_node = (p->flags & FRE_FLAG_GENERIC_KERNELS) || p->model != 0;
     if (!per_node && c->ks->row_width) {
         const unsigned sh = (p->flags >> FRE_FLAG_CHUNK_SHIFT) & 0xffu;
         c->row_w = c->ks->row_width(c->G, sh ? (1 << sh) : 0);
@@ -740,7 +785,7 @@ fre_status fre_step_timed(fre_ctx *c, int nsteps, double *ms, long long *launche
         else if (c->rows) c->ks->update_rows(L, pull);
         else c->ks->update(L, pull);
         ++nl;
-        if (full && c->G.device == FRE_FOUR_ROLLER) {
+        if ((full || (c->fullrow && c->G.interp)) && c->G.device == FRE_FOUR_ROLLER) {
             c->ks->reflect(L);
             ++nl;
         }

@@ -21,6 +21,7 @@ struct fre_ctx {
     void *rhof = nullptr, *murho = nullptr;  // model 1: rho and mu_rho fields
     unsigned char *solid = nullptr;
     int4 *rlinks = nullptr;     // four-roller: the wall links of a plane (Geo::rlinks)
+    int4 *rlinkq = nullptr;     // interpolated walls: their fractions (Geo::rlinkq)
     int n_rlinks = 0;
     int *ghost = nullptr;
     int n_ghost = 0;

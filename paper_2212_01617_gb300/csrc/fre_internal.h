@@ -24,6 +24,12 @@ struct Geo {
     // float bits of 2 w_i (c_i . u_w) / cs^2}
     const int4 *rlinks;
     int n_rlinks;
+    // interpolated roller walls on the row kernels: per entry of rlinks,
+    // {float bits of the fraction q of the link from the fluid node toward
+    // its roller source that lies outside the roller circle, the fluid
+    // node's neighbour x + c_i in the plane (y nx + x, wrapped), 1 if that
+    // neighbour is a roller node, 0}; nullptr otherwise
+    const int4 *rlinkq;
     double rcx[5], rcy[5], om[5];  // roller centres and angular velocities (1..4)
     double rr;                // roller radius
     int interp;               // four-roller: interpolated bounce-back at the roller surfaces

@@ -375,29 +375,35 @@ __device__ __forceinline__ void gather(const Launch &L, const Site &s, typename 
                 // the same at every point of the link (the rotation's
                 // c_i x (p - c_k) does not change along c_i).  The weights
                 // of each rule sum to 1, so 16-bit deviations combine alike.
-                // The crossing in the arithmetic of the format (FP32 for
-                // FP32 and 16-bit storage: GB300's FP64 pipe is narrow and
-                // this branch diverges within warps)
+                // The crossing and the wall velocity, in FP64 and rounded
+                // once to the format (the row kernels take both from a
+                // table made at create; this per-node path serves small or
+                // odd-sized lattices and first steps), measured from the
+                // node's periodic image beside the roller (the wrapped
+                // source plus c_i)
                 const int k = L.G.solid[site_src<Q>(s, i)];
-                const T ex = T(Lat<Q>::cx(i)), ey = T(Lat<Q>::cy(i));
-                const T dx = T(s.x) - T(L.G.rcx[k]), dy = T(s.y) - T(L.G.rcy[k]);
-                const T cc = ex * ex + ey * ey, dc = dx * ex + dy * ey;
-                const T dd = dx * dx + dy * dy - T(L.G.rr) * T(L.G.rr);
-                const T disc = dc * dc - cc * dd;
+                const int cxi = Lat<Q>::cx(i), cyi = Lat<Q>::cy(i);
+                const int xi = wrapi(s.x - cxi, L.G.nx) + cxi, yi = wrapi(s.y - cyi, L.G.ny) + cyi;
+                const double ex = cxi, ey = cyi;
+                const double dx = xi - L.G.rcx[k], dy = yi - L.G.rcy[k];
+                const double cc = ex * ex + ey * ey, dc = dx * ex + dy * ey;
+                const double dd = dx * dx + dy * dy - L.G.rr * L.G.rr;
+                const double disc = dc * dc - cc * dd;
                 // first crossing (dc - sqrt(disc)) / cc, written as
                 // dd / (dc + sqrt(disc)): the roots' product dd/cc and sum
                 // 2 dc/cc are positive, so no cancellation for small q
-                T qd = dd / (dc + sqrt(disc > T(0) ? disc : T(0)));
-                qd = qd <= T(0) ? T(1e-12) : (qd > T(1) ? T(1) : qd);
-                const T q2 = T(2) * qd;
-                const T lf = wi2 * rho0 * cu, lg = wi2 * php * cu;
+                double qd = dd / (dc + sqrt(disc > 0.0 ? disc : 0.0));
+                qd = qd <= 0.0 ? 1e-12 : (qd > 1.0 ? 1.0 : qd);
+                const T q2 = T(2.0 * qd);
+                const T cuk = T(L.G.om[k] * (ey * dx - ex * dy));  // c_i . u_w on the link
+                const T lf = wi2 * rho0 * cuk, lg = wi2 * php * cuk;
                 const int nb = site_nb<Q>(s, i);
                 T Wv, gv;
-                if (qd < T(0.5) && !L.G.solid[nb]) {
+                if (qd < 0.5 && !L.G.solid[nb]) {
                     const T Unb = DEV ? T(couette_u(L, s.y + Lat<Q>::cy(i))) : T(0);
                     Wv = q2 * ldW(o, n, U) + (T(1) - q2) * ldW(o, nb, Unb) + lf;
                     gv = q2 * P::ldg(L.src, np, o, n) + (T(1) - q2) * P::ldg(L.src, np, o, nb) + lg;
-                } else if (qd >= T(0.5)) {
+                } else if (qd >= 0.5) {
                     Wv = (ldW(o, n, U) + (q2 - T(1)) * ldW(i, n, U) + lf) / q2;
                     gv = (P::ldg(L.src, np, o, n) + (q2 - T(1)) * P::ldg(L.src, np, i, n) + lg) / q2;
                 } else {
@@ -728,6 +734,70 @@ __global__ void __launch_bounds__(kBlock) k_reflect(Launch L) {
             f[(size_t)i * np + src] = from_float<S>(fmaf(c, L.F.rho0, fo[q]));
             g[gi * np + src] = from_float<S>(fmaf(c, ph[q], gq[q]));
         }
+    }
+}
+
+// Interpolated roller walls on the row kernels: the linear rule of
+// Bouzidi, Firdaouss and Lallemand that gather applies per node, evaluated
+// once per wall link after the update from the post-collision values of
+// fluid nodes, and written into slot i of the link's roller source, which
+// the next step pulls like any other.  With the link's fraction q and
+// moving-wall coefficient c (the tables Geo::rlinkq and Geo::rlinks):
+//   q < 1/2, x + c_i fluid:       2q f*_ibar(x) + (1 - 2q) f*_ibar(x + c_i) + c rho0
+//   q < 1/2, x + c_i a roller node: f*_ibar(x) + c rho0
+//   q >= 1/2:                     [f*_ibar(x) + (2q - 1) f*_i(x) + c rho0] / (2q)
+// and g alike with c phi(x, t).  The weights of each rule sum to 1, so
+// 16-bit f combines as deviations from w_i rho0 (w_ibar = w_i).  Reads
+// touch fluid nodes only, each roller slot has a single writer.
+template <int FMT>
+__global__ void __launch_bounds__(kBlock) k_reflect_interp(Launch L) {
+    static_assert(FMT != FRE_FP64, "the row kernels compute in FP32");
+    using S = typename Fmt<FMT>::S;
+    constexpr bool DEV = Fmt<FMT>::DEV;
+    pdl_wait();
+    constexpr int PZ = kReflectPlanes;
+    const int nl = L.G.n_rlinks, nz = L.G.nz;
+    const int nzc = (nz + PZ - 1) / PZ;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)nl * nzc) return;
+    const int zc = (int)(t / nl);
+    const int l = (int)(t - (long long)zc * nl);
+    const int4 e = __ldg(L.G.rlinks + l);
+    const int4 a = __ldg(L.G.rlinkq + l);
+    const int i = e.z & 0xff, o = (e.z >> 8) & 0xff, cz = ((e.z >> 16) & 0xff) - 1;
+    const float c = __int_as_float(e.w);
+    const float q2 = 2.f * __int_as_float(a.x);
+    const bool near = q2 < 1.f, nb_solid = a.z != 0;
+    const size_t plane = (size_t)L.G.nx * L.G.ny, np = (size_t)L.G.np;
+    S *f = static_cast<S *>(L.dst.f);
+    S *g = static_cast<S *>(L.dst.g);
+    const float *phi = static_cast<const float *>(L.phi);
+    const size_t gi = DEV ? (size_t)(i - 1) : (size_t)i, go = DEV ? (size_t)(o - 1) : (size_t)o;
+    const float rho0 = L.F.rho0;
+#pragma unroll
+    for (int q = 0; q < PZ; ++q) {
+        const int z = zc * PZ + q;
+        if (z >= nz) break;
+        const size_t n = (size_t)z * plane + (size_t)e.x;
+        const float ph = phi[n];
+        const float fo = to_float(f[(size_t)o * np + n]), gov = to_float(g[go * np + n]);
+        float fv, gv;
+        if (near) {
+            if (nb_solid) {
+                fv = fo + c * rho0;
+                gv = gov + c * ph;
+            } else {
+                const size_t nb = (size_t)wrapi(z + cz, nz) * plane + (size_t)a.y;
+                fv = q2 * fo + (1.f - q2) * to_float(f[(size_t)o * np + nb]) + c * rho0;
+                gv = q2 * gov + (1.f - q2) * to_float(g[go * np + nb]) + c * ph;
+            }
+        } else {
+            fv = (fo + (q2 - 1.f) * to_float(f[(size_t)i * np + n]) + c * rho0) / q2;
+            gv = (gov + (q2 - 1.f) * to_float(g[gi * np + n]) + c * ph) / q2;
+        }
+        const size_t src = (size_t)wrapi(z - cz, nz) * plane + (size_t)e.y;
+        f[(size_t)i * np + src] = from_float<S>(fv);
+        g[gi * np + src] = from_float<S>(gv);
     }
 }
 
@@ -1265,7 +1335,9 @@ struct Launchers {
     static void reflect(const Launch &L) {
         if constexpr (FMT != FRE_FP64) {
             const long long nt = (long long)L.G.n_rlinks * ((L.G.nz + kReflectPlanes - 1) / kReflectPlanes);
-            if (nt > 0) launch_pdl(k_reflect<FMT>, dim3((unsigned)((nt + kBlock - 1) / kBlock)), dim3(kBlock), 0, L.stream, L);
+            if (nt > 0)
+                launch_pdl(L.G.rlinkq ? k_reflect_interp<FMT> : k_reflect<FMT>,
+                           dim3((unsigned)((nt + kBlock - 1) / kBlock)), dim3(kBlock), 0, L.stream, L);
         }
     }
     static void mei_prep(const Launch &L) { k_mei_prep<Q, FMT><<<grid3(L.G), kBlock, 0, L.stream>>>(L); }

@@ -180,21 +180,25 @@ ROLL_CASES = [
 
 @pytest.mark.parametrize("case", ROLL_CASES, ids=lambda c: f"{c[0]}-{c[1]}x{c[2]}x{c[3]}")
 @pytest.mark.parametrize("precision", ["fp32", "fp16dev", "bf16dev"])
-def test_four_roller_row_kernels(fre, orc, case, precision):
-    """The four-roller device on the row kernels (the wall links of every
-    node staged with its rows, the local opposite population and the
-    rollers' moving-wall term on each link, roller nodes stored as 0, ghost
-    fills between the passes) against the per-node kernels and the FP64
-    oracle after 200 steps, with the bounds of the shear rows above."""
+@pytest.mark.parametrize("interp", [False, True], ids=["halfway", "interpolated"])
+def test_four_roller_row_kernels(fre, orc, case, precision, interp):
+    """The four-roller device on the row kernels (roller nodes stored as 0,
+    the wall links of each step written into the roller nodes' slots by the
+    reflection pass, with half-way bounce-back or, with
+    FRE_FLAG_INTERPOLATED_WALLS, the interpolated rule from the link
+    fractions; ghost fills between the passes) against the per-node kernels
+    and the FP64 oracle after 200 steps, with the bounds of the shear rows
+    above."""
     lattice, nx, ny, nz = case
     kw = dict(u_wall=0.01, tau_f=1.2, tau_g=1.0, gamma_mob=0.8)
-    rows = make(fre, lattice, "four_roller", nx, ny, nz, precision, **kw)
-    gen = make(fre, lattice, "four_roller", nx, ny, nz, precision, flags=1, **kw)
+    iw = fre.FRE_FLAG_INTERPOLATED_WALLS if interp else 0
+    rows = make(fre, lattice, "four_roller", nx, ny, nz, precision, flags=iw, **kw)
+    gen = make(fre, lattice, "four_roller", nx, ny, nz, precision, flags=1 | iw, **kw)
     assert rows.kernel_path == 2 and gen.kernel_path == 0
     a = dict(tau_f=1.0, tau_g=1.0, A=0.04, kappa=0.04, gamma_mob=1.0, u_wall=0.0, rho0=1.0)
     a.update(kw)
     o = orc.Oracle({"d2q9": 0, "d3q19": 1}[lattice], 1, nx, ny, nz, a["tau_f"], a["tau_g"], a["A"], a["kappa"],
-                   a["gamma_mob"], a["u_wall"], a["rho0"])
+                   a["gamma_mob"], a["u_wall"], a["rho0"], interp=int(interp))
     c = ((nx - 1) / 2, (ny - 1) / 2, (nz - 1) / 2, nx / 10)
     for s in (rows, gen, o):
         s.init_droplet(*c)
