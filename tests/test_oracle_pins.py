@@ -667,7 +667,9 @@ def _link_fraction_bisection(p_fluid, c, centre, r):
 
 
 @pytest.mark.parametrize("interp", [0, 1])
-@pytest.mark.parametrize("lattice,shape", [(0, (1, 16, 16)), (1, (3, 16, 16))])
+@pytest.mark.parametrize("lattice,shape", [(0, (1, 16, 16)), (1, (3, 16, 16)),
+                                           # ny = nx/2: the rollers reach across the periodic y boundary
+                                           (0, (1, 16, 32)), (1, (3, 16, 32))])
 def test_brute_force_one_step_four_roller(orc, lattice, shape, interp):
     """One step of the four-roller device on a small lattice from random
     populations, recomputed from the geometry alone: the staircase mask,
