@@ -42,8 +42,11 @@
  *     cylinders of radius nx/8 centred at ((nx-1)/2 +- nx/4, (ny-1)/2 +- ny/4),
  *     surface speed u_wall, top-right and bottom-left counter-clockwise, the
  *     other two clockwise, periodic outer box), fully periodic box.
- * The four-roller wall point of a link (x - c_i/2) and the weighted-mean
- * stencil rule at roller solids are readings that no closed form fixes;
+ * The four-roller wall point of a link (x - c_i/2, taken in the frame of the
+ * roller the link meets: a roller of a box with ny = nx/2 reaches across the
+ * periodic y boundary, where the node's image beside it counts) and the
+ * weighted-mean stencil rule at roller solids are readings that no closed
+ * form fixes;
  * the tests recompute one step of them from the geometry alone (indices,
  * signs, points).  For a rigid rotation c_i . u_w does not depend on where
  * along the link the wall point sits (c_i . (z x c_i) = 0).
@@ -268,8 +271,11 @@ static int stream_source(const orc_state *s, int x, int y, int z, int i,
     *src = node(s, wrap(xs, s->p.nx), wrap(ys, s->p.ny), wrap(zs, s->p.nz));
     int k = s->solid[*src];
     if (k == 0) return 1;
-    /* rigid rotation of roller k about its axis (parallel to z) */
-    double xw = x - 0.5 * s->c[i][0], yw = y - 0.5 * s->c[i][1];
+    /* rigid rotation of roller k about its axis (parallel to z), at the
+     * link's wall point in the frame of the roller: the wrapped source plus
+     * c_i / 2 (a roller of a box with ny = nx/2 reaches across the
+     * periodic y boundary) */
+    double xw = wrap(xs, s->p.nx) + 0.5 * s->c[i][0], yw = wrap(ys, s->p.ny) + 0.5 * s->c[i][1];
     uw[0] = -s->omega[k] * (yw - s->rc[k][1]);
     uw[1] = s->omega[k] * (xw - s->rc[k][0]);
     return 0;

@@ -89,7 +89,9 @@ int wrap_host(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 // along x).  The moving-wall coefficient is
 // 2 w_i (c_i . u_w) / cs^2 with u_w = omega_k z x (p - c_k) at the link's
 // wall point p = x - c_i / 2; the shift along c_i drops out of c_i x (p - c_k),
-// so c_i . u_w = omega_k (c_iy (x - x_k) - c_ix (y - y_k)).  Returns the
+// so c_i . u_w = omega_k (c_iy (x - x_k) - c_ix (y - y_k)), with (x, y) the
+// node's image beside the roller (the wrapped source plus c_i: the rollers
+// of boxes with ny = nx/2 reach across the periodic y boundary).  Returns the
 // number of links; fills `out` when it is not NULL, and `outq` (the
 // interpolated walls' entries of Geo::rlinkq) when it is not NULL.  The
 // link from x toward x - c_i meets the circle of radius r about c_k at
@@ -118,7 +120,10 @@ long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::ve
                 }
                 const int c2 = ci[0] * ci[0] + ci[1] * ci[1] + ci[2] * ci[2];
                 const double w = q == 9 ? (c2 == 1 ? 1.0 / 9 : 1.0 / 36) : (c2 == 1 ? 1.0 / 18 : 1.0 / 36);
-                const double cu = g.om[k] * (ci[1] * (x - g.rcx[k]) - ci[0] * (y - g.rcy[k]));
+                // in the frame of the roller: the node's image beside it (the
+                // wrapped source plus c_i)
+                const double dx = xs + ci[0] - g.rcx[k], dy = ys + ci[1] - g.rcy[k];
+                const double cu = g.om[k] * (ci[1] * dx - ci[0] * dy);
                 const float coef = float(6.0 * w * cu);
                 int4 e;
                 e.x = y * p.nx + x;
@@ -127,13 +132,8 @@ long long roller_links(const fre_params &p, int q, const RollerPlane &g, std::ve
                 std::memcpy(&e.w, &coef, sizeof(float));
                 out->push_back(e);
                 if (outq) {
-                    // from the node's periodic image beside the roller (the
-                    // wrapped source plus c_i); the moving-wall coefficient
-                    // from the same image
+                    // from the node's periodic image beside the roller (dx, dy)
                     const double r = p.nx / 8.0;
-                    const double dx = xs + ci[0] - g.rcx[k], dy = ys + ci[1] - g.rcy[k];
-                    const float coefi = float(6.0 * w * g.om[k] * (ci[1] * dx - ci[0] * dy));
-                    std::memcpy(&out->back().w, &coefi, sizeof(float));
                     const double cc = ci[0] * ci[0] + ci[1] * ci[1], dc = dx * ci[0] + dy * ci[1];
                     const double dd = dx * dx + dy * dy - r * r, disc = dc * dc - cc * dd;
                     double t = dd / (dc + std::sqrt(disc > 0.0 ? disc : 0.0));

@@ -299,7 +299,10 @@ __device__ __forceinline__ int pull_source(const Geo &G, const Site &s, int i, T
     if (G.device == FRE_FOUR_ROLLER) {
         const int k = G.solid[src];
         if (k) {
-            const double xw = s.x - 0.5 * Lat<Q>::cx(i), yw = s.y - 0.5 * cy;
+            // the wall point in the frame of the roller: the wrapped source
+            // plus c_i / 2
+            const double xw = wrapi(s.x - Lat<Q>::cx(i), G.nx) + 0.5 * Lat<Q>::cx(i);
+            const double yw = wrapi(s.y - cy, G.ny) + 0.5 * cy;
             uwx = T(-G.om[k] * (yw - G.rcy[k]));
             uwy = T(G.om[k] * (xw - G.rcx[k]));
             return -1;
@@ -660,9 +663,12 @@ __device__ __forceinline__ void node_update(const Launch &L, const Site &s) {
             const int k = L.G.solid[nb];
             if (k) {
                 const int o = Lat<Q>::opp(i);
-                // c_opp(i) . u_w = -(c_i . u_w), u_w = omega_k z x (x - c_k)
-                const T cu = -T(L.G.om[k]) * (T(Lat<Q>::cy(i)) * (T(s.x) - T(L.G.rcx[k])) -
-                                               T(Lat<Q>::cx(i)) * (T(s.y) - T(L.G.rcy[k])));
+                // c_opp(i) . u_w = -(c_i . u_w), u_w = omega_k z x (x - c_k),
+                // x in the frame of the roller (the wrapped roller node - c_i)
+                const int xr = wrapi(s.x + Lat<Q>::cx(i), L.G.nx) - Lat<Q>::cx(i);
+                const int yr = wrapi(s.y + Lat<Q>::cy(i), L.G.ny) - Lat<Q>::cy(i);
+                const T cu = -T(L.G.om[k]) * (T(Lat<Q>::cy(i)) * (T(xr) - T(L.G.rcx[k])) -
+                                               T(Lat<Q>::cx(i)) * (T(yr) - T(L.G.rcy[k])));
                 const T wi6 = T(6.0 * Lat<Q>::w(i));
                 P::stf(L.dst, L.G.np, o, nb, fs + wi6 * T(L.P.rho0) * cu, T(L.P.rho0), T(0));
                 P::stg(L.dst, L.G.np, o, nb, gs + wi6 * m.phi * cu);

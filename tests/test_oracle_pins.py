@@ -765,7 +765,8 @@ def test_brute_force_one_step_four_roller(orc, lattice, shape, interp):
             links += 1
             x0, y0, om = rollers[k]
             if not interp:
-                xw, yw = x - 0.5 * ci[i, 0], y - 0.5 * ci[i, 1]
+                # the wall point in the frame of the roller: the wrapped source plus c_i / 2
+                xw, yw = xs + 0.5 * ci[i, 0], ys + 0.5 * ci[i, 1]
                 uw = np.array([-om * (yw - y0), om * (xw - x0), 0.0])[:d]
                 cu = float(cd[i] @ uw)
                 f_new[i, z, y, x] = post_f[opp[i], z, y, x] + 2 * w[i] * rho0 * cu / CS2
